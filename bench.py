@@ -1,0 +1,322 @@
+#!/usr/bin/env python
+"""Benchmark: whole-archive two-layer decode of FASTQ-shaped data.
+
+Workload: 256 MiB of synthetic FASTQ (seed 1; header/150-base read/'+'/
+quality records), 16 KiB blocks (16,384 blocks), encoded by the library's
+host encoder.  A step is one ace_decode_all: every block's three rANS
+streams decoded and its literals and absolute-offset matches resolved into
+the output, on the GPU.  Also measured: 10,000 random single-block seeks
+(seed 2), one launch sequence plus a synchronise per seek; the end-to-end
+time through the C ABI from pinned host memory; the CPU oracle on the host
+cores.
+
+Prints one JSON line.  Under torchrun each rank decodes its own replica of
+the archive (replicas only: no data-path collective).
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+TOTAL = 1 << 28
+LOG2B = 14
+MIN_MATCH = 16
+SEED = 1
+SEEK_SEED = 2
+WORKLOAD = "fastq-256MiB-16KiB-blocks"
+METRIC = "decompressed GB/s (% HBM roofline); 16KB seek p50/p99 us, batched vs plain"
+KERNEL_SOURCES = ["paper_2606_24531_gb300/csrc/ace.cu", "paper_2606_24531_gb300/csrc/ace_device.cuh"]
+PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "decode_kernel_fastq256.txt")
+
+
+def kernel_sha():
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic():
+    """dram read+write bytes per decode launch from the committed ncu summary,
+    if it was taken on the current kernel sources."""
+    try:
+        kv = {}
+        with open(PROFILE_SUMMARY) as f:
+            for ln in f:
+                if ":" in ln:
+                    k, v = ln.split(":", 1)
+                    kv[k.strip()] = v.strip()
+        if kv.get("kernel_sources_sha256") == kernel_sha():
+            return int(kv["traffic_bytes_per_launch"])
+    except (OSError, KeyError, ValueError):
+        pass
+    return None
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.f = tempfile.TemporaryFile(mode="w+")
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(gpu_index), "--query-gpu=" + self.Q,
+                                       "--format=csv,noheader,nounits", "-lms", "100"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        self.p.wait()
+        self.f.seek(0)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.f:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def make_workload():
+    import synth
+    from paper_2606_24531_gb300 import ace
+
+    data = synth.generate("fastq", TOTAL, SEED)
+    arc, stats = ace.ace_encode(data, LOG2B, MIN_MATCH, stats=True)
+    return data, arc, stats
+
+
+def run_reference(args, rank):
+    """The oracle (plain sequential C decoder) on the host cores."""
+    if rank != 0:
+        return
+    import oracle
+
+    data, arc, _ = make_workload()
+    t_all = []
+    for k in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        out = oracle.decode(arc)
+        t1 = time.perf_counter()
+        if k >= args.warmup:
+            t_all.append(t1 - t0)
+    assert np.array_equal(out, data)
+    ms = 1e3 * statistics.mean(t_all)
+    gbs = data.size / (ms / 1e3) / 1e9
+    sample = "whole archive, %d bytes decompressed, one thread" % data.size
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": gbs, "unit": "GB/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "blocks": int(data.size >> LOG2B)},
+        "cpu_baseline": {"value": gbs, "unit": "GB/s", "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": gbs, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--seeks", type=int, default=10000)
+    ap.add_argument("--no-extras", action="store_true", help="decode steps only (for profiler runs)")
+    args = ap.parse_args()
+    assert args.warmup >= 3 or args.no_extras, "at least 3 warm-up steps"
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+
+    import torch
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_2606_24531_gb300 import ace
+    from paper_2606_24531_gb300.archive import DeviceArchive
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    data, arc, stats = make_workload()
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    t0 = time.perf_counter()
+    da = DeviceArchive(arc, max_seek_blocks=512, device=dev)
+    index_ms = 1e3 * (time.perf_counter() - t0)
+    info = da.info
+    total = info["total_size"]
+    out = torch.empty(total, dtype=torch.uint8, device=dev)
+    d_data = torch.from_numpy(data).to(dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    # correctness before timing: bit-exact against the original bytes
+    da.decode_all(out)
+    st = da.sync()
+    assert st == ace.ACE_OK, ace.ace_status_str(st)
+    assert torch.equal(out, d_data), "decode differs from the original"
+
+    for _ in range(args.warmup):
+        da.decode_all(out)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    time.sleep(0.2)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for k in range(args.steps):
+        flush.fill_(k & 255)  # L2 flush between timed steps, outside the events
+        ev[k][0].record(stream)
+        da.decode_all(out)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = sampler.stop()
+    st = da.sync()
+    assert st == ace.ACE_OK, ace.ace_status_str(st)
+    times = [a.elapsed_time(b) for a, b in ev]
+    ms = statistics.mean(times)
+    if dist:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * total / (ms / 1e3) / 1e9
+
+    peaks, peak_kind = measured_peaks()
+    hdr = arc[:64].view(np.uint64)
+    deps_bytes = int(hdr[6]) - int(hdr[5])  # payload_off - deps_off: not read by a whole decode
+    alg = (arc.size - deps_bytes) + stats["match_src_bytes"] + total
+    achieved = alg / (ms / 1e3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / peaks["hbm_gbs"], "traffic": profiled_traffic(),
+                "algorithmic_bytes": alg, "peak_kind": peak_kind}
+
+    result = {
+        "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "blocks": info["n_blocks"], "block_size": info["block_size"],
+                   "archive_bytes": int(arc.size), "ratio": total / arc.size, "levels": info["n_levels"],
+                   "literal_fraction": stats["literal_bytes"] / total, "matches": stats["n_matches"],
+                   "l2": "flushed between timed steps (256 MiB fill)", "parallelism": "replicas"},
+        "roofline": roofline,
+        "gpu_launches": 2 * args.steps,
+        "clocks": clocks,
+        "index_build_ms": index_ms,
+    }
+
+    if not args.no_extras:
+        # plain seeks: one seek launch sequence + a synchronise per request
+        import synth
+
+        nb = info["n_blocks"]
+        blocks = synth.uniform(SEEK_SEED, args.seeks, 0, nb - 1)
+        B = info["block_size"]
+        seek_out = torch.empty(B, dtype=torch.uint8, device=dev)
+        lat = []
+        for i, b in enumerate(blocks):
+            b = int(b)
+            t0 = time.perf_counter()
+            ace.ace_seek(da.idx, b * B, B, seek_out, B, da.d_scratch, da.scratch_bytes, stream)
+            s = ace.ace_sync(da.idx, da.d_scratch, stream)
+            lat.append(time.perf_counter() - t0)
+            assert s == ace.ACE_OK
+            if i % 997 == 0:
+                assert torch.equal(seek_out, d_data[b * B:(b + 1) * B])
+        lat_us = np.array(lat) * 1e6
+        result["seek"] = {"kind": "plain: ace_seek + ace_sync per 16 KiB block", "n": len(lat),
+                          "p50_us": float(np.percentile(lat_us, 50)),
+                          "p99_us": float(np.percentile(lat_us, 99)),
+                          "mean_us": float(lat_us.mean()), "batched": None,
+                          "paper_context_us": 334.0}
+
+        # end to end through the C ABI from pinned host memory
+        h_arc = torch.from_numpy(arc).pin_memory()
+        h_out = torch.empty(total, dtype=torch.uint8).pin_memory()
+        e2e_t = []
+        n_e2e = min(args.steps, 10)
+        for k in range(n_e2e + 2):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            da.d_arc.copy_(h_arc, non_blocking=True)
+            idx = ace.ace_index_build(da.d_arc, arc.size, arc[:64], da.d_index, da.index_bytes, stream)
+            ace.ace_decode_all(idx, out, total, da.d_scratch, da.scratch_bytes, None, stream)
+            h_out.copy_(out, non_blocking=True)
+            s = ace.ace_sync(idx, da.d_scratch, stream)
+            t1 = time.perf_counter()
+            ace.ace_index_free(idx)
+            assert s == ace.ACE_OK
+            if k >= 2:
+                e2e_t.append(t1 - t0)
+        assert np.array_equal(h_out.numpy()[:4096], data[:4096])
+        e2e_s = statistics.mean(e2e_t)
+        result["e2e"] = {"value": world * total / e2e_s / 1e9, "unit": "GB/s",
+                         "h2d_bytes_per_step": int(arc.size), "d2h_bytes_per_step": int(total),
+                         "includes": "H2D archive, index build, decode, D2H output"}
+
+        # the oracle on the host cores (rank 0 only)
+        if rank == 0:
+            import oracle
+
+            t0 = time.perf_counter()
+            ref = oracle.decode(arc)
+            dt = time.perf_counter() - t0
+            assert np.array_equal(ref, data)
+            result["cpu_baseline"] = {"value": data.size / dt / 1e9, "unit": "GB/s", "cores": 1,
+                                      "kind": "oracle",
+                                      "sample": "the whole 256 MiB archive, one thread (%.1f s)" % dt,
+                                      "cpu": os.uname().machine, "nproc": os.cpu_count()}
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,242 @@
+/*
+ * ace.h -- C ABI of the GPU library for the two-layer codec of "Unified
+ * Position-Invariant Random Access Through Two Compression Layers via
+ * Absolute-Offset Coordinates" (ACEAPEX).
+ *
+ * The codec stacks an LZ77 match layer whose back-references are absolute
+ * positions in the decompressed output (Section 2, Section 3) under a
+ * per-block interleaved-rANS entropy layer over separated literal, length
+ * and offset streams (Section 3, Section 6.1, Section 9).  Because both
+ * layers are entered at the block boundary, one absolute coordinate names
+ * the entry point of both (Section 3), and a block decodes through both
+ * layers once the blocks holding its match sources are present (Section 2).
+ * The archive layout is in ace_format.h.
+ *
+ * Conventions for every call:
+ *  - Pointers named d_* are device pointers, h_* host pointers.
+ *  - The library never allocates device memory.  The caller sizes buffers
+ *    with the *_size calls and owns them: the archive (which must outlive
+ *    the index), the index memory, scratch and outputs.  The library owns
+ *    only the small host handle that ace_index_free releases.
+ *  - Device work is enqueued on the caller's stream and is asynchronous
+ *    unless a call says otherwise.  Host-side validation errors return at
+ *    once; errors found on the device (corrupt streams, a wait that gave up)
+ *    are recorded in the scratch status word and returned by ace_sync.
+ *  - Calls that share one scratch buffer must be ordered on one stream;
+ *    calls with separate scratch buffers may overlap on the device.
+ *  - The library keeps no global state except the CUDA device it runs on,
+ *    taken as the current device when the index is built.
+ */
+#ifndef ACE_H
+#define ACE_H
+#include <stddef.h>
+#include <stdint.h>
+
+#include <cuda_runtime_api.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t ace_status;
+enum {
+    ACE_OK = 0,
+    ACE_E_INVAL = 1,   /* bad argument, null pointer, unaligned buffer */
+    ACE_E_CORRUPT = 2, /* archive fails a structural or entropy check */
+    ACE_E_RANGE = 3,   /* coordinate range outside the decompressed data */
+    ACE_E_NOMEM = 4,   /* caller buffer or scratch too small */
+    ACE_E_TIMEOUT = 5, /* a device-side wait gave up */
+    ACE_E_CUDA = 6     /* a CUDA runtime call failed */
+};
+
+/* Name of a status code ("ACE_OK", ...); never NULL. */
+const char *ace_status_str(ace_status s);
+
+/* ------------------------------------------------------------ encoding */
+
+typedef struct {
+    uint32_t log2_block; /* block size 2^log2_block bytes, 8..16 (Section 2) */
+    uint32_t min_match;  /* shortest match taken, >= 4 */
+    uint32_t threads;    /* host threads; 0 = all hardware threads */
+    uint32_t max_chain;  /* candidates tried per position in the in-block chain */
+} ace_encode_params;
+
+/*
+ * Host encoder (CPU).  Writes the archive of h_in[0, n) into h_arc:
+ * greedy parse (Section 2's global match search: earliest occurrences of
+ * 16-byte keys anywhere earlier in the input, plus shorter repeats inside
+ * the block), stream separation, per-block rANS with 32 interleaved 32-bit
+ * states, 12-bit frequencies and byte renormalisation (Section 3), and the
+ * block dependency table.  ace_encode_bound gives a size that always
+ * suffices.  Returns ACE_E_INVAL for bad parameters, ACE_E_NOMEM when cap is
+ * too small.  Deterministic: the archive does not depend on the thread count.
+ */
+ace_status ace_encode_bound(uint64_t n, uint32_t log2_block, uint64_t *bound);
+ace_status ace_encode(const void *h_in, uint64_t n, const ace_encode_params *params,
+                      void *h_arc, uint64_t cap, uint64_t *arc_len);
+
+/*
+ * The same encoder in two steps, for inputs whose bound is too large to
+ * allocate: ace_encode_run encodes into library-owned host memory and
+ * reports the exact archive size; ace_encode_write copies the archive out
+ * (cap >= that size); ace_encode_free releases the encoder.
+ */
+typedef struct ace_encoder ace_encoder;
+ace_status ace_encode_run(const void *h_in, uint64_t n, const ace_encode_params *params,
+                          ace_encoder **out, uint64_t *arc_len);
+ace_status ace_encode_write(const ace_encoder *enc, void *h_arc, uint64_t cap);
+ace_status ace_encode_free(ace_encoder *enc);
+
+/* What the parse produced, for reporting: tokens, matches, literal and match
+ * bytes, match_src_bytes = sum over matches of min(length, distance) (the
+ * distinct source bytes a decoder must read), dependency intervals and
+ * levels (1 + the deepest block level). */
+typedef struct {
+    uint64_t n_tokens;
+    uint64_t n_matches;
+    uint64_t literal_bytes;
+    uint64_t match_bytes;
+    uint64_t match_src_bytes;
+    uint64_t n_dep_intervals;
+    uint32_t n_levels;
+    uint32_t reserved;
+} ace_encode_stats;
+ace_status ace_encode_get_stats(const ace_encoder *enc, ace_encode_stats *h_stats);
+
+/* ------------------------------------------------------------ the index */
+
+typedef struct ace_index ace_index;
+
+typedef struct {
+    uint64_t total_size;    /* decompressed bytes */
+    uint64_t n_blocks;
+    uint64_t archive_bytes;
+    uint64_t n_dep_intervals;
+    uint32_t block_size;
+    uint32_t off_width;
+    uint32_t n_levels;      /* dependency levels: 1 + the deepest level */
+    uint32_t reserved;
+} ace_info;
+
+/*
+ * Bytes of device memory the index of an archive needs, from its 64-byte
+ * header (h_header, header_bytes >= 64).  ACE_E_CORRUPT for a header that
+ * is not a version-1 archive.
+ */
+ace_status ace_index_size(const void *h_header, uint64_t header_bytes, uint64_t *index_bytes);
+
+/*
+ * Builds the block index on the device (Section 3: the block boundary is
+ * the entry point of both layers; Section 2: a block decodes once the blocks
+ * holding its sources are present): validates every directory entry and the
+ * dependency table, computes each block's dependency level (0 without
+ * sources in other blocks, else 1 + the deepest source block) and the decode
+ * order (level, then block).  d_archive holds archive_bytes bytes (16-byte
+ * aligned), h_header its first 64 bytes on the host.  d_index_mem (256-byte
+ * aligned, index_bytes from ace_index_size) is written by this call and
+ * only read afterwards.  Synchronises s before it returns; on success *out is
+ * a new handle.  ACE_E_CORRUPT when the archive fails validation.
+ */
+ace_status ace_index_build(const void *d_archive, uint64_t archive_bytes, const void *h_header,
+                           uint64_t header_bytes, void *d_index_mem, uint64_t index_bytes,
+                           cudaStream_t s, ace_index **out);
+
+/* Fills h_info from the host handle (no device access). */
+ace_status ace_index_info(const ace_index *idx, ace_info *h_info);
+
+/* Releases the host handle; the caller frees the device buffers. */
+ace_status ace_index_free(ace_index *idx);
+
+/* ------------------------------------------------------------- scratch */
+
+/*
+ * Scratch bytes for one call on this index.  max_seek_blocks is the largest
+ * number of blocks a seek may decode (its target blocks plus every block
+ * they read from, transitively); 0 sizes scratch for ace_decode_all only.
+ * Scratch must be 256-byte aligned.  Its first use must follow
+ * ace_scratch_init on the same stream.
+ */
+ace_status ace_scratch_size(const ace_index *idx, uint64_t max_seek_blocks, uint64_t *bytes);
+
+/* Clears scratch (asynchronous on s). */
+ace_status ace_scratch_init(const ace_index *idx, void *d_scratch, uint64_t scratch_bytes,
+                            cudaStream_t s);
+
+/* ------------------------------------------------------------ decoding */
+
+typedef struct {
+    uint32_t warps_per_cta;   /* 1..16; 0 = default (4) */
+    uint32_t ctas_per_sm;     /* 0 = as many as fit */
+    uint32_t chunk_tokens;    /* tokens staged per step, 32..256, multiple of 32; 0 = 128 */
+    uint32_t reserved;
+    uint64_t wait_timeout_ns; /* bound on each device-side wait; 0 = 2 s */
+} ace_tune;
+
+/*
+ * Whole-archive decode through both layers: every block's three streams are
+ * rANS-decoded and its literals and absolute-offset matches resolved
+ * straight into d_out (out_bytes >= total_size), by persistent warps that
+ * take blocks in (level, block) order and wait, bounded, for the blocks
+ * their matches read (Section 2).  tune may be NULL.  Asynchronous; check
+ * with ace_sync.
+ */
+ace_status ace_decode_all(const ace_index *idx, void *d_out, uint64_t out_bytes, void *d_scratch,
+                          uint64_t scratch_bytes, const ace_tune *tune, cudaStream_t s);
+
+/*
+ * Unified seek (Section 5): the absolute range [coord, coord + len) names
+ * its covering blocks; they and every block their matches read,
+ * transitively, are decoded from the archive alone into scratch, and exactly
+ * the len requested bytes are written to d_out[0, len).  Nothing else in
+ * d_out is touched.  coord and len need no alignment.  ACE_E_RANGE when
+ * len == 0 or coord + len > total_size.  If the blocks to decode exceed the
+ * max_seek_blocks the scratch was sized for, ace_sync reports ACE_E_NOMEM.
+ * Asynchronous.
+ */
+ace_status ace_seek(const ace_index *idx, uint64_t coord, uint64_t len, void *d_out,
+                    uint64_t out_bytes, void *d_scratch, uint64_t scratch_bytes, cudaStream_t s);
+
+/* Sets the tuning ace_seek uses, and ace_decode_all when given no tune
+ * (NULL restores the defaults).  Not thread-safe against calls in flight on
+ * the host. */
+ace_status ace_index_set_tune(ace_index *idx, const ace_tune *tune);
+
+/* Synchronises s and returns (then clears) the first device-side error
+ * recorded in the scratch status word. */
+ace_status ace_sync(const ace_index *idx, void *d_scratch, cudaStream_t s);
+
+/* ---------------------------------------------------------- verification */
+
+typedef struct {
+    uint64_t fnv_before;     /* FNV-1a 64 of the poisoned slice before the seek */
+    uint64_t fnv_after;      /* FNV-1a 64 of the slice after the seek */
+    uint64_t guard_bad_before; /* guard bytes differing from the canary, before */
+    uint64_t guard_bad_after;  /* ... and after the seek */
+    int32_t phase1_ok;       /* fnv_before != expected: the slice held no original data */
+    int32_t phase2_ok;       /* fnv_after == expected: the seek produced the original */
+    int32_t phase3_ok;       /* no guard byte changed: neighbours untouched */
+    ace_status seek_status;  /* ace_sync result of the seek */
+} ace_verify_report;
+
+/*
+ * The three-phase check of Section 5.  d_buf holds guard_bytes, then len
+ * bytes for the slice, then guard_bytes.  The guards are filled with a
+ * canary pattern from canary_seed and the slice with a different poison
+ * pattern; phase 1 checks the slice's FNV-1a 64 differs from
+ * expected_fnv1a64, the seek runs, phase 2 checks the slice's FNV equals it,
+ * phase 3 checks every guard byte still holds its canary.  Synchronous.
+ */
+ace_status ace_verify(const ace_index *idx, uint64_t coord, uint64_t len, void *d_buf,
+                      uint64_t guard_bytes, uint64_t expected_fnv1a64, uint32_t canary_seed,
+                      void *d_scratch, uint64_t scratch_bytes, ace_verify_report *h_rep,
+                      cudaStream_t s);
+
+/* FNV-1a 64 (Fowler/Noll/Vo; the paper's bit-perfect check, Section 4) of
+ * d_p[0, n), computed on the device into *d_result (8 bytes, device memory).
+ * Asynchronous. */
+ace_status ace_fnv1a64(const void *d_p, uint64_t n, uint64_t *d_result, cudaStream_t s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

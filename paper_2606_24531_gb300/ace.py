@@ -1,0 +1,235 @@
+"""Thin ctypes binding of libace.so: the C ABI of include/ace.h under the
+same names, doing argument marshalling only.  Every step of decoding runs in
+the library's CUDA kernels; there is no Python or CPU fallback, and loading
+fails loudly when the library has not been built.
+
+Device buffers are passed as integers or as objects with ``data_ptr()``
+(torch tensors); streams as integers or objects with ``cuda_stream``.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+ACE_OK, ACE_E_INVAL, ACE_E_CORRUPT, ACE_E_RANGE, ACE_E_NOMEM, ACE_E_TIMEOUT, ACE_E_CUDA = range(7)
+
+
+class AceError(RuntimeError):
+    def __init__(self, status, what):
+        super().__init__("%s: %s" % (what, ace_status_str(status)))
+        self.status = status
+
+
+class ace_encode_params(ctypes.Structure):
+    _fields_ = [("log2_block", ctypes.c_uint32), ("min_match", ctypes.c_uint32),
+                ("threads", ctypes.c_uint32), ("max_chain", ctypes.c_uint32)]
+
+
+class ace_encode_stats(ctypes.Structure):
+    _fields_ = [("n_tokens", ctypes.c_uint64), ("n_matches", ctypes.c_uint64),
+                ("literal_bytes", ctypes.c_uint64), ("match_bytes", ctypes.c_uint64),
+                ("match_src_bytes", ctypes.c_uint64), ("n_dep_intervals", ctypes.c_uint64),
+                ("n_levels", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+
+
+class ace_info(ctypes.Structure):
+    _fields_ = [("total_size", ctypes.c_uint64), ("n_blocks", ctypes.c_uint64),
+                ("archive_bytes", ctypes.c_uint64), ("n_dep_intervals", ctypes.c_uint64),
+                ("block_size", ctypes.c_uint32), ("off_width", ctypes.c_uint32),
+                ("n_levels", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+
+
+class ace_tune(ctypes.Structure):
+    _fields_ = [("warps_per_cta", ctypes.c_uint32), ("ctas_per_sm", ctypes.c_uint32),
+                ("chunk_tokens", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
+                ("wait_timeout_ns", ctypes.c_uint64)]
+
+
+class ace_verify_report(ctypes.Structure):
+    _fields_ = [("fnv_before", ctypes.c_uint64), ("fnv_after", ctypes.c_uint64),
+                ("guard_bad_before", ctypes.c_uint64), ("guard_bad_after", ctypes.c_uint64),
+                ("phase1_ok", ctypes.c_int32), ("phase2_ok", ctypes.c_int32),
+                ("phase3_ok", ctypes.c_int32), ("seek_status", ctypes.c_int32)]
+
+
+_lib = None
+_u64, _u32, _vp, _i32 = ctypes.c_uint64, ctypes.c_uint32, ctypes.c_void_p, ctypes.c_int32
+_P = ctypes.POINTER
+
+_SIGS = {
+    "ace_status_str": ([_i32], ctypes.c_char_p),
+    "ace_encode_bound": ([_u64, _u32, _P(_u64)], _i32),
+    "ace_encode": ([_vp, _u64, _P(ace_encode_params), _vp, _u64, _P(_u64)], _i32),
+    "ace_encode_run": ([_vp, _u64, _P(ace_encode_params), _P(_vp), _P(_u64)], _i32),
+    "ace_encode_write": ([_vp, _vp, _u64], _i32),
+    "ace_encode_free": ([_vp], _i32),
+    "ace_encode_get_stats": ([_vp, _P(ace_encode_stats)], _i32),
+    "ace_index_size": ([_vp, _u64, _P(_u64)], _i32),
+    "ace_index_build": ([_vp, _u64, _vp, _u64, _vp, _u64, _vp, _P(_vp)], _i32),
+    "ace_index_info": ([_vp, _P(ace_info)], _i32),
+    "ace_index_free": ([_vp], _i32),
+    "ace_scratch_size": ([_vp, _u64, _P(_u64)], _i32),
+    "ace_scratch_init": ([_vp, _vp, _u64, _vp], _i32),
+    "ace_decode_all": ([_vp, _vp, _u64, _vp, _u64, _P(ace_tune), _vp], _i32),
+    "ace_seek": ([_vp, _u64, _u64, _vp, _u64, _vp, _u64, _vp], _i32),
+    "ace_sync": ([_vp, _vp, _vp], _i32),
+    "ace_index_set_tune": ([_vp, _P(ace_tune)], _i32),
+    "ace_verify": ([_vp, _u64, _u64, _vp, _u64, _u64, _u32, _vp, _u64, _P(ace_verify_report), _vp], _i32),
+    "ace_fnv1a64": ([_vp, _u64, _vp, _vp], _i32),
+}
+
+
+def lib():
+    """The loaded libace.so; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(_build.LIB):
+            raise ImportError("libace.so is not built (%s); run __graft_entry__.build()" % _build.LIB)
+        L = ctypes.CDLL(_build.LIB)
+        for name, (args, res) in _SIGS.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = L
+    return _lib
+
+
+def exported_symbols():
+    return sorted(_SIGS)
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    raise TypeError("cannot take a device pointer of %r" % type(x))
+
+
+def _stream(s):
+    if s is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream
+
+
+def _check(rc, what):
+    if rc != ACE_OK:
+        raise AceError(rc, what)
+
+
+def ace_status_str(status):
+    return lib().ace_status_str(int(status)).decode()
+
+
+# ------------------------------------------------------------------ encoding
+
+def ace_encode_bound(n, log2_block):
+    out = _u64()
+    _check(lib().ace_encode_bound(n, log2_block, ctypes.byref(out)), "ace_encode_bound")
+    return out.value
+
+
+def ace_encode(h_in, log2_block=14, min_match=4, threads=0, max_chain=16, stats=False):
+    """Encode host bytes (numpy uint8) into an archive (numpy uint8) on the
+    CPU; with stats=True also return the parse statistics as a dict."""
+    a = np.ascontiguousarray(h_in, dtype=np.uint8)
+    prm = ace_encode_params(log2_block, min_match, threads, max_chain)
+    enc, n = _vp(), _u64()
+    _check(lib().ace_encode_run(a.ctypes.data, a.size, ctypes.byref(prm), ctypes.byref(enc),
+                                ctypes.byref(n)), "ace_encode_run")
+    try:
+        arc = np.empty(n.value, np.uint8)
+        _check(lib().ace_encode_write(enc, arc.ctypes.data, arc.size), "ace_encode_write")
+        st = ace_encode_stats()
+        _check(lib().ace_encode_get_stats(enc, ctypes.byref(st)), "ace_encode_get_stats")
+    finally:
+        lib().ace_encode_free(enc)
+    if stats:
+        return arc, {k: getattr(st, k) for k, _ in ace_encode_stats._fields_ if k != "reserved"}
+    return arc
+
+
+# --------------------------------------------------------------------- index
+
+def ace_index_size(h_header):
+    h = np.ascontiguousarray(h_header[:64], dtype=np.uint8)
+    out = _u64()
+    _check(lib().ace_index_size(h.ctypes.data, h.size, ctypes.byref(out)), "ace_index_size")
+    return out.value
+
+
+def ace_index_build(d_archive, archive_bytes, h_header, d_index_mem, index_bytes, stream=None):
+    h = np.ascontiguousarray(h_header[:64], dtype=np.uint8)
+    out = _vp()
+    _check(lib().ace_index_build(_ptr(d_archive), archive_bytes, h.ctypes.data, h.size,
+                                 _ptr(d_index_mem), index_bytes, _stream(stream), ctypes.byref(out)),
+           "ace_index_build")
+    return out
+
+
+def ace_index_info(idx):
+    info = ace_info()
+    _check(lib().ace_index_info(idx, ctypes.byref(info)), "ace_index_info")
+    return {k: getattr(info, k) for k, _ in ace_info._fields_ if k != "reserved"}
+
+
+def ace_index_free(idx):
+    lib().ace_index_free(idx)
+
+
+def ace_scratch_size(idx, max_seek_blocks=0):
+    out = _u64()
+    _check(lib().ace_scratch_size(idx, max_seek_blocks, ctypes.byref(out)), "ace_scratch_size")
+    return out.value
+
+
+def ace_scratch_init(idx, d_scratch, scratch_bytes, stream=None):
+    _check(lib().ace_scratch_init(idx, _ptr(d_scratch), scratch_bytes, _stream(stream)), "ace_scratch_init")
+
+
+# ------------------------------------------------------------------ decoding
+
+def make_tune(warps_per_cta=0, ctas_per_sm=0, chunk_tokens=0, wait_timeout_ns=0):
+    return ace_tune(warps_per_cta, ctas_per_sm, chunk_tokens, 0, wait_timeout_ns)
+
+
+def ace_decode_all(idx, d_out, out_bytes, d_scratch, scratch_bytes, tune=None, stream=None):
+    t = ctypes.byref(tune) if tune is not None else None
+    _check(lib().ace_decode_all(idx, _ptr(d_out), out_bytes, _ptr(d_scratch), scratch_bytes, t,
+                                _stream(stream)), "ace_decode_all")
+
+
+def ace_seek(idx, coord, length, d_out, out_bytes, d_scratch, scratch_bytes, stream=None):
+    _check(lib().ace_seek(idx, coord, length, _ptr(d_out), out_bytes, _ptr(d_scratch), scratch_bytes,
+                          _stream(stream)), "ace_seek")
+
+
+def ace_index_set_tune(idx, tune=None):
+    t = ctypes.byref(tune) if tune is not None else None
+    _check(lib().ace_index_set_tune(idx, t), "ace_index_set_tune")
+
+
+def ace_sync(idx, d_scratch, stream=None):
+    """Synchronise and return the first device-side status (does not raise)."""
+    return lib().ace_sync(idx, _ptr(d_scratch), _stream(stream))
+
+
+def ace_verify(idx, coord, length, d_buf, guard_bytes, expected_fnv1a64, canary_seed, d_scratch,
+               scratch_bytes, stream=None):
+    rep = ace_verify_report()
+    _check(lib().ace_verify(idx, coord, length, _ptr(d_buf), guard_bytes, expected_fnv1a64, canary_seed,
+                            _ptr(d_scratch), scratch_bytes, ctypes.byref(rep), _stream(stream)), "ace_verify")
+    return {k: getattr(rep, k) for k, _ in ace_verify_report._fields_}
+
+
+def ace_fnv1a64(d_p, n, d_result, stream=None):
+    _check(lib().ace_fnv1a64(_ptr(d_p), n, _ptr(d_result), _stream(stream)), "ace_fnv1a64")

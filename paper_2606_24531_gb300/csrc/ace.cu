@@ -1,0 +1,1034 @@
+// GPU library of the two-layer codec: block index, fused two-layer decode
+// (whole archive and unified seek), closure search, verification, and the
+// C ABI declared in include/ace.h.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "ace.h"
+#include "ace_device.cuh"
+#include "ace_format.h"
+
+using namespace ace;
+
+namespace {
+
+constexpr uint64_t kDefaultTimeoutNs = 2000000000ull;
+
+inline uint64_t align256(uint64_t v) { return (v + 255) & ~255ull; }
+
+__host__ __device__ inline uint32_t esc_cap(uint32_t log2B) { return 2 * ((1u << log2B) / 255) + 2; }
+
+// ------------------------------------------------------------ index kernels
+
+struct IndexArgs {
+  const uint8_t* arc;
+  const ace_block_dir* dir;
+  const uint32_t* dep_ptr;
+  const uint32_t* dep_iv;
+  IndexHdr* ih;
+  uint32_t* level;
+  uint32_t* order;
+  uint32_t* lv_count;  // n_blocks + 1 entries
+  uint32_t* lv_cursor; // n_blocks + 1 entries
+  uint64_t nb, total, payload_off, arc_bytes, deps_off;
+  uint32_t log2B, w;
+};
+
+// Checks every directory entry and dependency record so the decoder may trust
+// stream bounds and token counts (Section 2 block layout, Section 3 streams).
+__global__ void validate_kernel(IndexArgs a) {
+  uint64_t b = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  if (b >= a.nb) return;
+  const ace_block_dir d = a.dir[b];
+  uint64_t B = (uint64_t)1 << a.log2B, bstart = b << a.log2B;
+  uint64_t blen = min(B, a.total - bstart);
+  uint32_t where = 0;
+  for (int k = 0; k < 3 && !where; k++) {
+    if (d.mode[k] != 0) where = 1;
+    else if (d.nsym[k] == 0 && d.stream_bytes[k] != 0) where = 2;
+    else if (d.nsym[k] != 0) {
+      if (d.stream_bytes[k] < ACE_STREAM_HEAD || (d.stream_off[k] & 15)) where = 3;
+      else if (a.payload_off + d.stream_off[k] + d.stream_bytes[k] > a.arc_bytes ||
+               d.stream_off[k] > a.arc_bytes)
+        where = 4;
+    }
+  }
+  if (!where) {
+    if (d.ntok == 0 || d.ntok > blen + 1) where = 5;
+    else if (d.nsym[ACE_S_LIT] > blen) where = 6;
+    else if ((uint64_t)d.nsym[ACE_S_LEN] != 2ull * d.nesc + 2ull * d.ntok) where = 7;
+    else if ((uint64_t)d.nsym[ACE_S_OFF] != (uint64_t)a.w * (d.ntok - 1)) where = 8;
+    else if (d.nesc > esc_cap(a.log2B)) where = 9;
+  }
+  if (!where) {
+    uint32_t lo = a.dep_ptr[b], hi = a.dep_ptr[b + 1], niv = a.dep_ptr[a.nb];
+    if (lo > hi || hi > niv) where = 10;
+    else
+      for (uint32_t i = lo; i < hi && !where; i++) {
+        uint32_t f = a.dep_iv[2 * i], l = a.dep_iv[2 * i + 1];
+        if (f > l || l >= b) where = 11;
+      }
+  }
+  if (where) record_error(&a.ih->status, &a.ih->err_block, &a.ih->err_where, ACE_E_CORRUPT, (uint32_t)b, where);
+}
+
+// Dependency levels: level[b] = 0 without sources in other blocks, else
+// 1 + the deepest block it reads (Section 2).  Sources always precede, so
+// one CTA walks the blocks in chunks and relaxes each chunk to its fixed point.
+__global__ void levels_kernel(IndexArgs a) {
+  __shared__ int changed;
+  uint32_t maxlv = 0;
+  for (uint64_t c0 = 0; c0 < a.nb; c0 += blockDim.x) {
+    uint64_t b = c0 + threadIdx.x;
+    if (b < a.nb) a.level[b] = 0;
+    __syncthreads();
+    while (true) {
+      if (threadIdx.x == 0) changed = 0;
+      __syncthreads();
+      if (b < a.nb) {
+        uint32_t lv = 0;
+        for (uint32_t i = a.dep_ptr[b]; i < a.dep_ptr[b + 1]; i++)
+          for (uint32_t k = a.dep_iv[2 * i]; k <= a.dep_iv[2 * i + 1]; k++) lv = max(lv, a.level[k] + 1);
+        if (lv != a.level[b]) {
+          a.level[b] = lv;
+          changed = 1;
+        }
+      }
+      __syncthreads();
+      if (!changed) break;
+      __syncthreads();
+    }
+    if (b < a.nb) maxlv = max(maxlv, a.level[b]);
+  }
+  atomicMax(&a.ih->n_levels, maxlv + 1);
+}
+
+__global__ void level_hist_kernel(IndexArgs a) {
+  uint64_t b = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  if (b < a.nb) atomicAdd(&a.lv_count[a.level[b]], 1u);
+}
+
+// Exclusive scan of the level histogram into level start offsets (one CTA).
+__global__ void level_scan_kernel(IndexArgs a) {
+  __shared__ uint32_t carry;
+  __shared__ uint32_t wsum[32];
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (uint64_t c0 = 0; c0 < a.nb + 1; c0 += blockDim.x) {
+    uint64_t i = c0 + threadIdx.x;
+    uint32_t v = i < a.nb + 1 ? a.lv_count[i] : 0;
+    uint32_t incl = warp_incl_sum(v, lane);
+    if (lane == 31) wsum[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+      uint32_t s = lane < nw ? wsum[lane] : 0;
+      uint32_t si = warp_incl_sum(s, lane);
+      if (lane < nw) wsum[lane] = si - s;
+    }
+    __syncthreads();
+    uint32_t ex = carry + wsum[wid] + incl - v;
+    if (i < a.nb + 1) a.lv_cursor[i] = ex;
+    __syncthreads();
+    if (threadIdx.x == blockDim.x - 1) carry = ex + v;
+    __syncthreads();
+  }
+}
+
+__global__ void level_scatter_kernel(IndexArgs a) {
+  uint64_t b = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  if (b < a.nb) a.order[atomicAdd(&a.lv_cursor[a.level[b]], 1u)] = (uint32_t)b;
+}
+
+// ----------------------------------------------------------- decode kernel
+
+struct DecodeArgs {
+  const uint8_t* arc;
+  const ace_block_dir* dir;
+  uint64_t payload_off;
+  uint64_t total;
+  uint64_t nb;
+  uint32_t log2B, w;
+  uint32_t chunk;          // tokens staged per step (multiple of 32)
+  uint32_t esc_cap;
+  uint32_t warp_smem;      // bytes of shared memory per warp
+  uint32_t n_items;        // whole decode: work items; seek: read from the scratch header
+  const uint32_t* items;   // whole decode: blocks in (level, block) order; seek: the closure
+  uint8_t* out;            // whole decode: output (absolute positions); seek: block slots
+  ScratchHdr* sh;
+  uint32_t* ready;         // per block: the epoch once the block is decoded
+  const uint32_t* slot_of; // seek: block -> slot
+  uint8_t* slice;          // seek: caller's output
+  uint64_t coord, len;     // seek: requested range
+  uint64_t timeout_ns;
+};
+
+// Shared memory of one warp, carved from the dynamic allocation.
+struct WarpMem {
+  Lut* lut;        // [3]
+  uint32_t* tdst;  // [chunk + 1] start of each token's literal run, within the block
+  uint32_t* tlit;  // [chunk + 1] index of each token's first literal in the block's literals
+  uint32_t* tml;   // [chunk] match length
+  uint64_t* tsrc;  // [chunk] absolute source
+  uint8_t* codes;  // [2 chunk]
+  uint8_t* offb;   // [5 chunk]
+  uint16_t* esc;   // [esc_cap]
+};
+
+__host__ __device__ inline uint32_t warp_smem_bytes(uint32_t chunk, uint32_t escn) {
+  uint32_t b = 3 * sizeof(Lut);
+  b += 4 * (chunk + 1) * 2 + 4 * chunk + 8 * chunk;
+  b += 2 * chunk + 5 * chunk;
+  b += 2 * escn;
+  return (b + 15) & ~15u;
+}
+
+__device__ inline WarpMem carve(uint8_t* base, uint32_t chunk) {
+  WarpMem m;
+  m.lut = reinterpret_cast<Lut*>(base);
+  uint8_t* p = base + 3 * sizeof(Lut);
+  m.tsrc = reinterpret_cast<uint64_t*>(p);
+  p += 8 * chunk;
+  m.tdst = reinterpret_cast<uint32_t*>(p);
+  p += 4 * (chunk + 1);
+  m.tlit = reinterpret_cast<uint32_t*>(p);
+  p += 4 * (chunk + 1);
+  m.tml = reinterpret_cast<uint32_t*>(p);
+  p += 4 * chunk;
+  m.esc = reinterpret_cast<uint16_t*>(p);
+  p += 2 * 520;  // room for the largest escape table (64 KiB blocks)
+  m.codes = p;
+  p += 2 * chunk;
+  m.offb = p;
+  return m;
+}
+
+template <bool SEEK>
+struct Addr {
+  // device address of absolute output position p
+  __device__ __forceinline__ static uint8_t* at(const DecodeArgs& a, uint64_t p) {
+    if (SEEK) {
+      uint64_t k = p >> a.log2B;
+      return a.out + ((uint64_t)__ldg(a.slot_of + k) << a.log2B) + (p & ((1ull << a.log2B) - 1));
+    }
+    return a.out + p;
+  }
+};
+
+__device__ __forceinline__ void fail(const DecodeArgs& a, bool& ok, ace_status code, uint32_t b, uint32_t where,
+                                     uint32_t lane) {
+  if (ok && lane == 0) record_error(&a.sh->status, &a.sh->err_block, &a.sh->err_where, code, b, where);
+  ok = false;
+}
+
+// Copies one match: out[D + i] = out[S + i] for i < len in the sequential
+// LZ77 sense (a source overlapping its destination repeats with period D - S).
+// dst points at absolute position D inside the block being decoded.
+template <bool SEEK>
+__device__ __forceinline__ void copy_match_lane(const DecodeArgs& a, uint8_t* dst, uint64_t D, uint64_t S,
+                                                uint32_t len) {
+  if (!SEEK) {
+    const uint8_t* src = a.out + S;
+    for (uint32_t i = 0; i < len; i++) dst[i] = __ldcg(src + i);
+  } else {
+    for (uint32_t i = 0; i < len; i++) dst[i] = __ldcg(Addr<true>::at(a, S + i));
+  }
+  (void)D;
+}
+
+template <bool SEEK>
+__device__ __forceinline__ void copy_match_warp(const DecodeArgs& a, uint8_t* dst, uint64_t D, uint64_t S,
+                                                uint32_t len, uint32_t lane) {
+  uint64_t d = D - S;
+  if (d >= len) {
+    for (uint32_t i = lane; i < len; i += 32) dst[i] = __ldcg(Addr<SEEK>::at(a, S + i));
+  } else {
+    // period d: out[D + i] = out[S + (i mod d)], and [S, D) is complete
+    uint32_t dd = (uint32_t)d;
+    for (uint32_t i = lane; i < len; i += 32) dst[i] = __ldcg(Addr<SEEK>::at(a, S + i % dd));
+  }
+}
+
+// Decodes one block through both layers (Section 3 entry point, then the
+// Section 2 match layer) into its place.  Returns false if it found the block
+// corrupt or a wait gave up (the error is recorded).
+template <bool SEEK>
+__device__ bool decode_block(const DecodeArgs& a, const WarpMem& m, uint32_t b, uint32_t lane, uint32_t epoch) {
+  bool ok = true;
+  const uint32_t* dw = reinterpret_cast<const uint32_t*>(a.dir + b);
+  uint32_t dv = lane < 16 ? __ldg(dw + lane) : 0u;
+  uint64_t soff[3];
+  uint32_t sbytes[3], nsym[3];
+#pragma unroll
+  for (int k = 0; k < 3; k++) {
+    soff[k] = (uint64_t)__shfl_sync(kFull, dv, 2 * k) | ((uint64_t)__shfl_sync(kFull, dv, 2 * k + 1) << 32);
+    sbytes[k] = __shfl_sync(kFull, dv, 6 + k);
+    nsym[k] = __shfl_sync(kFull, dv, 9 + k);
+  }
+  const uint32_t ntok = __shfl_sync(kFull, dv, 12), nesc = __shfl_sync(kFull, dv, 13);
+  const uint64_t B = (uint64_t)1 << a.log2B, bstart = (uint64_t)b << a.log2B;
+  const uint32_t blen = (uint32_t)min(B, a.total - bstart);
+  const uint32_t w = a.w;
+  uint8_t* obase = SEEK ? a.out + ((uint64_t)__ldg(a.slot_of + b) << a.log2B) : a.out + bstart;
+
+  Rans st[3];
+  for (int k = 0; k < 3 && ok; k++)
+    if (!stream_setup(a.arc + a.payload_off + soff[k], sbytes[k], nsym[k], m.lut[k], st[k], lane))
+      fail(a, ok, ACE_E_CORRUPT, b, 20 + k, lane);
+  if (!ok) return false;
+
+  // escape values at the head of the length stream
+  uint8_t* escb = reinterpret_cast<uint8_t*>(m.esc);
+  if (!rans_decode(st[ACE_S_LEN], m.lut[ACE_S_LEN], 2 * nesc, lane, [&](uint32_t i, uint32_t s) { escb[i] = (uint8_t)s; }))
+    fail(a, ok, ACE_E_CORRUPT, b, 30, lane);
+  __syncwarp();
+
+  uint32_t out_pos = 0, lit_pos = 0, esc_rank = 0;
+  const uint32_t lt = lanemask_lt();
+  for (uint32_t t0 = 0; t0 < ntok && ok; t0 += a.chunk) {
+    const uint32_t tc = min(a.chunk, ntok - t0);
+    const uint32_t nm = (t0 + tc == ntok) ? tc - 1 : tc;  // matches in this chunk
+    uint32_t len_base = 2 * nesc + 2 * t0;
+    if (!rans_decode(st[ACE_S_LEN], m.lut[ACE_S_LEN], len_base + 2 * tc, lane,
+                     [&](uint32_t i, uint32_t s) { m.codes[i - len_base] = (uint8_t)s; }))
+      fail(a, ok, ACE_E_CORRUPT, b, 31, lane);
+    uint32_t off_base = w * t0;
+    if (ok && !rans_decode(st[ACE_S_OFF], m.lut[ACE_S_OFF], off_base + w * nm, lane,
+                           [&](uint32_t i, uint32_t s) { m.offb[i - off_base] = (uint8_t)s; }))
+      fail(a, ok, ACE_E_CORRUPT, b, 32, lane);
+    if (!ok) break;
+    __syncwarp();
+    // tokens: values, escapes, prefix sums (stream layout in ace_format.h)
+    bool bad = false;
+    for (uint32_t g = 0; g < tc; g += 32) {
+      uint32_t t = g + lane;
+      bool act = t < tc;
+      uint32_t c0 = act ? m.codes[2 * t] : 0, c1 = act ? m.codes[2 * t + 1] : 0;
+      bool e0 = act && c0 == 255, e1 = act && c1 == 255;
+      uint32_t b0 = __ballot_sync(kFull, e0), b1 = __ballot_sync(kFull, e1);
+      uint32_t r0 = esc_rank + __popc(b0 & lt) + __popc(b1 & lt), r1 = r0 + (e0 ? 1 : 0);
+      uint32_t lr = c0, ml = c1;
+      if (e0) {
+        if (r0 < nesc) lr = 255 + m.esc[r0];
+        else bad = true;
+      }
+      if (e1) {
+        if (r1 < nesc) ml = 255 + m.esc[r1];
+        else bad = true;
+      }
+      esc_rank += __popc(b0) + __popc(b1);
+      uint32_t io = warp_incl_sum(lr + ml, lane), il = warp_incl_sum(lr, lane);
+      if (act) {
+        m.tdst[t] = out_pos + io - (lr + ml);
+        m.tlit[t] = lit_pos + il - lr;
+        m.tml[t] = ml;
+        uint64_t src = 0;
+        if (t < nm) {
+          const uint8_t* q = m.offb + w * t;
+          src = (uint64_t)q[0] | ((uint64_t)q[1] << 8) | ((uint64_t)q[2] << 16) | ((uint64_t)q[3] << 24);
+          if (w == 5) src |= (uint64_t)q[4] << 32;
+          uint64_t D = bstart + out_pos + io - ml;  // match destination
+          if (ml && src >= D) bad = true;
+        } else if (ml) {
+          bad = true;  // the block's last token carries no match
+        }
+        m.tsrc[t] = src;
+      }
+      out_pos += __shfl_sync(kFull, io, 31);
+      lit_pos += __shfl_sync(kFull, il, 31);
+    }
+    if (lane == 0) {
+      m.tdst[tc] = out_pos;
+      m.tlit[tc] = lit_pos;
+    }
+    bad |= out_pos > blen || lit_pos > nsym[ACE_S_LIT];
+    if (__any_sync(kFull, bad)) fail(a, ok, ACE_E_CORRUPT, b, 33, lane);
+    if (!ok) break;
+    __syncwarp();
+
+    // literal layer: literal i lands at its token's run start plus its offset in the run
+    uint32_t tp = 0;
+    if (!rans_decode(st[ACE_S_LIT], m.lut[ACE_S_LIT], lit_pos, lane, [&](uint32_t i, uint32_t s) {
+          while (m.tlit[tp + 1] <= i) tp++;
+          obase[m.tdst[tp] + (i - m.tlit[tp])] = (uint8_t)s;
+        }))
+      fail(a, ok, ACE_E_CORRUPT, b, 34, lane);
+    if (!ok) break;
+    __syncwarp();
+
+    // match layer: wait for source blocks, then resolve in dependency waves
+    bool timeout = false;
+    for (uint32_t t = lane; t < nm; t += 32) {
+      uint32_t ml = m.tml[t];
+      if (!ml) continue;
+      uint64_t S = m.tsrc[t];
+      uint64_t D = bstart + m.tdst[t + 1] - ml;
+      uint64_t rend = S + min((uint64_t)ml, D - S);
+      uint64_t k0 = S >> a.log2B, k1 = (rend - 1) >> a.log2B;
+      for (uint64_t k = k0; k <= k1 && k < b; k++)
+        if (!wait_flag(a.ready + k, epoch, a.timeout_ns)) {
+          timeout = true;
+          break;
+        }
+    }
+    if (__any_sync(kFull, timeout)) fail(a, ok, ACE_E_TIMEOUT, b, 35, lane);
+    if (!ok) break;
+    // each lane owns matches lane, lane+32, ...; pending bits track them
+    uint32_t pend = 0;
+    for (uint32_t j = 0, t = lane; t < nm; j++, t += 32)
+      if (m.tml[t]) pend |= 1u << j;
+    while (__any_sync(kFull, pend != 0)) {
+      // W: destination of the first pending match; anything whose read range
+      // ends at or before W reads only finished bytes
+      uint64_t myW = ~0ull;
+      for (uint32_t j = 0; j < 32; j++)
+        if ((pend >> j) & 1) {
+          uint32_t t = lane + 32 * j;
+          myW = bstart + m.tdst[t + 1] - m.tml[t];
+          break;
+        }
+      uint64_t W = warp_min64(myW);
+      uint32_t go = 0;
+      for (uint32_t j = 0; j < 32; j++)
+        if ((pend >> j) & 1) {
+          uint32_t t = lane + 32 * j;
+          uint32_t ml = m.tml[t];
+          uint64_t S = m.tsrc[t], D = bstart + m.tdst[t + 1] - ml;
+          uint64_t rend = S + min((uint64_t)ml, D - S);
+          if (rend <= W) go |= 1u << j;
+        }
+      // short matches: the owning lane copies; long ones: the whole warp
+      for (uint32_t j = 0; j < 32; j++)
+        if ((go >> j) & 1) {
+          uint32_t t = lane + 32 * j;
+          uint32_t ml = m.tml[t];
+          if (ml <= 64) {
+            uint32_t dl = m.tdst[t + 1] - ml;
+            copy_match_lane<SEEK>(a, obase + dl, bstart + dl, m.tsrc[t], ml);
+            go &= ~(1u << j);
+            pend &= ~(1u << j);
+          }
+        }
+      uint32_t any_long;
+      while ((any_long = __ballot_sync(kFull, go != 0)) != 0) {
+        uint32_t src_lane = __ffs(any_long) - 1;
+        uint32_t j = __ffs(__shfl_sync(kFull, go, src_lane)) - 1;
+        uint32_t t = src_lane + 32 * j;
+        uint32_t ml = m.tml[t];
+        uint32_t dl = m.tdst[t + 1] - ml;
+        copy_match_warp<SEEK>(a, obase + dl, bstart + dl, m.tsrc[t], ml, lane);
+        if (lane == src_lane) {
+          go &= ~(1u << j);
+          pend &= ~(1u << j);
+        }
+      }
+      __syncwarp();
+    }
+  }
+  if (ok) {
+    bool fin = out_pos == blen && lit_pos == nsym[ACE_S_LIT] && esc_rank == nesc;
+    fin = fin && rans_finished(st[0]) && rans_finished(st[1]) && rans_finished(st[2]);
+    if (!__all_sync(kFull, fin)) fail(a, ok, ACE_E_CORRUPT, b, 40, lane);
+  }
+  return ok;
+}
+
+template <bool SEEK>
+__global__ void __launch_bounds__(512) decode_kernel(DecodeArgs a) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  WarpMem m = carve(smem + (size_t)wid * a.warp_smem, a.chunk);
+  const uint32_t epoch = *(volatile uint32_t*)&a.sh->epoch;
+  const uint32_t n_items = SEEK ? *(volatile uint32_t*)&a.sh->n_work : a.n_items;
+  while (true) {
+    uint32_t it = 0;
+    if (lane == 0) it = atomicAdd(&a.sh->ticket, 1u);
+    it = __shfl_sync(kFull, it, 0);
+    if (it >= n_items) break;
+    uint32_t b = __ldg(a.items + it);
+    bool ok = decode_block<SEEK>(a, m, b, lane, epoch);
+    if (SEEK && ok) {
+      // copy the part of this block inside [coord, coord + len) to the caller
+      uint64_t bs = (uint64_t)b << a.log2B, be = min(bs + ((uint64_t)1 << a.log2B), a.total);
+      uint64_t lo = max(bs, a.coord), hi = min(be, a.coord + a.len);
+      const uint8_t* src = a.out + ((uint64_t)a.slot_of[b] << a.log2B) - bs;
+      for (uint64_t p = lo + lane; p < hi; p += 32) a.slice[p - a.coord] = __ldcg(src + p);
+    }
+    // publish: all lanes' writes are visible device-wide before the flag
+    __threadfence();
+    __syncwarp();
+    if (lane == 0) st_release(a.ready + b, epoch);
+  }
+}
+
+// ---------------------------------------------------------- seek closure
+
+struct ClosureArgs {
+  const uint32_t* dep_ptr;
+  const uint32_t* dep_iv;
+  ScratchHdr* sh;
+  uint32_t* marks;   // one bit per block, all clear between calls
+  uint32_t* front0;
+  uint32_t* front1;
+  uint32_t* work;
+  uint32_t* slot_of;
+  uint64_t nb;
+  uint64_t first, last;  // target blocks
+  uint64_t cap;          // slots available
+};
+
+// The blocks a seek must decode: its target blocks and, transitively, every
+// block their matches read (Section 2), listed in ascending block order (a
+// valid decode order: sources always precede).  One CTA.
+__global__ void closure_kernel(ClosureArgs a) {
+  __shared__ uint32_t n_next, s_min;
+  __shared__ uint32_t wsum[32];
+  __shared__ uint32_t carry;
+  const uint32_t tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
+  if (tid == 0) {
+    a.sh->epoch += 1;
+    a.sh->ticket = 0;
+    s_min = (uint32_t)a.first;
+  }
+  uint32_t ntar = (uint32_t)(a.last - a.first + 1);
+  for (uint32_t i = tid; i < ntar; i += blockDim.x) {
+    uint32_t b = (uint32_t)a.first + i;
+    atomicOr(&a.marks[b >> 5], 1u << (b & 31));
+    a.front0[i] = b;
+  }
+  uint32_t n_front = ntar;
+  uint32_t* cur = a.front0;
+  uint32_t* nxt = a.front1;
+  __syncthreads();
+  while (n_front) {
+    if (tid == 0) n_next = 0;
+    __syncthreads();
+    for (uint32_t i = tid; i < n_front; i += blockDim.x) {
+      uint32_t b = cur[i];
+      for (uint32_t e = a.dep_ptr[b]; e < a.dep_ptr[b + 1]; e++)
+        for (uint32_t k = a.dep_iv[2 * e]; k <= a.dep_iv[2 * e + 1]; k++) {
+          uint32_t old = atomicOr(&a.marks[k >> 5], 1u << (k & 31));
+          if (!(old & (1u << (k & 31)))) {
+            nxt[atomicAdd(&n_next, 1u)] = k;
+            atomicMin(&s_min, k);
+          }
+        }
+    }
+    __syncthreads();
+    n_front = n_next;
+    uint32_t* t = cur;
+    cur = nxt;
+    nxt = t;
+    __syncthreads();
+  }
+  // ordered compaction of the marked blocks, clearing the marks behind it
+  if (tid == 0) carry = 0;
+  __syncthreads();
+  uint32_t w0 = s_min >> 5, w1 = (uint32_t)(a.last >> 5);
+  for (uint32_t c0 = w0; c0 <= w1; c0 += blockDim.x) {
+    uint32_t wi = c0 + tid;
+    uint32_t bits = wi <= w1 ? a.marks[wi] : 0u;
+    uint32_t cnt = __popc(bits);
+    uint32_t incl = warp_incl_sum(cnt, lane);
+    if (lane == 31) wsum[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+      uint32_t s = lane < nw ? wsum[lane] : 0;
+      uint32_t si = warp_incl_sum(s, lane);
+      if (lane < nw) wsum[lane] = si - s;
+    }
+    __syncthreads();
+    uint32_t pos = carry + wsum[wid] + incl - cnt;
+    while (bits) {
+      uint32_t bit = __ffs(bits) - 1;
+      bits &= bits - 1;
+      uint32_t b = wi * 32 + bit;
+      a.work[pos] = b;
+      if (pos < a.cap) a.slot_of[b] = pos;
+      pos++;
+    }
+    if (wi <= w1) a.marks[wi] = 0;
+    __syncthreads();
+    if (tid == blockDim.x - 1) carry = pos;
+    __syncthreads();
+  }
+  if (tid == 0) {
+    uint32_t n = carry;
+    if (n > a.cap) {
+      record_error(&a.sh->status, &a.sh->err_block, &a.sh->err_where, ACE_E_NOMEM, n, 50);
+      n = 0;
+    }
+    a.sh->n_work = n;
+  }
+}
+
+// ------------------------------------------------------------ verification
+
+__device__ __forceinline__ uint8_t pattern_byte(uint32_t seed, uint64_t i) {
+  uint64_t z = (i + 1) * 0x9e3779b97f4a7c15ull ^ ((uint64_t)seed << 32 | seed);
+  z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+  z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+  return (uint8_t)(z ^ (z >> 31));
+}
+
+__global__ void fill_pattern_kernel(uint8_t* p, uint64_t n, uint32_t seed) {
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
+    p[i] = pattern_byte(seed, i);
+}
+
+__global__ void count_pattern_mismatch_kernel(const uint8_t* p, uint64_t n, uint32_t seed, uint64_t* bad) {
+  uint64_t c = 0;
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
+    c += p[i] != pattern_byte(seed, i);
+  if (c) atomicAdd((unsigned long long*)bad, (unsigned long long)c);
+}
+
+// New call on a scratch buffer: next epoch, ticket back to zero.
+__global__ void begin_call_kernel(ScratchHdr* sh) {
+  sh->epoch += 1;
+  sh->ticket = 0;
+}
+
+// FNV-1a 64 (Fowler/Noll/Vo): sequential by definition, one thread.
+__global__ void fnv_kernel(const uint8_t* p, uint64_t n, uint64_t* out) {
+  uint64_t h = 0xcbf29ce484222325ull;
+  for (uint64_t i = 0; i < n; i++) {
+    h ^= p[i];
+    h *= 0x100000001b3ull;
+  }
+  *out = h;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- host side
+
+struct ace_index {
+  const uint8_t* d_arc;
+  uint64_t arc_bytes;
+  ace_file_header h;
+  uint8_t* d_mem;
+  uint64_t mem_bytes;
+  IndexHdr* d_ih;
+  uint32_t* d_level;
+  uint32_t* d_order;
+  const uint32_t* d_dep_ptr;
+  const uint32_t* d_dep_iv;
+  uint64_t n_iv;
+  uint32_t n_levels;
+  int device;
+  int num_sms;
+  ace_tune tune;
+};
+
+namespace {
+
+struct IndexLayout {
+  uint64_t level, order, lv_count, lv_cursor, total;
+};
+
+IndexLayout index_layout(uint64_t nb) {
+  IndexLayout L;
+  uint64_t o = sizeof(IndexHdr);
+  L.level = o;
+  o = align256(o + 4 * nb);
+  L.order = o;
+  o = align256(o + 4 * nb);
+  L.lv_count = o;
+  o = align256(o + 4 * (nb + 1));
+  L.lv_cursor = o;
+  o = align256(o + 4 * (nb + 1));
+  L.total = o;
+  return L;
+}
+
+struct ScratchLayout {
+  uint64_t ready, slot_of, work, marks, front0, front1, slots, total;
+};
+
+ScratchLayout scratch_layout(uint64_t nb, uint32_t log2B, uint64_t max_seek) {
+  ScratchLayout L;
+  uint64_t o = sizeof(ScratchHdr);
+  L.ready = o;
+  o = align256(o + 4 * nb);
+  L.slot_of = L.work = L.marks = L.front0 = L.front1 = L.slots = o;
+  if (max_seek) {
+    L.slot_of = o;
+    o = align256(o + 4 * nb);
+    L.work = o;
+    o = align256(o + 4 * nb);
+    L.marks = o;
+    o = align256(o + 4 * ((nb + 31) / 32));
+    L.front0 = o;
+    o = align256(o + 4 * nb);
+    L.front1 = o;
+    o = align256(o + 4 * nb);
+    L.slots = o;
+    o = align256(o + (max_seek << log2B));
+  }
+  L.total = o;
+  return L;
+}
+
+ace_status parse_header(const void* h_header, uint64_t header_bytes, ace_file_header* h) {
+  if (!h_header || header_bytes < sizeof(ace_file_header)) return ACE_E_INVAL;
+  std::memcpy(h, h_header, sizeof *h);
+  if (h->magic != ACE_MAGIC || h->version != ACE_VERSION || h->n_streams != ACE_NSTREAMS ||
+      h->n_states != ACE_NSTATES || h->scale_bits != ACE_SCALE_BITS)
+    return ACE_E_CORRUPT;
+  if (h->off_width != 4 && h->off_width != 5) return ACE_E_CORRUPT;
+  if (h->log2_block < ACE_MIN_LOG2_BLOCK || h->log2_block > ACE_MAX_LOG2_BLOCK) return ACE_E_CORRUPT;
+  uint64_t B = 1ull << h->log2_block;
+  if (h->n_blocks != (h->total_size + B - 1) / B || h->n_blocks > 0xFFFFFFF0ull) return ACE_E_CORRUPT;
+  if (h->dir_off < sizeof(ace_file_header) || h->dir_off + h->n_blocks * sizeof(ace_block_dir) > h->deps_off)
+    return ACE_E_CORRUPT;
+  if (h->deps_off + 4 * (h->n_blocks + 1) > h->payload_off || h->payload_off > h->archive_bytes)
+    return ACE_E_CORRUPT;
+  if ((h->dir_off & 7) || (h->deps_off & 3) || (h->payload_off & 15) || (h->archive_bytes & 15))
+    return ACE_E_CORRUPT;
+  return ACE_OK;
+}
+
+inline bool aligned(const void* p, uintptr_t a) { return (reinterpret_cast<uintptr_t>(p) & (a - 1)) == 0; }
+
+#define CUDA_TRY(x)                         \
+  do {                                      \
+    if ((x) != cudaSuccess) return ACE_E_CUDA; \
+  } while (0)
+
+struct Launch {
+  uint32_t warps, ctas_per_sm, chunk, smem_per_warp, grid;
+  uint64_t timeout;
+};
+
+template <bool SEEK>
+ace_status plan_launch(const ace_index* idx, const ace_tune* tune, uint64_t max_items, Launch* L) {
+  ace_tune t = tune ? *tune : idx->tune;
+  L->warps = t.warps_per_cta ? t.warps_per_cta : 4;
+  L->chunk = t.chunk_tokens ? t.chunk_tokens : 128;
+  if (L->warps > 16 || (L->chunk & 31) || L->chunk > 256) return ACE_E_INVAL;
+  L->timeout = t.wait_timeout_ns ? t.wait_timeout_ns : kDefaultTimeoutNs;
+  L->smem_per_warp = warp_smem_bytes(L->chunk, 520);
+  size_t smem = (size_t)L->warps * L->smem_per_warp;
+  CUDA_TRY(cudaFuncSetAttribute(decode_kernel<SEEK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int per_sm = 0;
+  CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, decode_kernel<SEEK>, 32 * L->warps, smem));
+  if (per_sm < 1) return ACE_E_INVAL;
+  if (t.ctas_per_sm && (int)t.ctas_per_sm < per_sm) per_sm = (int)t.ctas_per_sm;
+  L->ctas_per_sm = (uint32_t)per_sm;
+  uint64_t grid = (uint64_t)idx->num_sms * per_sm;
+  uint64_t need = (max_items + L->warps - 1) / L->warps;
+  L->grid = (uint32_t)std::max<uint64_t>(1, std::min(grid, need));
+  return ACE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* ace_status_str(ace_status s) {
+  switch (s) {
+    case ACE_OK: return "ACE_OK";
+    case ACE_E_INVAL: return "ACE_E_INVAL";
+    case ACE_E_CORRUPT: return "ACE_E_CORRUPT";
+    case ACE_E_RANGE: return "ACE_E_RANGE";
+    case ACE_E_NOMEM: return "ACE_E_NOMEM";
+    case ACE_E_TIMEOUT: return "ACE_E_TIMEOUT";
+    case ACE_E_CUDA: return "ACE_E_CUDA";
+    default: return "ACE_E_UNKNOWN";
+  }
+}
+
+ace_status ace_index_size(const void* h_header, uint64_t header_bytes, uint64_t* index_bytes) {
+  if (!index_bytes) return ACE_E_INVAL;
+  ace_file_header h;
+  ace_status rc = parse_header(h_header, header_bytes, &h);
+  if (rc) return rc;
+  *index_bytes = index_layout(h.n_blocks).total;
+  return ACE_OK;
+}
+
+ace_status ace_index_build(const void* d_archive, uint64_t archive_bytes, const void* h_header,
+                           uint64_t header_bytes, void* d_index_mem, uint64_t index_bytes, cudaStream_t s,
+                           ace_index** out) {
+  if (!out || !d_index_mem || (!d_archive && archive_bytes)) return ACE_E_INVAL;
+  if (!aligned(d_archive, 16) || !aligned(d_index_mem, 256)) return ACE_E_INVAL;
+  ace_file_header h;
+  ace_status rc = parse_header(h_header, header_bytes, &h);
+  if (rc) return rc;
+  if (h.archive_bytes > archive_bytes) return ACE_E_CORRUPT;
+  IndexLayout L = index_layout(h.n_blocks);
+  if (index_bytes < L.total) return ACE_E_NOMEM;
+  ace_index* idx = new (std::nothrow) ace_index();
+  if (!idx) return ACE_E_NOMEM;
+  idx->d_arc = static_cast<const uint8_t*>(d_archive);
+  idx->arc_bytes = archive_bytes;
+  idx->h = h;
+  idx->d_mem = static_cast<uint8_t*>(d_index_mem);
+  idx->mem_bytes = index_bytes;
+  idx->d_ih = reinterpret_cast<IndexHdr*>(idx->d_mem);
+  idx->d_level = reinterpret_cast<uint32_t*>(idx->d_mem + L.level);
+  idx->d_order = reinterpret_cast<uint32_t*>(idx->d_mem + L.order);
+  idx->d_dep_ptr = reinterpret_cast<const uint32_t*>(idx->d_arc + h.deps_off);
+  idx->tune = ace_tune{};
+  auto bail = [&](ace_status r) {
+    delete idx;
+    return r;
+  };
+  if (cudaGetDevice(&idx->device) != cudaSuccess) return bail(ACE_E_CUDA);
+  if (cudaDeviceGetAttribute(&idx->num_sms, cudaDevAttrMultiProcessorCount, idx->device) != cudaSuccess)
+    return bail(ACE_E_CUDA);
+  uint32_t niv = 0;
+  if (cudaMemcpyAsync(&niv, idx->d_arc + h.deps_off + 4 * h.n_blocks, 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return bail(ACE_E_CUDA);
+  idx->n_iv = niv;
+  if (h.deps_off + 4 * (h.n_blocks + 1) + 8ull * niv > h.payload_off) return bail(ACE_E_CORRUPT);
+  idx->d_dep_iv = reinterpret_cast<const uint32_t*>(idx->d_arc + h.deps_off + 4 * (h.n_blocks + 1));
+  if (cudaMemsetAsync(idx->d_mem, 0, L.total, s) != cudaSuccess) return bail(ACE_E_CUDA);
+  IndexArgs a;
+  a.arc = idx->d_arc;
+  a.dir = reinterpret_cast<const ace_block_dir*>(idx->d_arc + h.dir_off);
+  a.dep_ptr = idx->d_dep_ptr;
+  a.dep_iv = idx->d_dep_iv;
+  a.ih = idx->d_ih;
+  a.level = idx->d_level;
+  a.order = idx->d_order;
+  a.lv_count = reinterpret_cast<uint32_t*>(idx->d_mem + L.lv_count);
+  a.lv_cursor = reinterpret_cast<uint32_t*>(idx->d_mem + L.lv_cursor);
+  a.nb = h.n_blocks;
+  a.total = h.total_size;
+  a.payload_off = h.payload_off;
+  a.arc_bytes = h.archive_bytes;
+  a.deps_off = h.deps_off;
+  a.log2B = h.log2_block;
+  a.w = h.off_width;
+  if (h.n_blocks) {
+    uint32_t g = (uint32_t)((h.n_blocks + 255) / 256);
+    validate_kernel<<<g, 256, 0, s>>>(a);
+    IndexHdr ih;
+    if (cudaMemcpyAsync(&ih, idx->d_ih, sizeof ih, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+      return bail(ACE_E_CUDA);
+    if (ih.status) return bail((ace_status)ih.status);
+    levels_kernel<<<1, 1024, 0, s>>>(a);
+    level_hist_kernel<<<g, 256, 0, s>>>(a);
+    level_scan_kernel<<<1, 1024, 0, s>>>(a);
+    level_scatter_kernel<<<g, 256, 0, s>>>(a);
+    if (cudaMemcpyAsync(&ih, idx->d_ih, sizeof ih, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+      return bail(ACE_E_CUDA);
+    if (ih.status) return bail((ace_status)ih.status);
+    idx->n_levels = ih.n_levels;
+  }
+  *out = idx;
+  return ACE_OK;
+}
+
+ace_status ace_index_info(const ace_index* idx, ace_info* info) {
+  if (!idx || !info) return ACE_E_INVAL;
+  info->total_size = idx->h.total_size;
+  info->n_blocks = idx->h.n_blocks;
+  info->archive_bytes = idx->h.archive_bytes;
+  info->n_dep_intervals = idx->n_iv;
+  info->block_size = 1u << idx->h.log2_block;
+  info->off_width = idx->h.off_width;
+  info->n_levels = idx->n_levels;
+  info->reserved = 0;
+  return ACE_OK;
+}
+
+ace_status ace_index_set_tune(ace_index* idx, const ace_tune* tune) {
+  if (!idx) return ACE_E_INVAL;
+  if (tune && (tune->warps_per_cta > 16 || (tune->chunk_tokens & 31) || tune->chunk_tokens > 256))
+    return ACE_E_INVAL;
+  idx->tune = tune ? *tune : ace_tune{};
+  return ACE_OK;
+}
+
+ace_status ace_index_free(ace_index* idx) {
+  delete idx;
+  return ACE_OK;
+}
+
+ace_status ace_scratch_size(const ace_index* idx, uint64_t max_seek_blocks, uint64_t* bytes) {
+  if (!idx || !bytes) return ACE_E_INVAL;
+  *bytes = scratch_layout(idx->h.n_blocks, idx->h.log2_block, max_seek_blocks).total;
+  return ACE_OK;
+}
+
+ace_status ace_scratch_init(const ace_index* idx, void* d_scratch, uint64_t scratch_bytes, cudaStream_t s) {
+  if (!idx || !d_scratch || !aligned(d_scratch, 256)) return ACE_E_INVAL;
+  uint64_t need = scratch_layout(idx->h.n_blocks, idx->h.log2_block, 0).total;
+  if (scratch_bytes < need) return ACE_E_NOMEM;
+  // header, ready flags, and (when present) slot map, work list and marks
+  uint64_t clear = std::min<uint64_t>(scratch_bytes, scratch_layout(idx->h.n_blocks, idx->h.log2_block, 1).slots);
+  CUDA_TRY(cudaMemsetAsync(d_scratch, 0, clear, s));
+  return ACE_OK;
+}
+
+ace_status ace_decode_all(const ace_index* idx, void* d_out, uint64_t out_bytes, void* d_scratch,
+                          uint64_t scratch_bytes, const ace_tune* tune, cudaStream_t s) {
+  if (!idx || !d_scratch || (!d_out && idx->h.total_size)) return ACE_E_INVAL;
+  if (!aligned(d_scratch, 256)) return ACE_E_INVAL;
+  if (out_bytes < idx->h.total_size) return ACE_E_NOMEM;
+  ScratchLayout SL = scratch_layout(idx->h.n_blocks, idx->h.log2_block, 0);
+  if (scratch_bytes < SL.total) return ACE_E_NOMEM;
+  if (!idx->h.n_blocks) return ACE_OK;
+  Launch L;
+  ace_status rc = plan_launch<false>(idx, tune, idx->h.n_blocks, &L);
+  if (rc) return rc;
+  ScratchHdr* sh = static_cast<ScratchHdr*>(d_scratch);
+  DecodeArgs a{};
+  a.arc = idx->d_arc;
+  a.dir = reinterpret_cast<const ace_block_dir*>(idx->d_arc + idx->h.dir_off);
+  a.payload_off = idx->h.payload_off;
+  a.total = idx->h.total_size;
+  a.nb = idx->h.n_blocks;
+  a.log2B = idx->h.log2_block;
+  a.w = idx->h.off_width;
+  a.chunk = L.chunk;
+  a.esc_cap = esc_cap(a.log2B);
+  a.warp_smem = L.smem_per_warp;
+  a.n_items = (uint32_t)idx->h.n_blocks;
+  a.items = idx->d_order;
+  a.out = static_cast<uint8_t*>(d_out);
+  a.sh = sh;
+  a.ready = reinterpret_cast<uint32_t*>(static_cast<uint8_t*>(d_scratch) + SL.ready);
+  a.timeout_ns = L.timeout;
+  begin_call_kernel<<<1, 1, 0, s>>>(sh);
+  decode_kernel<false><<<L.grid, 32 * L.warps, (size_t)L.warps * L.smem_per_warp, s>>>(a);
+  CUDA_TRY(cudaGetLastError());
+  return ACE_OK;
+}
+
+ace_status ace_seek(const ace_index* idx, uint64_t coord, uint64_t len, void* d_out, uint64_t out_bytes,
+                    void* d_scratch, uint64_t scratch_bytes, cudaStream_t s) {
+  if (!idx || !d_out || !d_scratch || !aligned(d_scratch, 256)) return ACE_E_INVAL;
+  if (len == 0 || coord >= idx->h.total_size || len > idx->h.total_size - coord) return ACE_E_RANGE;
+  if (out_bytes < len) return ACE_E_NOMEM;
+  uint64_t nb = idx->h.n_blocks;
+  uint32_t log2B = idx->h.log2_block;
+  ScratchLayout S1 = scratch_layout(nb, log2B, 1);
+  if (scratch_bytes < S1.total) return ACE_E_NOMEM;
+  uint64_t cap = (scratch_bytes - S1.slots) >> log2B;
+  uint64_t first = coord >> log2B, last = (coord + len - 1) >> log2B;
+  if (last - first + 1 > cap) return ACE_E_NOMEM;
+  uint8_t* base = static_cast<uint8_t*>(d_scratch);
+  ScratchHdr* sh = reinterpret_cast<ScratchHdr*>(base);
+  ClosureArgs c;
+  c.dep_ptr = idx->d_dep_ptr;
+  c.dep_iv = idx->d_dep_iv;
+  c.sh = sh;
+  c.marks = reinterpret_cast<uint32_t*>(base + S1.marks);
+  c.front0 = reinterpret_cast<uint32_t*>(base + S1.front0);
+  c.front1 = reinterpret_cast<uint32_t*>(base + S1.front1);
+  c.work = reinterpret_cast<uint32_t*>(base + S1.work);
+  c.slot_of = reinterpret_cast<uint32_t*>(base + S1.slot_of);
+  c.nb = nb;
+  c.first = first;
+  c.last = last;
+  c.cap = cap;
+  closure_kernel<<<1, 1024, 0, s>>>(c);
+  Launch L;
+  ace_status rc = plan_launch<true>(idx, nullptr, cap, &L);
+  if (rc) return rc;
+  DecodeArgs a{};
+  a.arc = idx->d_arc;
+  a.dir = reinterpret_cast<const ace_block_dir*>(idx->d_arc + idx->h.dir_off);
+  a.payload_off = idx->h.payload_off;
+  a.total = idx->h.total_size;
+  a.nb = nb;
+  a.log2B = log2B;
+  a.w = idx->h.off_width;
+  a.chunk = L.chunk;
+  a.esc_cap = esc_cap(log2B);
+  a.warp_smem = L.smem_per_warp;
+  a.items = c.work;
+  a.out = base + S1.slots;
+  a.sh = sh;
+  a.ready = reinterpret_cast<uint32_t*>(base + S1.ready);
+  a.slot_of = c.slot_of;
+  a.slice = static_cast<uint8_t*>(d_out);
+  a.coord = coord;
+  a.len = len;
+  a.timeout_ns = L.timeout;
+  decode_kernel<true><<<L.grid, 32 * L.warps, (size_t)L.warps * L.smem_per_warp, s>>>(a);
+  CUDA_TRY(cudaGetLastError());
+  return ACE_OK;
+}
+
+ace_status ace_sync(const ace_index* idx, void* d_scratch, cudaStream_t s) {
+  if (!idx || !d_scratch) return ACE_E_INVAL;
+  CUDA_TRY(cudaStreamSynchronize(s));
+  ScratchHdr h;
+  CUDA_TRY(cudaMemcpyAsync(&h, d_scratch, sizeof h, cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  if (h.status) {
+    CUDA_TRY(cudaMemsetAsync(d_scratch, 0, 3 * sizeof(uint32_t), s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+  }
+  return (ace_status)h.status;
+}
+
+ace_status ace_fnv1a64(const void* d_p, uint64_t n, uint64_t* d_result, cudaStream_t s) {
+  if ((!d_p && n) || !d_result) return ACE_E_INVAL;
+  fnv_kernel<<<1, 1, 0, s>>>(static_cast<const uint8_t*>(d_p), n, d_result);
+  CUDA_TRY(cudaGetLastError());
+  return ACE_OK;
+}
+
+ace_status ace_verify(const ace_index* idx, uint64_t coord, uint64_t len, void* d_buf, uint64_t guard_bytes,
+                      uint64_t expected, uint32_t canary_seed, void* d_scratch, uint64_t scratch_bytes,
+                      ace_verify_report* rep, cudaStream_t s) {
+  if (!idx || !d_buf || !d_scratch || !rep) return ACE_E_INVAL;
+  if (len == 0 || coord >= idx->h.total_size || len > idx->h.total_size - coord) return ACE_E_RANGE;
+  std::memset(rep, 0, sizeof *rep);
+  uint8_t* buf = static_cast<uint8_t*>(d_buf);
+  uint8_t* slice = buf + guard_bytes;
+  ScratchHdr* sh = static_cast<ScratchHdr*>(d_scratch);
+  uint32_t poison_seed = canary_seed ^ 0x5bd1e995u;
+  auto guards_bad = [&](uint64_t* out_bad) -> ace_status {
+    CUDA_TRY(cudaMemsetAsync(&sh->guard_bad, 0, 8, s));
+    if (guard_bytes) {
+      count_pattern_mismatch_kernel<<<64, 256, 0, s>>>(buf, guard_bytes, canary_seed, &sh->guard_bad);
+      count_pattern_mismatch_kernel<<<64, 256, 0, s>>>(slice + len, guard_bytes, canary_seed ^ 0x9e3779b9u,
+                                                       &sh->guard_bad);
+    }
+    CUDA_TRY(cudaMemcpyAsync(out_bad, &sh->guard_bad, 8, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    return ACE_OK;
+  };
+  // set up: canaries around, poison inside
+  if (guard_bytes) {
+    fill_pattern_kernel<<<64, 256, 0, s>>>(buf, guard_bytes, canary_seed);
+    fill_pattern_kernel<<<64, 256, 0, s>>>(slice + len, guard_bytes, canary_seed ^ 0x9e3779b9u);
+  }
+  fill_pattern_kernel<<<256, 256, 0, s>>>(slice, len, poison_seed);
+  CUDA_TRY(cudaGetLastError());
+  // phase 1: the slice holds none of the original
+  fnv_kernel<<<1, 1, 0, s>>>(slice, len, &sh->fnv);
+  CUDA_TRY(cudaMemcpyAsync(&rep->fnv_before, &sh->fnv, 8, cudaMemcpyDeviceToHost, s));
+  ace_status rc = guards_bad(&rep->guard_bad_before);
+  if (rc) return rc;
+  rep->phase1_ok = rep->fnv_before != expected;
+  // the seek through both layers
+  rc = ace_seek(idx, coord, len, slice, len, d_scratch, scratch_bytes, s);
+  if (rc) return rc;
+  rep->seek_status = ace_sync(idx, d_scratch, s);
+  // phase 2: the slice equals the original; phase 3: the guards are untouched
+  fnv_kernel<<<1, 1, 0, s>>>(slice, len, &sh->fnv);
+  CUDA_TRY(cudaMemcpyAsync(&rep->fnv_after, &sh->fnv, 8, cudaMemcpyDeviceToHost, s));
+  rc = guards_bad(&rep->guard_bad_after);
+  if (rc) return rc;
+  rep->phase2_ok = rep->seek_status == ACE_OK && rep->fnv_after == expected;
+  rep->phase3_ok = rep->guard_bad_before == 0 && rep->guard_bad_after == 0;
+  return ACE_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,56 @@
+"""The library's host encoder, checked with the oracle decoder: every
+archive it writes decodes to the original, every match is valid, the
+dependency table is exact, and dependency levels stay within the cap."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from paper_2606_24531_gb300 import ace
+import __graft_entry__
+
+from test_oracle_lz import _check_parse, _deps_from_tokens
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    __graft_entry__.build()
+
+
+@pytest.mark.parametrize("profile,mm", [("mixed", 4), ("fastq", 16), ("genome", 20), ("text", 4)])
+@pytest.mark.parametrize("log2b", [8, 12, 14, 16])
+def test_round_trip_through_oracle(profile, mm, log2b):
+    data = synth.generate(profile, 300_000, 21)
+    arc = ace.ace_encode(data, log2b, mm)
+    assert np.array_equal(oracle.decode(arc), data)
+    lv = oracle.levels(arc)
+    assert lv.max() <= 3
+
+
+def test_edge_sizes():
+    rng = np.random.default_rng(0)
+    B = 256
+    for n in [0, 1, 2, 3, 4, 5, B - 1, B, B + 1, 3 * B + 7, 64 * B, 64 * B + 1]:
+        for alpha in (1, 3, 256):
+            data = rng.integers(0, alpha, n).astype(np.uint8)
+            arc = ace.ace_encode(data, 8, 4)
+            assert np.array_equal(oracle.decode(arc), data)
+
+
+def test_matches_valid_and_dependencies_exact():
+    data = synth.generate("mixed", 200_000, 3)
+    arc = ace.ace_encode(data, 12, 4)
+    _check_parse(data, arc, 4096, 4, exhaustive=False)
+    want = _deps_from_tokens(arc)
+    for b, ivs in enumerate(oracle.deps(arc)):
+        s = set()
+        for f, l in ivs:
+            s.update(range(f, l + 1))
+        assert s == want[b]
+
+
+def test_deterministic_across_thread_counts():
+    data = synth.generate("fastq", 1 << 21, 8)
+    a1 = ace.ace_encode(data, 14, 16, threads=1)
+    a8 = ace.ace_encode(data, 14, 16, threads=8)
+    assert np.array_equal(a1, a8)

@@ -1,0 +1,269 @@
+"""GPU parity: the sm_103a decoder, called through the C ABI, against the
+oracle and the original bytes.  Decoded output has exactly one correct
+value, so every comparison is bit-exact (tolerance 0 bytes)."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+import __graft_entry__
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_2606_24531_gb300 import ace  # noqa: E402
+from paper_2606_24531_gb300.archive import DeviceArchive  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    __graft_entry__.build()
+    assert torch.cuda.is_available()
+    torch.cuda.set_device(0)
+
+
+def gpu_decode(arc, tune=None):
+    da = DeviceArchive(arc)
+    out = da.decode_all(tune=tune)
+    st = da.sync()
+    res = out.cpu().numpy()[: da.total]
+    da.close()
+    return st, res
+
+
+MIN_MATCH = {"mixed": 4, "text": 4, "fastq": 16, "genome": 20}
+
+
+@pytest.mark.parametrize("profile", ["mixed", "fastq", "genome", "text"])
+@pytest.mark.parametrize("log2b", [8, 12, 14, 16])
+def test_decode_all_library_archives(profile, log2b):
+    data = synth.generate(profile, 3_000_000 + 12345, 100 + log2b)
+    arc = ace.ace_encode(data, log2b, MIN_MATCH[profile])
+    st, out = gpu_decode(arc)
+    assert st == ace.ACE_OK, ace.ace_status_str(st)
+    assert np.array_equal(out, data)
+
+
+@pytest.mark.parametrize("profile", ["mixed", "fastq", "genome", "text"])
+@pytest.mark.parametrize("log2b", [8, 14])
+def test_decode_all_oracle_archives(profile, log2b):
+    """Archives written by the oracle (most-recent-first sources, deep
+    dependency chains) decode to the oracle's own output."""
+    data = synth.generate(profile, 400_000, 7)
+    arc = oracle.encode(data, log2b, 4, 16)
+    ref = oracle.decode(arc)
+    assert np.array_equal(ref, data)
+    st, out = gpu_decode(arc)
+    assert st == ace.ACE_OK, ace.ace_status_str(st)
+    assert np.array_equal(out, ref)
+
+
+def test_plain_small_config_decode_seek_and_three_phase():
+    """1 MiB mixed data (seed 0), 16 KiB blocks, min match 4: full decode,
+    seek of block 37, and the three-phase check (Section 5)."""
+    data = synth.generate("mixed", 1 << 20, 0)
+    B = 1 << 14
+    for arc in (ace.ace_encode(data, 14, 4), oracle.encode(data, 14, 4, 64)):
+        da = DeviceArchive(arc, max_seek_blocks=64)
+        out = da.decode_all()
+        assert da.sync() == ace.ACE_OK
+        assert np.array_equal(out.cpu().numpy(), data)
+        s = da.seek(37 * B, B)
+        assert da.sync() == ace.ACE_OK
+        assert np.array_equal(s.cpu().numpy(), oracle.seek(arc, 37 * B, B))
+        want = oracle.fnv1a64(data[37 * B: 38 * B])
+        rep, buf = da.verify(37 * B, B, want)
+        assert rep["phase1_ok"] == 1 and rep["phase2_ok"] == 1 and rep["phase3_ok"] == 1, rep
+        assert rep["fnv_after"] == want and rep["fnv_before"] != want
+        assert np.array_equal(buf[B:2 * B].cpu().numpy(), data[37 * B: 38 * B])
+        da.close()
+
+
+def test_edge_sizes_and_empty():
+    rng = np.random.default_rng(5)
+    B = 256
+    for n in [1, 2, 7, B - 1, B, B + 1, 3 * B + 7, 200 * B + 3]:
+        for alpha in (1, 2, 256):
+            data = rng.integers(0, alpha, n).astype(np.uint8)
+            for arc in (ace.ace_encode(data, 8, 4), oracle.encode(data, 8, 4, 16)):
+                st, out = gpu_decode(arc)
+                assert st == ace.ACE_OK
+                assert np.array_equal(out, data), (n, alpha)
+    arc = ace.ace_encode(np.zeros(0, np.uint8), 12, 4)
+    da = DeviceArchive(arc)
+    assert da.total == 0
+    da.decode_all()
+    assert da.sync() == ace.ACE_OK
+    da.close()
+
+
+def test_tunings_agree():
+    data = synth.generate("text", 2_000_000, 9)
+    arc = ace.ace_encode(data, 14, 4)
+    for warps in (1, 2, 4, 8, 16):
+        for chunk in (32, 64, 128, 256):
+            st, out = gpu_decode(arc, ace.make_tune(warps, 0, chunk))
+            assert st == ace.ACE_OK
+            assert np.array_equal(out, data), (warps, chunk)
+
+
+def test_overlap_rule():
+    """Matches whose source overlaps the destination (distance d < length)
+    reproduce the sequential bytewise copy, for d = 1..64."""
+    rng = np.random.default_rng(2)
+    parts = []
+    for d in range(1, 65):
+        for ln in (4, 5, 17, 31, 32, 33, 63, 64, 65, 100, 200, 300):
+            parts.append(rng.integers(0, 256, 24).astype(np.uint8))  # separator
+            unit = rng.integers(0, 256, d).astype(np.uint8)
+            parts.append(np.resize(unit, d + ln))
+    data = np.concatenate(parts)
+    for arc in (ace.ace_encode(data, 12, 4), oracle.encode(data, 12, 4, 16)):
+        overl = 0
+        for b in range(oracle.info(arc)["n_blocks"]):
+            lr, ml, src = oracle.block_tokens(arc, b)
+            dst = b * 4096
+            for t in range(len(lr)):
+                dst += int(lr[t])
+                if ml[t] and dst - int(src[t]) < ml[t]:
+                    overl += 1
+                dst += int(ml[t])
+        assert overl > 500
+        st, out = gpu_decode(arc)
+        assert st == ace.ACE_OK
+        assert np.array_equal(out, data)
+
+
+def test_seek_random_ranges():
+    data = synth.generate("mixed", 3_000_000, 11)
+    arc = ace.ace_encode(data, 12, 4)
+    da = DeviceArchive(arc, max_seek_blocks=1024)
+    rng = np.random.default_rng(3)
+    n = data.size
+    cases = [(0, 1), (n - 1, 1), (0, n), (4096 * 37, 4096), (4095, 2), (n - 5000, 5000)]
+    cases += [(int(c), int(rng.integers(1, 300_000))) for c in rng.integers(0, n - 300_000, 40)]
+    for coord, length in cases:
+        out = da.seek(coord, length)
+        st = da.sync()
+        assert st == ace.ACE_OK, (coord, length, ace.ace_status_str(st))
+        assert np.array_equal(out.cpu().numpy(), data[coord:coord + length]), (coord, length)
+    # the seek writes exactly len bytes of the caller's buffer
+    buf = torch.full((10000,), 7, dtype=torch.uint8, device="cuda")
+    ace.ace_seek(da.idx, 5000, 3000, buf[1000:].data_ptr(), 3000, da.d_scratch, da.scratch_bytes)
+    assert da.sync() == ace.ACE_OK
+    h = buf.cpu().numpy()
+    assert (h[:1000] == 7).all() and (h[4000:] == 7).all()
+    assert np.array_equal(h[1000:4000], data[5000:8000])
+    for coord, length in [(n, 1), (0, 0), (1, n)]:
+        with pytest.raises(ace.AceError) as e:
+            da.seek(coord, max(length, 1) if length else 0, out=torch.empty(8, dtype=torch.uint8, device="cuda"))
+        assert e.value.status in (ace.ACE_E_RANGE, ace.ACE_E_NOMEM)
+    da.close()
+
+
+def test_seek_closure_larger_than_scratch_reports_nomem():
+    data = synth.generate("genome", 2_000_000, 4)
+    arc = oracle.encode(data, 12, 4, 16)  # deep chains: long closures
+    cl = oracle.closure(arc, 400, 400)
+    assert len(cl) > 4
+    da = DeviceArchive(arc, max_seek_blocks=2)
+    da.seek(400 * 4096, 10)
+    assert da.sync() == ace.ACE_E_NOMEM
+    # the scratch stays usable afterwards
+    da2 = DeviceArchive(arc, max_seek_blocks=len(cl))
+    out = da2.seek(400 * 4096, 10)
+    assert da2.sync() == ace.ACE_OK
+    assert np.array_equal(out.cpu().numpy(), data[400 * 4096: 400 * 4096 + 10])
+    da.close()
+    da2.close()
+
+
+def _with_dep_removed(arc, block):
+    """The archive with one block's dependency intervals pointed at block 0:
+    its real source blocks leave the seek closure (a host-made corruption)."""
+    bad = arc.copy()
+    nb = oracle.info(arc)["n_blocks"]
+    deps_off = int(arc[40:48].view(np.uint64)[0])
+    ptr = bad[deps_off:deps_off + 4 * (nb + 1)].view(np.uint32)
+    ivs = bad[deps_off + 4 * (nb + 1):].view(np.uint32)
+    for i in range(int(ptr[block]), int(ptr[block + 1])):
+        ivs[2 * i] = 0
+        ivs[2 * i + 1] = 0
+    return bad
+
+
+def test_wait_gives_up_with_timeout_status():
+    """A seek whose closure misses a source block waits on a flag nothing
+    sets; the bounded wait ends with ACE_E_TIMEOUT and the context stays
+    usable."""
+    data = synth.generate("text", 200_000, 12)
+    arc = oracle.encode(data, 12, 4, 16)
+    b = 30
+    deps = oracle.deps(arc)[b]
+    assert deps and deps != [(0, 0)]
+    bad = _with_dep_removed(arc, b)
+    da = DeviceArchive(bad, max_seek_blocks=64)
+    ace.ace_index_set_tune(da.idx, ace.make_tune(wait_timeout_ns=2_000_000))
+    da.seek(b * 4096, 100)
+    assert da.sync() == ace.ACE_E_TIMEOUT
+    # a clean seek on the same scratch still works
+    out = da.seek(0, 4096)
+    assert da.sync() == ace.ACE_OK
+    assert np.array_equal(out.cpu().numpy(), data[:4096])
+    da.close()
+
+
+def test_corrupt_payloads_are_reported_not_faulted():
+    data = synth.generate("mixed", 300_000, 13)
+    arc = ace.ace_encode(data, 12, 4)
+    payload_off = int(arc[48:56].view(np.uint64)[0])
+    rng = np.random.default_rng(1)
+    seen = set()
+    for trial in range(40):
+        bad = arc.copy()
+        k = int(rng.integers(payload_off, bad.size))
+        bad[k] ^= np.uint8(1 << int(rng.integers(0, 8)))
+        da = DeviceArchive(bad)
+        ace.ace_index_set_tune(da.idx, ace.make_tune(wait_timeout_ns=50_000_000))
+        out = da.decode_all()
+        st = da.sync()
+        assert st in (ace.ACE_OK, ace.ACE_E_CORRUPT), ace.ace_status_str(st)
+        seen.add(st)
+        if st == ace.ACE_OK:
+            # only a flip in padding can leave the archive valid
+            assert np.array_equal(out.cpu().numpy()[: data.size], data)
+        da.close()
+    assert ace.ACE_E_CORRUPT in seen
+    torch.cuda.synchronize()
+
+
+def test_corrupt_directory_rejected_at_index_build():
+    data = synth.generate("text", 100_000, 14)
+    arc = ace.ace_encode(data, 10, 4)
+    dir_off = int(arc[32:40].view(np.uint64)[0])
+    bad = arc.copy()
+    bad[dir_off + 24: dir_off + 28] = np.frombuffer(np.uint32(0xFFFFFFF0).tobytes(), np.uint8)  # stream_bytes
+    with pytest.raises(ace.AceError) as e:
+        DeviceArchive(bad)
+    assert e.value.status == ace.ACE_E_CORRUPT
+
+
+def test_device_fnv_matches_oracle():
+    data = synth.generate("fastq", 100_000, 15)
+    d = torch.from_numpy(data).cuda()
+    res = torch.zeros(1, dtype=torch.int64, device="cuda")
+    ace.ace_fnv1a64(d, data.size, res)
+    torch.cuda.synchronize()
+    assert int(res.cpu().numpy().view(np.uint64)[0]) == oracle.fnv1a64(data)
+
+
+def test_levels_match_oracle():
+    data = synth.generate("mixed", 1_000_000, 16)
+    for arc in (ace.ace_encode(data, 12, 4), oracle.encode(data, 12, 4, 16)):
+        da = DeviceArchive(arc)
+        lv = oracle.levels(arc)
+        assert da.info["n_levels"] == int(lv.max()) + 1
+        nb = da.info["n_blocks"]
+        level = da.d_index[256:256 + 4 * nb].cpu().numpy().view(np.uint32)
+        assert np.array_equal(level, lv)
+        da.close()
