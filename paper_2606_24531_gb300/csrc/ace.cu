@@ -715,6 +715,9 @@ ace_status plan_launch(const ace_index* idx, const ace_tune* tune, uint64_t max_
   L->timeout = t.wait_timeout_ns ? t.wait_timeout_ns : kDefaultTimeoutNs;
   L->smem_per_warp = warp_smem_bytes(L->chunk, 520);
   size_t smem = (size_t)L->warps * L->smem_per_warp;
+  int optin = 0;
+  CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, idx->device));
+  if (smem > (size_t)optin) return ACE_E_INVAL;  // this many warps with this chunk do not fit one CTA
   CUDA_TRY(cudaFuncSetAttribute(decode_kernel<SEEK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 0;
   CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, decode_kernel<SEEK>, 32 * L->warps, smem));
