@@ -165,7 +165,7 @@ ace_status ace_scratch_init(const ace_index *idx, void *d_scratch, uint64_t scra
 /* ------------------------------------------------------------ decoding */
 
 typedef struct {
-    uint32_t warps_per_cta;   /* 1..16; 0 = default (4) */
+    uint32_t warps_per_cta;   /* 1..8; 0 = default (4) */
     uint32_t ctas_per_sm;     /* 0 = as many as fit */
     uint32_t chunk_tokens;    /* tokens staged per step, 32..256, multiple of 32; 0 = 128 */
     uint32_t reserved;

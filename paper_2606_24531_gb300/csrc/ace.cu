@@ -155,7 +155,7 @@ struct DecodeArgs {
   uint64_t nb;
   uint32_t log2B, w;
   uint32_t chunk;          // tokens staged per step (multiple of 32)
-  uint32_t esc_cap;
+  uint32_t esc_cap;        // escape values a block may hold
   uint32_t warp_smem;      // bytes of shared memory per warp
   uint32_t n_items;        // whole decode: work items; seek: read from the scratch header
   const uint32_t* items;   // whole decode: blocks in (level, block) order; seek: the closure
@@ -166,52 +166,43 @@ struct DecodeArgs {
   uint8_t* slice;          // seek: caller's output
   uint64_t coord, len;     // seek: requested range
   uint64_t timeout_ns;
+  uint8_t* warp_scratch;   // per-warp token spill: match lengths and offset bytes
+  uint32_t warp_scratch_bytes;
 };
 
-// Shared memory of one warp, carved from the dynamic allocation.
+// Shared memory of one warp: one stream's tables at a time, the three
+// renormalisation rings, the current chunk's token positions, the escapes.
 struct WarpMem {
-  Lut* lut;        // [3]
+  Lut* lut;
+  uint8_t* ring;   // [3][kRing]
   uint32_t* tdst;  // [chunk + 1] start of each token's literal run, within the block
-  uint32_t* tlit;  // [chunk + 1] index of each token's first literal in the block's literals
-  uint32_t* tml;   // [chunk] match length
-  uint64_t* tsrc;  // [chunk] absolute source
-  uint8_t* codes;  // [2 chunk]
-  uint8_t* offb;   // [5 chunk]
+  uint32_t* tlit;  // [chunk + 1] index of each token's first literal among the block's literals
   uint16_t* esc;   // [esc_cap]
 };
 
 __host__ __device__ inline uint32_t warp_smem_bytes(uint32_t chunk, uint32_t escn) {
-  uint32_t b = 3 * sizeof(Lut);
-  b += 4 * (chunk + 1) * 2 + 4 * chunk + 8 * chunk;
-  b += 2 * chunk + 5 * chunk;
-  b += 2 * escn;
+  uint32_t b = sizeof(Lut) + 3 * kRing + 8 * (chunk + 1) + 2 * escn;
   return (b + 15) & ~15u;
+}
+
+__host__ __device__ inline uint32_t warp_scratch_bytes(uint32_t chunk) {
+  return (4 * chunk + 5 * chunk + 255) & ~255u;  // match lengths, then offset bytes
 }
 
 __device__ inline WarpMem carve(uint8_t* base, uint32_t chunk) {
   WarpMem m;
   m.lut = reinterpret_cast<Lut*>(base);
-  uint8_t* p = base + 3 * sizeof(Lut);
-  m.tsrc = reinterpret_cast<uint64_t*>(p);
-  p += 8 * chunk;
-  m.tdst = reinterpret_cast<uint32_t*>(p);
-  p += 4 * (chunk + 1);
-  m.tlit = reinterpret_cast<uint32_t*>(p);
-  p += 4 * (chunk + 1);
-  m.tml = reinterpret_cast<uint32_t*>(p);
-  p += 4 * chunk;
-  m.esc = reinterpret_cast<uint16_t*>(p);
-  p += 2 * 520;  // room for the largest escape table (64 KiB blocks)
-  m.codes = p;
-  p += 2 * chunk;
-  m.offb = p;
+  m.ring = base + sizeof(Lut);
+  m.tdst = reinterpret_cast<uint32_t*>(m.ring + 3 * kRing);
+  m.tlit = m.tdst + (chunk + 1);
+  m.esc = reinterpret_cast<uint16_t*>(m.tlit + (chunk + 1));
   return m;
 }
 
 template <bool SEEK>
 struct Addr {
   // device address of absolute output position p
-  __device__ __forceinline__ static uint8_t* at(const DecodeArgs& a, uint64_t p) {
+  __device__ __forceinline__ static const uint8_t* at(const DecodeArgs& a, uint64_t p) {
     if (SEEK) {
       uint64_t k = p >> a.log2B;
       return a.out + ((uint64_t)__ldg(a.slot_of + k) << a.log2B) + (p & ((1ull << a.log2B) - 1));
@@ -226,21 +217,21 @@ __device__ __forceinline__ void fail(const DecodeArgs& a, bool& ok, ace_status c
   ok = false;
 }
 
-// Copies one match: out[D + i] = out[S + i] for i < len in the sequential
-// LZ77 sense (a source overlapping its destination repeats with period D - S).
-// dst points at absolute position D inside the block being decoded.
+// Copies one match, sequential LZ77 semantics: dst[i] = out[S + i] in order,
+// so a source overlapping its destination repeats.  dst is the destination
+// inside the block being decoded.
 template <bool SEEK>
-__device__ __forceinline__ void copy_match_lane(const DecodeArgs& a, uint8_t* dst, uint64_t D, uint64_t S,
-                                                uint32_t len) {
+__device__ __forceinline__ void copy_match_lane(const DecodeArgs& a, uint8_t* dst, uint64_t S, uint32_t len) {
   if (!SEEK) {
     const uint8_t* src = a.out + S;
     for (uint32_t i = 0; i < len; i++) dst[i] = __ldcg(src + i);
   } else {
     for (uint32_t i = 0; i < len; i++) dst[i] = __ldcg(Addr<true>::at(a, S + i));
   }
-  (void)D;
 }
 
+// The same by a whole warp: with distance d = D - S, byte i comes from
+// S + (i mod d), all of which precede D and are complete.
 template <bool SEEK>
 __device__ __forceinline__ void copy_match_warp(const DecodeArgs& a, uint8_t* dst, uint64_t D, uint64_t S,
                                                 uint32_t len, uint32_t lane) {
@@ -248,96 +239,98 @@ __device__ __forceinline__ void copy_match_warp(const DecodeArgs& a, uint8_t* ds
   if (d >= len) {
     for (uint32_t i = lane; i < len; i += 32) dst[i] = __ldcg(Addr<SEEK>::at(a, S + i));
   } else {
-    // period d: out[D + i] = out[S + (i mod d)], and [S, D) is complete
     uint32_t dd = (uint32_t)d;
     for (uint32_t i = lane; i < len; i += 32) dst[i] = __ldcg(Addr<SEEK>::at(a, S + i % dd));
   }
 }
 
+enum { LUT_NONE = 3 };
+
 // Decodes one block through both layers (Section 3 entry point, then the
-// Section 2 match layer) into its place.  Returns false if it found the block
-// corrupt or a wait gave up (the error is recorded).
+// Section 2 match layer) into its place.  Tokens are processed in chunks:
+// the length codes of a chunk are decoded and parsed into token positions,
+// then its offsets, then its literals go straight to their output positions,
+// then its matches are resolved.  Returns false if the block is corrupt or a
+// wait gave up (the error is recorded).
 template <bool SEEK>
-__device__ bool decode_block(const DecodeArgs& a, const WarpMem& m, uint32_t b, uint32_t lane, uint32_t epoch) {
+__device__ bool decode_block(const DecodeArgs& a, const WarpMem& m, uint32_t* g_tml, uint8_t* g_offb, uint32_t b,
+                             uint32_t lane, uint32_t epoch) {
   bool ok = true;
   const uint32_t* dw = reinterpret_cast<const uint32_t*>(a.dir + b);
   uint32_t dv = lane < 16 ? __ldg(dw + lane) : 0u;
-  uint64_t soff[3];
-  uint32_t sbytes[3], nsym[3];
-#pragma unroll
-  for (int k = 0; k < 3; k++) {
-    soff[k] = (uint64_t)__shfl_sync(kFull, dv, 2 * k) | ((uint64_t)__shfl_sync(kFull, dv, 2 * k + 1) << 32);
-    sbytes[k] = __shfl_sync(kFull, dv, 6 + k);
-    nsym[k] = __shfl_sync(kFull, dv, 9 + k);
-  }
-  const uint32_t ntok = __shfl_sync(kFull, dv, 12), nesc = __shfl_sync(kFull, dv, 13);
   const uint64_t B = (uint64_t)1 << a.log2B, bstart = (uint64_t)b << a.log2B;
   const uint32_t blen = (uint32_t)min(B, a.total - bstart);
   const uint32_t w = a.w;
+  const uint32_t ntok = __shfl_sync(kFull, dv, 12), nesc = __shfl_sync(kFull, dv, 13);
   uint8_t* obase = SEEK ? a.out + ((uint64_t)__ldg(a.slot_of + b) << a.log2B) : a.out + bstart;
+  const uint32_t lt = lanemask_lt();
 
-  Rans st[3];
-  for (int k = 0; k < 3 && ok; k++)
-    if (!stream_setup(a.arc + a.payload_off + soff[k], sbytes[k], nsym[k], m.lut[k], st[k], lane))
+  Stream st[3];
+#pragma unroll
+  for (int k = 0; k < 3; k++) {
+    uint64_t soff = (uint64_t)__shfl_sync(kFull, dv, 2 * k) | ((uint64_t)__shfl_sync(kFull, dv, 2 * k + 1) << 32);
+    uint32_t sbytes = __shfl_sync(kFull, dv, 6 + k), nsym = __shfl_sync(kFull, dv, 9 + k);
+    if (!stream_open(a.arc + a.payload_off + soff, sbytes, nsym, m.ring + k * kRing, st[k], lane))
       fail(a, ok, ACE_E_CORRUPT, b, 20 + k, lane);
+  }
   if (!ok) return false;
-
-  // escape values at the head of the length stream
-  uint8_t* escb = reinterpret_cast<uint8_t*>(m.esc);
-  if (!rans_decode(st[ACE_S_LEN], m.lut[ACE_S_LEN], 2 * nesc, lane, [&](uint32_t i, uint32_t s) { escb[i] = (uint8_t)s; }))
-    fail(a, ok, ACE_E_CORRUPT, b, 30, lane);
+  cp_async_wait<2>();
   __syncwarp();
+  Stream& sl = st[ACE_S_LIT];
+  Stream& sn = st[ACE_S_LEN];
+  Stream& so = st[ACE_S_OFF];
+  uint32_t loaded = LUT_NONE;
+  auto use_lut = [&](uint32_t k, Stream& s) -> bool {
+    if (loaded == k) return true;
+    loaded = k;
+    return lut_build(s, *m.lut, lane);
+  };
+
+  bool bad = false;
+  // escape values at the head of the length stream
+  if (nesc) {
+    if (!use_lut(ACE_S_LEN, sn)) fail(a, ok, ACE_E_CORRUPT, b, 29, lane);
+    uint8_t* escb = reinterpret_cast<uint8_t*>(m.esc);
+    while (ok && sn.next < 2 * nesc) {
+      bool act;
+      uint32_t i;
+      uint32_t s = rans_round(sn, m.ring + ACE_S_LEN * kRing, *m.lut, 2 * nesc, lane, lt, act, i, bad);
+      if (act) escb[i] = (uint8_t)s;
+    }
+    __syncwarp();
+  }
+  if (bad) fail(a, ok, ACE_E_CORRUPT, b, 30, lane);
 
   uint32_t out_pos = 0, lit_pos = 0, esc_rank = 0;
-  const uint32_t lt = lanemask_lt();
   for (uint32_t t0 = 0; t0 < ntok && ok; t0 += a.chunk) {
     const uint32_t tc = min(a.chunk, ntok - t0);
     const uint32_t nm = (t0 + tc == ntok) ? tc - 1 : tc;  // matches in this chunk
-    uint32_t len_base = 2 * nesc + 2 * t0;
-    if (!rans_decode(st[ACE_S_LEN], m.lut[ACE_S_LEN], len_base + 2 * tc, lane,
-                     [&](uint32_t i, uint32_t s) { m.codes[i - len_base] = (uint8_t)s; }))
-      fail(a, ok, ACE_E_CORRUPT, b, 31, lane);
-    uint32_t off_base = w * t0;
-    if (ok && !rans_decode(st[ACE_S_OFF], m.lut[ACE_S_OFF], off_base + w * nm, lane,
-                           [&](uint32_t i, uint32_t s) { m.offb[i - off_base] = (uint8_t)s; }))
-      fail(a, ok, ACE_E_CORRUPT, b, 32, lane);
-    if (!ok) break;
-    __syncwarp();
-    // tokens: values, escapes, prefix sums (stream layout in ace_format.h)
-    bool bad = false;
-    for (uint32_t g = 0; g < tc; g += 32) {
-      uint32_t t = g + lane;
-      bool act = t < tc;
-      uint32_t c0 = act ? m.codes[2 * t] : 0, c1 = act ? m.codes[2 * t + 1] : 0;
-      bool e0 = act && c0 == 255, e1 = act && c1 == 255;
-      uint32_t b0 = __ballot_sync(kFull, e0), b1 = __ballot_sync(kFull, e1);
-      uint32_t r0 = esc_rank + __popc(b0 & lt) + __popc(b1 & lt), r1 = r0 + (e0 ? 1 : 0);
-      uint32_t lr = c0, ml = c1;
-      if (e0) {
-        if (r0 < nesc) lr = 255 + m.esc[r0];
+    // length codes: two per token; parse values, escapes and running positions
+    if (!use_lut(ACE_S_LEN, sn)) fail(a, ok, ACE_E_CORRUPT, b, 31, lane);
+    const uint32_t cbase = 2 * nesc, cend = cbase + 2 * (t0 + tc);
+    while (ok && sn.next < cend) {
+      bool act;
+      uint32_t i;
+      uint32_t s = rans_round(sn, m.ring + ACE_S_LEN * kRing, *m.lut, cend, lane, lt, act, i, bad);
+      bool e = act && s == 255;
+      uint32_t eb = __ballot_sync(kFull, e);
+      uint32_t r = esc_rank + __popc(eb & lt);
+      uint32_t v = s;
+      if (e) {
+        if (r < nesc) v = 255u + m.esc[r];
         else bad = true;
       }
-      if (e1) {
-        if (r1 < nesc) ml = 255 + m.esc[r1];
-        else bad = true;
-      }
-      esc_rank += __popc(b0) + __popc(b1);
-      uint32_t io = warp_incl_sum(lr + ml, lane), il = warp_incl_sum(lr, lane);
-      if (act) {
-        m.tdst[t] = out_pos + io - (lr + ml);
-        m.tlit[t] = lit_pos + il - lr;
-        m.tml[t] = ml;
-        uint64_t src = 0;
-        if (t < nm) {
-          const uint8_t* q = m.offb + w * t;
-          src = (uint64_t)q[0] | ((uint64_t)q[1] << 8) | ((uint64_t)q[2] << 16) | ((uint64_t)q[3] << 24);
-          if (w == 5) src |= (uint64_t)q[4] << 32;
-          uint64_t D = bstart + out_pos + io - ml;  // match destination
-          if (ml && src >= D) bad = true;
-        } else if (ml) {
-          bad = true;  // the block's last token carries no match
-        }
-        m.tsrc[t] = src;
+      esc_rank += __popc(eb);
+      uint32_t lr = __shfl_sync(kFull, v, lane & ~1u), ml = __shfl_sync(kFull, v, lane | 1u);
+      bool own = act && !(lane & 1);  // codes start at an even index: pairs never straddle rounds
+      uint32_t to = own ? lr + ml : 0u, tl = own ? lr : 0u;
+      uint32_t io = warp_incl_sum(to, lane), il = warp_incl_sum(tl, lane);
+      if (own) {
+        uint32_t t = ((i - cbase) >> 1) - t0;
+        m.tdst[t] = out_pos + io - to;
+        m.tlit[t] = lit_pos + il - tl;
+        g_tml[t] = ml;
+        if (t0 + t == ntok - 1 && ml) bad = true;  // the block's last token carries no match
       }
       out_pos += __shfl_sync(kFull, io, 31);
       lit_pos += __shfl_sync(kFull, il, 31);
@@ -346,50 +339,78 @@ __device__ bool decode_block(const DecodeArgs& a, const WarpMem& m, uint32_t b, 
       m.tdst[tc] = out_pos;
       m.tlit[tc] = lit_pos;
     }
-    bad |= out_pos > blen || lit_pos > nsym[ACE_S_LIT];
-    if (__any_sync(kFull, bad)) fail(a, ok, ACE_E_CORRUPT, b, 33, lane);
+    bad |= out_pos > blen || lit_pos > sl.nsym;
+    if (__any_sync(kFull, bad)) fail(a, ok, ACE_E_CORRUPT, b, 32, lane);
+    if (!ok) break;
+    // absolute offsets of this chunk's matches, off_width bytes each
+    if (nm) {
+      if (!use_lut(ACE_S_OFF, so)) fail(a, ok, ACE_E_CORRUPT, b, 33, lane);
+      const uint32_t obase0 = w * t0, oend = obase0 + w * nm;
+      while (ok && so.next < oend) {
+        bool act;
+        uint32_t i;
+        uint32_t s = rans_round(so, m.ring + ACE_S_OFF * kRing, *m.lut, oend, lane, lt, act, i, bad);
+        if (act) g_offb[i - obase0] = (uint8_t)s;
+      }
+      if (__any_sync(kFull, bad)) fail(a, ok, ACE_E_CORRUPT, b, 34, lane);
+    }
+    __syncwarp();
+    // literals land at their token's run start plus their offset in the run
+    if (ok && lit_pos > sl.next) {
+      if (!use_lut(ACE_S_LIT, sl)) fail(a, ok, ACE_E_CORRUPT, b, 35, lane);
+      uint32_t tp = 0, cur_lit = m.tlit[0], cur_dst = m.tdst[0], nxt_lit = m.tlit[1];
+      while (ok && sl.next < lit_pos) {
+        bool act;
+        uint32_t i;
+        uint32_t s = rans_round(sl, m.ring + ACE_S_LIT * kRing, *m.lut, lit_pos, lane, lt, act, i, bad);
+        if (act) {
+          while (nxt_lit <= i) {
+            tp++;
+            cur_lit = nxt_lit;
+            cur_dst = m.tdst[tp];
+            nxt_lit = m.tlit[tp + 1];
+          }
+          obase[cur_dst + (i - cur_lit)] = (uint8_t)s;
+        }
+      }
+      if (__any_sync(kFull, bad)) fail(a, ok, ACE_E_CORRUPT, b, 36, lane);
+    }
     if (!ok) break;
     __syncwarp();
 
-    // literal layer: literal i lands at its token's run start plus its offset in the run
-    uint32_t tp = 0;
-    if (!rans_decode(st[ACE_S_LIT], m.lut[ACE_S_LIT], lit_pos, lane, [&](uint32_t i, uint32_t s) {
-          while (m.tlit[tp + 1] <= i) tp++;
-          obase[m.tdst[tp] + (i - m.tlit[tp])] = (uint8_t)s;
-        }))
-      fail(a, ok, ACE_E_CORRUPT, b, 34, lane);
-    if (!ok) break;
-    __syncwarp();
-
-    // match layer: wait for source blocks, then resolve in dependency waves
+    // match layer: wait for the source blocks, then resolve in dependency waves
     bool timeout = false;
     for (uint32_t t = lane; t < nm; t += 32) {
-      uint32_t ml = m.tml[t];
+      uint32_t ml = g_tml[t];
       if (!ml) continue;
-      uint64_t S = m.tsrc[t];
+      const uint8_t* q = g_offb + w * t;
+      uint64_t S = (uint64_t)q[0] | ((uint64_t)q[1] << 8) | ((uint64_t)q[2] << 16) | ((uint64_t)q[3] << 24);
+      if (w == 5) S |= (uint64_t)q[4] << 32;
       uint64_t D = bstart + m.tdst[t + 1] - ml;
+      if (S >= D) {
+        bad = true;
+        continue;
+      }
       uint64_t rend = S + min((uint64_t)ml, D - S);
       uint64_t k0 = S >> a.log2B, k1 = (rend - 1) >> a.log2B;
-      for (uint64_t k = k0; k <= k1 && k < b; k++)
-        if (!wait_flag(a.ready + k, epoch, a.timeout_ns)) {
-          timeout = true;
-          break;
-        }
+      for (uint64_t k = k0; k <= k1 && k < b && !timeout; k++)
+        if (!wait_flag(a.ready + k, epoch, a.timeout_ns)) timeout = true;
     }
-    if (__any_sync(kFull, timeout)) fail(a, ok, ACE_E_TIMEOUT, b, 35, lane);
+    if (__any_sync(kFull, bad)) fail(a, ok, ACE_E_CORRUPT, b, 37, lane);
+    if (__any_sync(kFull, timeout)) fail(a, ok, ACE_E_TIMEOUT, b, 38, lane);
     if (!ok) break;
-    // each lane owns matches lane, lane+32, ...; pending bits track them
+    // each lane owns matches lane, lane + 32, ...; pending bits track them
     uint32_t pend = 0;
     for (uint32_t j = 0, t = lane; t < nm; j++, t += 32)
-      if (m.tml[t]) pend |= 1u << j;
+      if (g_tml[t]) pend |= 1u << j;
     while (__any_sync(kFull, pend != 0)) {
-      // W: destination of the first pending match; anything whose read range
+      // W: destination of the first pending match; a match whose read range
       // ends at or before W reads only finished bytes
       uint64_t myW = ~0ull;
       for (uint32_t j = 0; j < 32; j++)
         if ((pend >> j) & 1) {
           uint32_t t = lane + 32 * j;
-          myW = bstart + m.tdst[t + 1] - m.tml[t];
+          myW = bstart + m.tdst[t + 1] - g_tml[t];
           break;
         }
       uint64_t W = warp_min64(myW);
@@ -397,31 +418,32 @@ __device__ bool decode_block(const DecodeArgs& a, const WarpMem& m, uint32_t b, 
       for (uint32_t j = 0; j < 32; j++)
         if ((pend >> j) & 1) {
           uint32_t t = lane + 32 * j;
-          uint32_t ml = m.tml[t];
-          uint64_t S = m.tsrc[t], D = bstart + m.tdst[t + 1] - ml;
+          uint32_t ml = g_tml[t];
+          const uint8_t* q = g_offb + w * t;
+          uint64_t S = (uint64_t)q[0] | ((uint64_t)q[1] << 8) | ((uint64_t)q[2] << 16) | ((uint64_t)q[3] << 24);
+          if (w == 5) S |= (uint64_t)q[4] << 32;
+          uint64_t D = bstart + m.tdst[t + 1] - ml;
           uint64_t rend = S + min((uint64_t)ml, D - S);
-          if (rend <= W) go |= 1u << j;
-        }
-      // short matches: the owning lane copies; long ones: the whole warp
-      for (uint32_t j = 0; j < 32; j++)
-        if ((go >> j) & 1) {
-          uint32_t t = lane + 32 * j;
-          uint32_t ml = m.tml[t];
-          if (ml <= 64) {
-            uint32_t dl = m.tdst[t + 1] - ml;
-            copy_match_lane<SEEK>(a, obase + dl, bstart + dl, m.tsrc[t], ml);
-            go &= ~(1u << j);
-            pend &= ~(1u << j);
+          if (rend <= W) {
+            go |= 1u << j;
+            if (ml <= 64) {  // short: the owning lane copies it
+              copy_match_lane<SEEK>(a, obase + (D - bstart), S, ml);
+              go &= ~(1u << j);
+              pend &= ~(1u << j);
+            }
           }
         }
       uint32_t any_long;
-      while ((any_long = __ballot_sync(kFull, go != 0)) != 0) {
+      while ((any_long = __ballot_sync(kFull, go != 0)) != 0) {  // long: the whole warp
         uint32_t src_lane = __ffs(any_long) - 1;
         uint32_t j = __ffs(__shfl_sync(kFull, go, src_lane)) - 1;
         uint32_t t = src_lane + 32 * j;
-        uint32_t ml = m.tml[t];
-        uint32_t dl = m.tdst[t + 1] - ml;
-        copy_match_warp<SEEK>(a, obase + dl, bstart + dl, m.tsrc[t], ml, lane);
+        uint32_t ml = g_tml[t];
+        const uint8_t* q = g_offb + w * t;
+        uint64_t S = (uint64_t)q[0] | ((uint64_t)q[1] << 8) | ((uint64_t)q[2] << 16) | ((uint64_t)q[3] << 24);
+        if (w == 5) S |= (uint64_t)q[4] << 32;
+        uint64_t D = bstart + m.tdst[t + 1] - ml;
+        copy_match_warp<SEEK>(a, obase + (D - bstart), D, S, ml, lane);
         if (lane == src_lane) {
           go &= ~(1u << j);
           pend &= ~(1u << j);
@@ -431,18 +453,23 @@ __device__ bool decode_block(const DecodeArgs& a, const WarpMem& m, uint32_t b, 
     }
   }
   if (ok) {
-    bool fin = out_pos == blen && lit_pos == nsym[ACE_S_LIT] && esc_rank == nesc;
-    fin = fin && rans_finished(st[0]) && rans_finished(st[1]) && rans_finished(st[2]);
+    bool fin = out_pos == blen && lit_pos == sl.nsym && esc_rank == nesc;
+    fin = fin && stream_finished(st[0]) && stream_finished(st[1]) && stream_finished(st[2]);
     if (!__all_sync(kFull, fin)) fail(a, ok, ACE_E_CORRUPT, b, 40, lane);
   }
+  cp_async_wait<0>();  // no ring fill may land after the next block reuses the rings
+  __syncwarp();
   return ok;
 }
 
 template <bool SEEK>
-__global__ void __launch_bounds__(512) decode_kernel(DecodeArgs a) {
+__global__ void __launch_bounds__(256, 3) decode_kernel(DecodeArgs a) {
   extern __shared__ __align__(16) uint8_t smem[];
   const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   WarpMem m = carve(smem + (size_t)wid * a.warp_smem, a.chunk);
+  uint8_t* ws = a.warp_scratch + (size_t)(blockIdx.x * (blockDim.x >> 5) + wid) * a.warp_scratch_bytes;
+  uint32_t* g_tml = reinterpret_cast<uint32_t*>(ws);
+  uint8_t* g_offb = ws + 4 * a.chunk;
   const uint32_t epoch = *(volatile uint32_t*)&a.sh->epoch;
   const uint32_t n_items = SEEK ? *(volatile uint32_t*)&a.sh->n_work : a.n_items;
   while (true) {
@@ -451,7 +478,7 @@ __global__ void __launch_bounds__(512) decode_kernel(DecodeArgs a) {
     it = __shfl_sync(kFull, it, 0);
     if (it >= n_items) break;
     uint32_t b = __ldg(a.items + it);
-    bool ok = decode_block<SEEK>(a, m, b, lane, epoch);
+    bool ok = decode_block<SEEK>(a, m, g_tml, g_offb, b, lane, epoch);
     if (SEEK && ok) {
       // copy the part of this block inside [coord, coord + len) to the caller
       uint64_t bs = (uint64_t)b << a.log2B, be = min(bs + ((uint64_t)1 << a.log2B), a.total);
@@ -648,29 +675,39 @@ IndexLayout index_layout(uint64_t nb) {
 }
 
 struct ScratchLayout {
-  uint64_t ready, slot_of, work, marks, front0, front1, slots, total;
+  uint64_t ready, slot_of, work, marks, front0, front1, warps, slots, total;
+  uint64_t n_warps;  // per-warp token regions available
 };
 
-ScratchLayout scratch_layout(uint64_t nb, uint32_t log2B, uint64_t max_seek) {
+constexpr uint32_t kMaxChunk = 256;
+constexpr uint32_t kMaxWarpsPerCta = 8;  // the decode kernel's launch bounds: 256 threads
+constexpr uint32_t kMaxWarpsPerSM = 64;
+
+// One layout serves every call on a scratch buffer, so whole decodes and
+// seeks may share it: header, ready flags, the seek's slot map, work list,
+// closure marks and frontiers, the per-warp token regions, then (for seeks)
+// the block slots.
+ScratchLayout scratch_layout(uint64_t nb, uint32_t log2B, uint64_t max_seek, int num_sms) {
   ScratchLayout L;
   uint64_t o = sizeof(ScratchHdr);
   L.ready = o;
   o = align256(o + 4 * nb);
-  L.slot_of = L.work = L.marks = L.front0 = L.front1 = L.slots = o;
-  if (max_seek) {
-    L.slot_of = o;
-    o = align256(o + 4 * nb);
-    L.work = o;
-    o = align256(o + 4 * nb);
-    L.marks = o;
-    o = align256(o + 4 * ((nb + 31) / 32));
-    L.front0 = o;
-    o = align256(o + 4 * nb);
-    L.front1 = o;
-    o = align256(o + 4 * nb);
-    L.slots = o;
-    o = align256(o + (max_seek << log2B));
-  }
+  L.slot_of = o;
+  o = align256(o + 4 * nb);
+  L.work = o;
+  o = align256(o + 4 * nb);
+  L.marks = o;
+  o = align256(o + 4 * ((nb + 31) / 32));
+  L.front0 = o;
+  o = align256(o + 4 * nb);
+  L.front1 = o;
+  o = align256(o + 4 * nb);
+  uint64_t items = std::max<uint64_t>(nb, max_seek);
+  L.n_warps = std::min<uint64_t>((uint64_t)num_sms * kMaxWarpsPerSM, items + 16);
+  L.warps = o;
+  o = align256(o + L.n_warps * warp_scratch_bytes(kMaxChunk));
+  L.slots = o;
+  o = align256(o + (max_seek << log2B));
   L.total = o;
   return L;
 }
@@ -707,13 +744,14 @@ struct Launch {
 };
 
 template <bool SEEK>
-ace_status plan_launch(const ace_index* idx, const ace_tune* tune, uint64_t max_items, Launch* L) {
+ace_status plan_launch(const ace_index* idx, const ace_tune* tune, uint64_t max_items, uint64_t max_warps,
+                       Launch* L) {
   ace_tune t = tune ? *tune : idx->tune;
   L->warps = t.warps_per_cta ? t.warps_per_cta : 4;
   L->chunk = t.chunk_tokens ? t.chunk_tokens : 128;
-  if (L->warps > 16 || (L->chunk & 31) || L->chunk > 256) return ACE_E_INVAL;
+  if (L->warps > kMaxWarpsPerCta || (L->chunk & 31) || L->chunk > kMaxChunk) return ACE_E_INVAL;
   L->timeout = t.wait_timeout_ns ? t.wait_timeout_ns : kDefaultTimeoutNs;
-  L->smem_per_warp = warp_smem_bytes(L->chunk, 520);
+  L->smem_per_warp = warp_smem_bytes(L->chunk, esc_cap(idx->h.log2_block));
   size_t smem = (size_t)L->warps * L->smem_per_warp;
   int optin = 0;
   CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, idx->device));
@@ -726,7 +764,9 @@ ace_status plan_launch(const ace_index* idx, const ace_tune* tune, uint64_t max_
   L->ctas_per_sm = (uint32_t)per_sm;
   uint64_t grid = (uint64_t)idx->num_sms * per_sm;
   uint64_t need = (max_items + L->warps - 1) / L->warps;
-  L->grid = (uint32_t)std::max<uint64_t>(1, std::min(grid, need));
+  grid = std::min(grid, max_warps / L->warps);
+  if (grid < 1) return ACE_E_NOMEM;
+  L->grid = (uint32_t)std::min(grid, std::max<uint64_t>(1, need));
   return ACE_OK;
 }
 
@@ -848,7 +888,7 @@ ace_status ace_index_info(const ace_index* idx, ace_info* info) {
 
 ace_status ace_index_set_tune(ace_index* idx, const ace_tune* tune) {
   if (!idx) return ACE_E_INVAL;
-  if (tune && (tune->warps_per_cta > 16 || (tune->chunk_tokens & 31) || tune->chunk_tokens > 256))
+  if (tune && (tune->warps_per_cta > kMaxWarpsPerCta || (tune->chunk_tokens & 31) || tune->chunk_tokens > kMaxChunk))
     return ACE_E_INVAL;
   idx->tune = tune ? *tune : ace_tune{};
   return ACE_OK;
@@ -861,16 +901,16 @@ ace_status ace_index_free(ace_index* idx) {
 
 ace_status ace_scratch_size(const ace_index* idx, uint64_t max_seek_blocks, uint64_t* bytes) {
   if (!idx || !bytes) return ACE_E_INVAL;
-  *bytes = scratch_layout(idx->h.n_blocks, idx->h.log2_block, max_seek_blocks).total;
+  *bytes = scratch_layout(idx->h.n_blocks, idx->h.log2_block, max_seek_blocks, idx->num_sms).total;
   return ACE_OK;
 }
 
 ace_status ace_scratch_init(const ace_index* idx, void* d_scratch, uint64_t scratch_bytes, cudaStream_t s) {
   if (!idx || !d_scratch || !aligned(d_scratch, 256)) return ACE_E_INVAL;
-  uint64_t need = scratch_layout(idx->h.n_blocks, idx->h.log2_block, 0).total;
-  if (scratch_bytes < need) return ACE_E_NOMEM;
+  ScratchLayout L0 = scratch_layout(idx->h.n_blocks, idx->h.log2_block, 0, idx->num_sms);
+  if (scratch_bytes < L0.total) return ACE_E_NOMEM;
   // header, ready flags, and (when present) slot map, work list and marks
-  uint64_t clear = std::min<uint64_t>(scratch_bytes, scratch_layout(idx->h.n_blocks, idx->h.log2_block, 1).slots);
+  uint64_t clear = L0.warps;
   CUDA_TRY(cudaMemsetAsync(d_scratch, 0, clear, s));
   return ACE_OK;
 }
@@ -880,11 +920,11 @@ ace_status ace_decode_all(const ace_index* idx, void* d_out, uint64_t out_bytes,
   if (!idx || !d_scratch || (!d_out && idx->h.total_size)) return ACE_E_INVAL;
   if (!aligned(d_scratch, 256)) return ACE_E_INVAL;
   if (out_bytes < idx->h.total_size) return ACE_E_NOMEM;
-  ScratchLayout SL = scratch_layout(idx->h.n_blocks, idx->h.log2_block, 0);
+  ScratchLayout SL = scratch_layout(idx->h.n_blocks, idx->h.log2_block, 0, idx->num_sms);
   if (scratch_bytes < SL.total) return ACE_E_NOMEM;
   if (!idx->h.n_blocks) return ACE_OK;
   Launch L;
-  ace_status rc = plan_launch<false>(idx, tune, idx->h.n_blocks, &L);
+  ace_status rc = plan_launch<false>(idx, tune, idx->h.n_blocks, SL.n_warps, &L);
   if (rc) return rc;
   ScratchHdr* sh = static_cast<ScratchHdr*>(d_scratch);
   DecodeArgs a{};
@@ -904,6 +944,8 @@ ace_status ace_decode_all(const ace_index* idx, void* d_out, uint64_t out_bytes,
   a.sh = sh;
   a.ready = reinterpret_cast<uint32_t*>(static_cast<uint8_t*>(d_scratch) + SL.ready);
   a.timeout_ns = L.timeout;
+  a.warp_scratch = static_cast<uint8_t*>(d_scratch) + SL.warps;
+  a.warp_scratch_bytes = warp_scratch_bytes(kMaxChunk);
   begin_call_kernel<<<1, 1, 0, s>>>(sh);
   decode_kernel<false><<<L.grid, 32 * L.warps, (size_t)L.warps * L.smem_per_warp, s>>>(a);
   CUDA_TRY(cudaGetLastError());
@@ -917,9 +959,13 @@ ace_status ace_seek(const ace_index* idx, uint64_t coord, uint64_t len, void* d_
   if (out_bytes < len) return ACE_E_NOMEM;
   uint64_t nb = idx->h.n_blocks;
   uint32_t log2B = idx->h.log2_block;
-  ScratchLayout S1 = scratch_layout(nb, log2B, 1);
+  ScratchLayout S1 = scratch_layout(nb, log2B, 1, idx->num_sms);
   if (scratch_bytes < S1.total) return ACE_E_NOMEM;
   uint64_t cap = (scratch_bytes - S1.slots) >> log2B;
+  uint64_t max_seek = cap;
+  while (max_seek > 1 && scratch_layout(nb, log2B, max_seek, idx->num_sms).total > scratch_bytes) max_seek--;
+  S1 = scratch_layout(nb, log2B, max_seek, idx->num_sms);
+  cap = (scratch_bytes - S1.slots) >> log2B;
   uint64_t first = coord >> log2B, last = (coord + len - 1) >> log2B;
   if (last - first + 1 > cap) return ACE_E_NOMEM;
   uint8_t* base = static_cast<uint8_t*>(d_scratch);
@@ -939,7 +985,7 @@ ace_status ace_seek(const ace_index* idx, uint64_t coord, uint64_t len, void* d_
   c.cap = cap;
   closure_kernel<<<1, 1024, 0, s>>>(c);
   Launch L;
-  ace_status rc = plan_launch<true>(idx, nullptr, cap, &L);
+  ace_status rc = plan_launch<true>(idx, nullptr, cap, S1.n_warps, &L);
   if (rc) return rc;
   DecodeArgs a{};
   a.arc = idx->d_arc;
@@ -961,6 +1007,8 @@ ace_status ace_seek(const ace_index* idx, uint64_t coord, uint64_t len, void* d_
   a.coord = coord;
   a.len = len;
   a.timeout_ns = L.timeout;
+  a.warp_scratch = base + S1.warps;
+  a.warp_scratch_bytes = warp_scratch_bytes(kMaxChunk);
   decode_kernel<true><<<L.grid, 32 * L.warps, (size_t)L.warps * L.smem_per_warp, s>>>(a);
   CUDA_TRY(cudaGetLastError());
   return ACE_OK;

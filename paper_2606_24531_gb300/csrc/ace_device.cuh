@@ -121,47 +121,94 @@ __device__ __forceinline__ uint64_t warp_min64(uint64_t v) {
   return v;
 }
 
-// State of one interleaved-rANS stream being decoded by a warp: lane j holds
-// the state of interleaved lane j; pos/next are warp-uniform.
-struct Rans {
-  const uint8_t* bytes;  // renormalisation bytes (global)
-  uint32_t nbytes;       // their count
-  uint32_t pos;          // bytes consumed
-  uint32_t next;         // next symbol index to decode
-  uint32_t nsym;
-  uint32_t x;            // this lane's state
+// ----------------------------------------------------------- async copies
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  uint32_t d = (uint32_t)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// ------------------------------------------------------- one rANS stream
+
+// Renormalisation bytes reach the decoder through a 512-byte ring in shared
+// memory: four 128-byte segments, each refilled with cp.async as soon as it
+// has been consumed, so the byte loads on the decode chain hit shared memory.
+constexpr uint32_t kRing = 512;
+constexpr uint32_t kSeg = 128;
+
+// State of one interleaved-rANS stream decoded by one warp: lane j holds the
+// state of interleaved lane j; every other field is warp-uniform.
+struct Stream {
+  const uint8_t* g;    // renormalisation bytes (16-byte aligned); the payload starts head bytes before
+  uint32_t head;       // bytes of states, present bitmap and frequencies
+  uint32_t nsym;       // symbols in the stream
+  uint32_t nbytes;     // renormalisation bytes
+  uint32_t next;       // next symbol index to decode
+  uint32_t pos;        // renormalisation bytes consumed
+  uint32_t base;       // renormalisation offset held by the ring's oldest segment
+  uint32_t x;          // this lane's state
 };
 
-// Reads one stream's entry states and frequency table and builds its lookup
-// tables (the entropy layer's per-block entry point, Section 3).  The stream
-// bounds were validated when the index was built.  Returns false (all lanes)
-// on a bad table or state.
-__device__ __forceinline__ bool stream_setup(const uint8_t* sp, uint32_t sbytes, uint32_t nsym, Lut& lut,
-                                             Rans& r, uint32_t lane) {
-  r.nsym = nsym;
-  r.next = 0;
-  r.pos = 0;
-  r.x = ACE_RANS_L;
-  r.bytes = sp;
-  r.nbytes = 0;
+// Copies renormalisation bytes [off, off + 128) into their ring segment; the
+// copyable extent is nbytes rounded up to 16, which stays inside the archive.
+__device__ __forceinline__ void ring_issue(const Stream& st, uint8_t* ring, uint32_t off, uint32_t lane) {
+  uint32_t o = off + 16 * lane;
+  if (lane < kSeg / 16 && o < ((st.nbytes + 15) & ~15u)) cp_async16(ring + (o & (kRing - 1)), st.g + o);
+  cp_async_commit();
+}
+
+// Reads the entry states (Section 3: the block boundary is the entropy entry
+// point) and locates the renormalisation bytes; issues the first ring fill.
+// The stream bounds were validated when the index was built.  Returns false
+// (all lanes) for a state outside [L, 2^31) or a table overrunning the stream.
+__device__ __forceinline__ bool stream_open(const uint8_t* pay, uint32_t sbytes, uint32_t nsym, uint8_t* ring,
+                                            Stream& st, uint32_t lane) {
+  st.nsym = nsym;
+  st.next = st.pos = st.base = 0;
+  st.x = ACE_RANS_L;
+  st.g = pay;
+  st.head = 0;
+  st.nbytes = 0;
   if (nsym == 0) return sbytes == 0;
-  uint32_t x = reinterpret_cast<const uint32_t*>(sp)[lane];
-  bool bad = x < ACE_RANS_L || x >= (1u << 31);
+  uint32_t x = reinterpret_cast<const uint32_t*>(pay)[lane];
+  uint32_t present = __popc(pay[128 + lane]);
+  present = warp_incl_sum(present, lane);
+  present = __shfl_sync(kFull, present, 31);
+  uint32_t head = ACE_STREAM_HEAD + ((2 * present + 15) & ~15u);
+  bool bad = x < ACE_RANS_L || x >= (1u << 31) || head > sbytes;
+  if (__any_sync(kFull, bad)) return false;
+  st.x = x;
+  st.g = pay + head;
+  st.head = head;
+  st.nbytes = sbytes - head;
+  for (uint32_t s = 0; s < kRing / kSeg; s++) ring_issue(st, ring, s * kSeg, lane);
+  return true;
+}
+
+// Builds the stream's decode tables: fc[s] = f_s << 16 | c_s, and the slot ->
+// symbol table by marking each symbol's first slot and taking a prefix
+// maximum (symbols increase with their slots).  Returns false (all lanes) if
+// the frequencies do not sum to 4096.
+__device__ __forceinline__ bool lut_build(const Stream& st, Lut& lut, uint32_t lane) {
+  if (st.nsym == 0) return true;
+  const uint8_t* sp = st.g - st.head;
   uint32_t bm = sp[128 + lane];
   uint32_t cnt = __popc(bm);
-  uint32_t incl = warp_incl_sum(cnt, lane);
-  uint32_t first = incl - cnt;
-  uint32_t present = __shfl_sync(kFull, incl, 31);
-  uint32_t head = ACE_STREAM_HEAD + ((2 * present + 15) & ~15u);
-  bad |= head > sbytes;
+  uint32_t first = warp_incl_sum(cnt, lane) - cnt;
   uint32_t f[8], fsum = 0;
   const uint8_t* fp = sp + ACE_STREAM_HEAD;
   uint32_t k = first;
+  bool bad = false;
 #pragma unroll
   for (int j = 0; j < 8; j++) {
     f[j] = 0;
     if ((bm >> j) & 1) {
-      if (!bad) f[j] = (uint32_t)fp[2 * k] | ((uint32_t)fp[2 * k + 1] << 8);
+      f[j] = (uint32_t)fp[2 * k] | ((uint32_t)fp[2 * k + 1] << 8);
       k++;
       bad |= f[j] == 0 || f[j] > ACE_SCALE;
     }
@@ -170,7 +217,6 @@ __device__ __forceinline__ bool stream_setup(const uint8_t* sp, uint32_t sbytes,
   uint32_t cincl = warp_incl_sum(fsum, lane);
   bad |= __shfl_sync(kFull, cincl, 31) != ACE_SCALE;
   if (__any_sync(kFull, bad)) return false;
-  // slot -> symbol: zero the table, mark each symbol's first slot, prefix-max
   uint4* sym4 = reinterpret_cast<uint4*>(lut.sym);
 #pragma unroll
   for (int j = 0; j < 8; j++) sym4[lane * 8 + j] = make_uint4(0, 0, 0, 0);
@@ -207,52 +253,54 @@ __device__ __forceinline__ bool stream_setup(const uint8_t* sp, uint32_t sbytes,
     sym4[lane * 8 + j] = w[j];
   }
   __syncwarp();
-  r.bytes = sp + head;
-  r.nbytes = sbytes - head;
-  r.x = x;
   return true;
 }
 
-// Decodes symbols [r.next, end) of a stream; symbol i is on lane i mod 32.
-// sink(i, s) receives each symbol on the lane that decoded it.  Renormalisation
-// bytes are taken in symbol order: a lane needing k in {0,1,2} bytes reads
-// them at the running position plus the bytes needed by lower lanes, high
-// byte first.  Returns false (all lanes) if the stream runs out of bytes.
-template <class Sink>
-__device__ __forceinline__ bool rans_decode(Rans& r, const Lut& lut, uint32_t end, uint32_t lane, Sink&& sink) {
-  const uint32_t lt = lanemask_lt();
-  while (r.next < end) {
-    uint32_t base = r.next & ~31u;
-    uint32_t i = base + lane;
-    bool act = i >= r.next && i < end;
-    uint32_t x = r.x, k = 0, s = 0;
-    if (act) {
-      uint32_t slot = x & (ACE_SCALE - 1);
-      s = lut.sym[slot];
-      uint32_t fc = lut.fc[s];
-      x = (fc >> 16) * (x >> ACE_SCALE_BITS) + slot - (fc & 0xffffu);
-      k = (x < (1u << 15)) + (x < ACE_RANS_L);
-    }
-    uint32_t b1 = __ballot_sync(kFull, k >= 1), b2 = __ballot_sync(kFull, k == 2);
-    uint32_t pre = __popc(b1 & lt) + __popc(b2 & lt);
-    uint32_t tot = __popc(b1) + __popc(b2);
-    if (r.pos + tot > r.nbytes) return false;
-    const uint8_t* p = r.bytes + r.pos + pre;
-    if (k >= 1) x = (x << 8) | p[0];
-    if (k == 2) x = (x << 8) | p[1];
-    r.pos += tot;
-    if (act) {
-      r.x = x;
-      sink(i, s);
-    }
-    r.next = min(base + 32, end);
+// Decodes one round of up to 32 symbols of [st.next, end): symbol i is on
+// lane i mod 32 (interleaved rANS).  slot = x mod 4096, s = sym[slot],
+// x <- f_s floor(x / 4096) + slot - c_s, then x takes k in {0,1,2} bytes,
+// k = [x < 2^15] + [x < 2^23]; bytes are consumed in symbol order, so lane j
+// reads at the running position plus the bytes of lower lanes, high byte
+// first.  Sets act/i for this lane; sets bad (all lanes) if the stream runs
+// out of bytes.  Returns the symbol.
+__device__ __forceinline__ uint32_t rans_round(Stream& st, uint8_t* ring, const Lut& lut, uint32_t end,
+                                               uint32_t lane, uint32_t lt, bool& act, uint32_t& i, bool& bad) {
+  if (st.pos >= st.base + kSeg) {  // oldest segment consumed: refill it further on
+    ring_issue(st, ring, st.base + kRing, lane);
+    st.base += kSeg;
+    cp_async_wait<2>();
+    __syncwarp();
   }
-  return true;
+  uint32_t base = st.next & ~31u;
+  i = base + lane;
+  act = i >= st.next && i < end;
+  uint32_t x = st.x, k = 0, s = 0;
+  if (act) {
+    uint32_t slot = x & (ACE_SCALE - 1);
+    s = lut.sym[slot];
+    uint32_t fc = lut.fc[s];
+    x = (fc >> 16) * (x >> ACE_SCALE_BITS) + slot - (fc & 0xffffu);
+    k = (x < (1u << 15)) + (x < ACE_RANS_L);
+  }
+  uint32_t b1 = __ballot_sync(kFull, k >= 1), b2 = __ballot_sync(kFull, k == 2);
+  uint32_t pre = __popc(b1 & lt) + __popc(b2 & lt);
+  uint32_t tot = __popc(b1) + __popc(b2);
+  if (st.pos + tot > st.nbytes) {
+    bad = true;
+  } else {
+    uint32_t p = st.pos + pre;
+    if (k >= 1) x = (x << 8) | ring[p & (kRing - 1)];
+    if (k == 2) x = (x << 8) | ring[(p + 1) & (kRing - 1)];
+  }
+  st.pos += tot;
+  if (act) st.x = x;
+  st.next = min(base + 32, end);
+  return s;
 }
 
 // All symbols consumed, all bytes consumed and every state back at L.
-__device__ __forceinline__ bool rans_finished(const Rans& r) {
-  bool ok = r.next == r.nsym && r.pos == r.nbytes && (r.nsym == 0 || r.x == ACE_RANS_L);
+__device__ __forceinline__ bool stream_finished(const Stream& st) {
+  bool ok = st.next == st.nsym && st.pos == st.nbytes && (st.nsym == 0 || st.x == ACE_RANS_L);
   return __all_sync(kFull, ok);
 }
 
