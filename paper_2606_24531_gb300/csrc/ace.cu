@@ -75,6 +75,7 @@ __global__ void validate_kernel(IndexArgs a) {
       }
   }
   if (where) record_error(&a.ih->status, &a.ih->err_block, &a.ih->err_where, ACE_E_CORRUPT, (uint32_t)b, where);
+  else atomicMax(&a.ih->max_ntok, d.ntok);
 }
 
 // Dependency levels: level[b] = 0 without sources in other blocks, else
@@ -154,9 +155,10 @@ struct DecodeArgs {
   uint64_t total;
   uint64_t nb;
   uint32_t log2B, w;
-  uint32_t chunk;          // tokens staged per step (multiple of 32)
+  uint32_t window;         // tokens whose positions sit in shared memory at a time (multiple of 32)
   uint32_t esc_cap;        // escape values a block may hold
   uint32_t warp_smem;      // bytes of shared memory per warp
+  uint32_t max_ntok;       // most tokens in any block
   uint32_t n_items;        // whole decode: work items; seek: read from the scratch header
   const uint32_t* items;   // whole decode: blocks in (level, block) order; seek: the closure
   uint8_t* out;            // whole decode: output (absolute positions); seek: block slots
@@ -166,37 +168,64 @@ struct DecodeArgs {
   uint8_t* slice;          // seek: caller's output
   uint64_t coord, len;     // seek: requested range
   uint64_t timeout_ns;
-  uint8_t* warp_scratch;   // per-warp token spill: match lengths and offset bytes
-  uint32_t warp_scratch_bytes;
+  uint8_t* warp_scratch;   // per-warp token records
+  uint64_t warp_scratch_bytes;
 };
 
 // Shared memory of one warp: one stream's tables at a time, the three
-// renormalisation rings, the current chunk's token positions, the escapes.
+// renormalisation rings, a window of token positions (reused for match
+// records in the match phase), and the escape values.
 struct WarpMem {
   Lut* lut;
   uint8_t* ring;   // [3][kRing]
-  uint32_t* tdst;  // [chunk + 1] start of each token's literal run, within the block
-  uint32_t* tlit;  // [chunk + 1] index of each token's first literal among the block's literals
+  uint32_t* tdst;  // [window + 1] start of each token's literal run, within the block
+  uint32_t* tlit;  // [window + 1] index of each token's first literal among the block's literals
   uint16_t* esc;   // [esc_cap]
 };
 
-__host__ __device__ inline uint32_t warp_smem_bytes(uint32_t chunk, uint32_t escn) {
-  uint32_t b = sizeof(Lut) + 3 * kRing + 8 * (chunk + 1) + 2 * escn;
+// Token records of the block a warp is decoding, in global scratch: for
+// every token the start of its literal run and of its literals, its match
+// length, and its match's offset bytes.
+struct TokRec {
+  uint32_t* tdst;  // [max_ntok + 1]
+  uint32_t* tlit;  // [max_ntok + 1]
+  uint32_t* tml;   // [max_ntok]
+  uint8_t* offb;   // [5 max_ntok]
+};
+
+constexpr uint32_t kMatchGroup = 128;  // matches whose records sit in shared memory at a time
+
+// the token window doubles as the match-record area, so it holds either
+__host__ __device__ inline uint32_t window_area_bytes(uint32_t window) {
+  return max(8 * (window + 1), 16 * kMatchGroup);
+}
+
+__host__ __device__ inline uint32_t warp_smem_bytes(uint32_t window, uint32_t escn) {
+  uint32_t b = sizeof(Lut) + 3 * kRing + window_area_bytes(window) + 2 * escn;
   return (b + 15) & ~15u;
 }
 
-__host__ __device__ inline uint32_t warp_scratch_bytes(uint32_t chunk) {
-  return (4 * chunk + 5 * chunk + 255) & ~255u;  // match lengths, then offset bytes
+__host__ __device__ inline uint64_t warp_scratch_bytes(uint64_t max_ntok) {
+  return (4 * (max_ntok + 1) * 3 + 5 * max_ntok + 255) & ~255ull;
 }
 
-__device__ inline WarpMem carve(uint8_t* base, uint32_t chunk) {
+__device__ inline WarpMem carve(uint8_t* base, uint32_t window) {
   WarpMem m;
   m.lut = reinterpret_cast<Lut*>(base);
   m.ring = base + sizeof(Lut);
   m.tdst = reinterpret_cast<uint32_t*>(m.ring + 3 * kRing);
-  m.tlit = m.tdst + (chunk + 1);
-  m.esc = reinterpret_cast<uint16_t*>(m.tlit + (chunk + 1));
+  m.tlit = m.tdst + (window + 1);
+  m.esc = reinterpret_cast<uint16_t*>(m.ring + 3 * kRing + window_area_bytes(window));
   return m;
+}
+
+__device__ inline TokRec tok_records(uint8_t* base, uint64_t max_ntok) {
+  TokRec r;
+  r.tdst = reinterpret_cast<uint32_t*>(base);
+  r.tlit = r.tdst + (max_ntok + 1);
+  r.tml = r.tlit + (max_ntok + 1);
+  r.offb = reinterpret_cast<uint8_t*>(r.tml + (max_ntok + 1));
+  return r;
 }
 
 template <bool SEEK>
@@ -217,44 +246,67 @@ __device__ __forceinline__ void fail(const DecodeArgs& a, bool& ok, ace_status c
   ok = false;
 }
 
-// Copies one match, sequential LZ77 semantics: dst[i] = out[S + i] in order,
-// so a source overlapping its destination repeats.  dst is the destination
-// inside the block being decoded.
+// Source byte i of a match (sequential LZ77 semantics): with distance
+// d = D - S, byte i of the destination equals byte S + (i mod d) when the
+// source overlaps the destination (d < len), and S + i otherwise; either way
+// every byte read precedes D and is final when the copy starts.
+__device__ __forceinline__ uint64_t src_index(uint64_t S, uint64_t d, uint32_t len, uint32_t i) {
+  return d >= len ? S + i : S + (i % (uint32_t)d);
+}
+
+// One lane copies one match.  Loads go in batches of 8 independent byte
+// loads before their stores, so a batch costs one memory round trip.
 template <bool SEEK>
-__device__ __forceinline__ void copy_match_lane(const DecodeArgs& a, uint8_t* dst, uint64_t S, uint32_t len) {
-  if (!SEEK) {
-    const uint8_t* src = a.out + S;
-    for (uint32_t i = 0; i < len; i++) dst[i] = __ldcg(src + i);
-  } else {
-    for (uint32_t i = 0; i < len; i++) dst[i] = __ldcg(Addr<true>::at(a, S + i));
+__device__ __forceinline__ void copy_match_lane(const DecodeArgs& a, uint8_t* dst, uint64_t D, uint64_t S,
+                                                uint32_t len) {
+  const uint64_t d = D - S;
+  for (uint32_t i0 = 0; i0 < len; i0 += 8) {
+    uint8_t v[8];
+#pragma unroll
+    for (uint32_t u = 0; u < 8; u++)
+      if (i0 + u < len) v[u] = __ldcg(Addr<SEEK>::at(a, src_index(S, d, len, i0 + u)));
+#pragma unroll
+    for (uint32_t u = 0; u < 8; u++)
+      if (i0 + u < len) dst[i0 + u] = v[u];
   }
 }
 
-// The same by a whole warp: with distance d = D - S, byte i comes from
-// S + (i mod d), all of which precede D and are complete.
+// The whole warp copies one match, four independent byte loads per lane per
+// round trip (128 bytes).
 template <bool SEEK>
 __device__ __forceinline__ void copy_match_warp(const DecodeArgs& a, uint8_t* dst, uint64_t D, uint64_t S,
                                                 uint32_t len, uint32_t lane) {
-  uint64_t d = D - S;
-  if (d >= len) {
-    for (uint32_t i = lane; i < len; i += 32) dst[i] = __ldcg(Addr<SEEK>::at(a, S + i));
-  } else {
-    uint32_t dd = (uint32_t)d;
-    for (uint32_t i = lane; i < len; i += 32) dst[i] = __ldcg(Addr<SEEK>::at(a, S + i % dd));
+  const uint64_t d = D - S;
+  for (uint32_t i0 = 0; i0 < len; i0 += 128) {
+    uint8_t v[4];
+#pragma unroll
+    for (uint32_t u = 0; u < 4; u++) {
+      uint32_t i = i0 + 32 * u + lane;
+      if (i < len) v[u] = __ldcg(Addr<SEEK>::at(a, src_index(S, d, len, i)));
+    }
+#pragma unroll
+    for (uint32_t u = 0; u < 4; u++) {
+      uint32_t i = i0 + 32 * u + lane;
+      if (i < len) dst[i] = v[u];
+    }
   }
 }
 
-enum { LUT_NONE = 3 };
+__device__ __forceinline__ uint64_t read_src(const uint8_t* q, uint32_t w) {
+  uint64_t S = (uint64_t)q[0] | ((uint64_t)q[1] << 8) | ((uint64_t)q[2] << 16) | ((uint64_t)q[3] << 24);
+  if (w == 5) S |= (uint64_t)q[4] << 32;
+  return S;
+}
 
 // Decodes one block through both layers (Section 3 entry point, then the
-// Section 2 match layer) into its place.  Tokens are processed in chunks:
-// the length codes of a chunk are decoded and parsed into token positions,
-// then its offsets, then its literals go straight to their output positions,
-// then its matches are resolved.  Returns false if the block is corrupt or a
-// wait gave up (the error is recorded).
+// Section 2 match layer) into its place, in four phases: the length stream
+// (parsed into token records), the offset stream, the literals (placed
+// straight at their output positions), and the matches (resolved in
+// dependency waves).  Each phase builds its stream's tables once.  Returns
+// false if the block is corrupt or a wait gave up (the error is recorded).
 template <bool SEEK>
-__device__ bool decode_block(const DecodeArgs& a, const WarpMem& m, uint32_t* g_tml, uint8_t* g_offb, uint32_t b,
-                             uint32_t lane, uint32_t epoch) {
+__device__ bool decode_block(const DecodeArgs& a, const WarpMem& m, const TokRec& g, uint32_t b, uint32_t lane,
+                             uint32_t epoch) {
   bool ok = true;
   const uint32_t* dw = reinterpret_cast<const uint32_t*>(a.dir + b);
   uint32_t dv = lane < 16 ? __ldg(dw + lane) : 0u;
@@ -273,96 +325,100 @@ __device__ bool decode_block(const DecodeArgs& a, const WarpMem& m, uint32_t* g_
     if (!stream_open(a.arc + a.payload_off + soff, sbytes, nsym, m.ring + k * kRing, st[k], lane))
       fail(a, ok, ACE_E_CORRUPT, b, 20 + k, lane);
   }
-  if (!ok) return false;
+  if (!ok || ntok > a.max_ntok) {
+    fail(a, ok, ACE_E_CORRUPT, b, 23, lane);
+    cp_async_wait<0>();
+    __syncwarp();
+    return false;
+  }
   cp_async_wait<2>();
   __syncwarp();
   Stream& sl = st[ACE_S_LIT];
   Stream& sn = st[ACE_S_LEN];
   Stream& so = st[ACE_S_OFF];
-  uint32_t loaded = LUT_NONE;
-  auto use_lut = [&](uint32_t k, Stream& s) -> bool {
-    if (loaded == k) return true;
-    loaded = k;
-    return lut_build(s, *m.lut, lane);
-  };
+  uint8_t* rl = m.ring + ACE_S_LIT * kRing;
+  uint8_t* rn = m.ring + ACE_S_LEN * kRing;
+  uint8_t* ro = m.ring + ACE_S_OFF * kRing;
 
-  bool bad = false;
-  // escape values at the head of the length stream
-  if (nesc) {
-    if (!use_lut(ACE_S_LEN, sn)) fail(a, ok, ACE_E_CORRUPT, b, 29, lane);
-    uint8_t* escb = reinterpret_cast<uint8_t*>(m.esc);
-    while (ok && sn.next < 2 * nesc) {
-      bool act;
-      uint32_t i;
-      uint32_t s = rans_round(sn, m.ring + ACE_S_LEN * kRing, *m.lut, 2 * nesc, lane, lt, act, i, bad);
-      if (act) escb[i] = (uint8_t)s;
-    }
-    __syncwarp();
+  // ---- lengths: escape values, then two codes per token
+  if (!lut_build(sn, *m.lut, lane)) fail(a, ok, ACE_E_CORRUPT, b, 30, lane);
+  uint8_t* escb = reinterpret_cast<uint8_t*>(m.esc);
+  while (ok && sn.next < 2 * nesc) {
+    bool act;
+    uint32_t i;
+    uint32_t s = rans_round(sn, rn, *m.lut, 2 * nesc, lane, lt, act, i);
+    if (act) escb[i] = (uint8_t)s;
   }
-  if (bad) fail(a, ok, ACE_E_CORRUPT, b, 30, lane);
-
+  __syncwarp();
   uint32_t out_pos = 0, lit_pos = 0, esc_rank = 0;
-  for (uint32_t t0 = 0; t0 < ntok && ok; t0 += a.chunk) {
-    const uint32_t tc = min(a.chunk, ntok - t0);
-    const uint32_t nm = (t0 + tc == ntok) ? tc - 1 : tc;  // matches in this chunk
-    // length codes: two per token; parse values, escapes and running positions
-    if (!use_lut(ACE_S_LEN, sn)) fail(a, ok, ACE_E_CORRUPT, b, 31, lane);
-    const uint32_t cbase = 2 * nesc, cend = cbase + 2 * (t0 + tc);
-    while (ok && sn.next < cend) {
+  bool bad = false;
+  const uint32_t cbase = 2 * nesc, cend = cbase + 2 * ntok;
+  while (ok && sn.next < cend) {
+    bool act;
+    uint32_t i;
+    uint32_t s = rans_round(sn, rn, *m.lut, cend, lane, lt, act, i);
+    bool e = act && s == 255;
+    uint32_t eb = __ballot_sync(kFull, e);
+    uint32_t r = esc_rank + __popc(eb & lt);
+    uint32_t v = s;
+    if (e) {
+      if (r < nesc) v = 255u + m.esc[r];
+      else bad = true;
+    }
+    esc_rank += __popc(eb);
+    uint32_t lr = __shfl_sync(kFull, v, lane & ~1u), ml = __shfl_sync(kFull, v, lane | 1u);
+    bool own = act && !(lane & 1);  // codes start at an even index: pairs never straddle rounds
+    uint32_t to = own ? lr + ml : 0u, tl = own ? lr : 0u;
+    uint32_t io = warp_incl_sum(to, lane), il = warp_incl_sum(tl, lane);
+    if (own) {
+      uint32_t t = (i - cbase) >> 1;
+      g.tdst[t] = out_pos + io - to;
+      g.tlit[t] = lit_pos + il - tl;
+      g.tml[t] = ml;
+      if (t == ntok - 1 && ml) bad = true;  // the block's last token carries no match
+    }
+    out_pos += __shfl_sync(kFull, io, 31);
+    lit_pos += __shfl_sync(kFull, il, 31);
+    if (out_pos > blen) bad = true;
+  }
+  if (lane == 0) {
+    g.tdst[ntok] = out_pos;
+    g.tlit[ntok] = lit_pos;
+  }
+  bad |= out_pos != blen || lit_pos != sl.nsym || esc_rank != nesc;
+  if (__any_sync(kFull, bad)) fail(a, ok, ACE_E_CORRUPT, b, 32, lane);
+
+  // ---- absolute offsets: off_width bytes for every token but the last
+  const uint32_t nm = ntok - 1;
+  if (ok && nm) {
+    if (!lut_build(so, *m.lut, lane)) fail(a, ok, ACE_E_CORRUPT, b, 33, lane);
+    const uint32_t oend = w * nm;
+    while (ok && so.next < oend) {
       bool act;
       uint32_t i;
-      uint32_t s = rans_round(sn, m.ring + ACE_S_LEN * kRing, *m.lut, cend, lane, lt, act, i, bad);
-      bool e = act && s == 255;
-      uint32_t eb = __ballot_sync(kFull, e);
-      uint32_t r = esc_rank + __popc(eb & lt);
-      uint32_t v = s;
-      if (e) {
-        if (r < nesc) v = 255u + m.esc[r];
-        else bad = true;
-      }
-      esc_rank += __popc(eb);
-      uint32_t lr = __shfl_sync(kFull, v, lane & ~1u), ml = __shfl_sync(kFull, v, lane | 1u);
-      bool own = act && !(lane & 1);  // codes start at an even index: pairs never straddle rounds
-      uint32_t to = own ? lr + ml : 0u, tl = own ? lr : 0u;
-      uint32_t io = warp_incl_sum(to, lane), il = warp_incl_sum(tl, lane);
-      if (own) {
-        uint32_t t = ((i - cbase) >> 1) - t0;
-        m.tdst[t] = out_pos + io - to;
-        m.tlit[t] = lit_pos + il - tl;
-        g_tml[t] = ml;
-        if (t0 + t == ntok - 1 && ml) bad = true;  // the block's last token carries no match
-      }
-      out_pos += __shfl_sync(kFull, io, 31);
-      lit_pos += __shfl_sync(kFull, il, 31);
+      uint32_t s = rans_round(so, ro, *m.lut, oend, lane, lt, act, i);
+      if (act) g.offb[i] = (uint8_t)s;
     }
-    if (lane == 0) {
-      m.tdst[tc] = out_pos;
-      m.tlit[tc] = lit_pos;
-    }
-    bad |= out_pos > blen || lit_pos > sl.nsym;
-    if (__any_sync(kFull, bad)) fail(a, ok, ACE_E_CORRUPT, b, 32, lane);
-    if (!ok) break;
-    // absolute offsets of this chunk's matches, off_width bytes each
-    if (nm) {
-      if (!use_lut(ACE_S_OFF, so)) fail(a, ok, ACE_E_CORRUPT, b, 33, lane);
-      const uint32_t obase0 = w * t0, oend = obase0 + w * nm;
-      while (ok && so.next < oend) {
-        bool act;
-        uint32_t i;
-        uint32_t s = rans_round(so, m.ring + ACE_S_OFF * kRing, *m.lut, oend, lane, lt, act, i, bad);
-        if (act) g_offb[i - obase0] = (uint8_t)s;
+  }
+  __syncwarp();
+
+  // ---- literals: literal i lands at its token's run start plus its offset in
+  // the run; token positions come through a shared-memory window
+  if (ok && lit_pos) {
+    if (!lut_build(sl, *m.lut, lane)) fail(a, ok, ACE_E_CORRUPT, b, 35, lane);
+    for (uint32_t w0 = 0; ok && w0 < ntok; w0 += a.window) {
+      const uint32_t wn = min(a.window, ntok - w0);
+      for (uint32_t k = lane; k <= wn; k += 32) {
+        m.tdst[k] = g.tdst[w0 + k];
+        m.tlit[k] = g.tlit[w0 + k];
       }
-      if (__any_sync(kFull, bad)) fail(a, ok, ACE_E_CORRUPT, b, 34, lane);
-    }
-    __syncwarp();
-    // literals land at their token's run start plus their offset in the run
-    if (ok && lit_pos > sl.next) {
-      if (!use_lut(ACE_S_LIT, sl)) fail(a, ok, ACE_E_CORRUPT, b, 35, lane);
+      __syncwarp();
+      const uint32_t lend = m.tlit[wn];
       uint32_t tp = 0, cur_lit = m.tlit[0], cur_dst = m.tdst[0], nxt_lit = m.tlit[1];
-      while (ok && sl.next < lit_pos) {
+      while (sl.next < lend) {
         bool act;
         uint32_t i;
-        uint32_t s = rans_round(sl, m.ring + ACE_S_LIT * kRing, *m.lut, lit_pos, lane, lt, act, i, bad);
+        uint32_t s = rans_round(sl, rl, *m.lut, lend, lane, lt, act, i);
         if (act) {
           while (nxt_lit <= i) {
             tp++;
@@ -373,20 +429,27 @@ __device__ bool decode_block(const DecodeArgs& a, const WarpMem& m, uint32_t* g_
           obase[cur_dst + (i - cur_lit)] = (uint8_t)s;
         }
       }
-      if (__any_sync(kFull, bad)) fail(a, ok, ACE_E_CORRUPT, b, 36, lane);
+      __syncwarp();
     }
-    if (!ok) break;
-    __syncwarp();
+  }
 
-    // match layer: wait for the source blocks, then resolve in dependency waves
+  // ---- matches, in groups whose records sit in shared memory (the window)
+  uint64_t* gS = reinterpret_cast<uint64_t*>(m.tdst);              // [kMatchGroup] sources
+  uint32_t* gD = reinterpret_cast<uint32_t*>(gS + kMatchGroup);     // [kMatchGroup] destinations in the block
+  uint32_t* gL = gD + kMatchGroup;                                  // [kMatchGroup] lengths
+  for (uint32_t t0 = 0; ok && t0 < nm; t0 += kMatchGroup) {
+    const uint32_t gn = min(kMatchGroup, nm - t0);
     bool timeout = false;
-    for (uint32_t t = lane; t < nm; t += 32) {
-      uint32_t ml = g_tml[t];
+    for (uint32_t j = lane; j < gn; j += 32) {
+      uint32_t t = t0 + j;
+      uint32_t ml = g.tml[t];
+      uint64_t S = read_src(g.offb + w * t, w);
+      uint32_t dl = g.tdst[t + 1] - ml;
+      uint64_t D = bstart + dl;
+      gS[j] = S;
+      gD[j] = dl;
+      gL[j] = ml;
       if (!ml) continue;
-      const uint8_t* q = g_offb + w * t;
-      uint64_t S = (uint64_t)q[0] | ((uint64_t)q[1] << 8) | ((uint64_t)q[2] << 16) | ((uint64_t)q[3] << 24);
-      if (w == 5) S |= (uint64_t)q[4] << 32;
-      uint64_t D = bstart + m.tdst[t + 1] - ml;
       if (S >= D) {
         bad = true;
         continue;
@@ -399,62 +462,51 @@ __device__ bool decode_block(const DecodeArgs& a, const WarpMem& m, uint32_t* g_
     if (__any_sync(kFull, bad)) fail(a, ok, ACE_E_CORRUPT, b, 37, lane);
     if (__any_sync(kFull, timeout)) fail(a, ok, ACE_E_TIMEOUT, b, 38, lane);
     if (!ok) break;
-    // each lane owns matches lane, lane + 32, ...; pending bits track them
+    __syncwarp();
+    // lane owns matches j = lane + 32 q, q < 4; pending bits track them
     uint32_t pend = 0;
-    for (uint32_t j = 0, t = lane; t < nm; j++, t += 32)
-      if (g_tml[t]) pend |= 1u << j;
+    for (uint32_t q = 0, j = lane; j < gn; q++, j += 32)
+      if (gL[j]) pend |= 1u << q;
     while (__any_sync(kFull, pend != 0)) {
       // W: destination of the first pending match; a match whose read range
       // ends at or before W reads only finished bytes
-      uint64_t myW = ~0ull;
-      for (uint32_t j = 0; j < 32; j++)
-        if ((pend >> j) & 1) {
-          uint32_t t = lane + 32 * j;
-          myW = bstart + m.tdst[t + 1] - g_tml[t];
-          break;
-        }
-      uint64_t W = warp_min64(myW);
+      uint32_t myW = 0xffffffffu;
+      if (pend) myW = gD[lane + 32 * (__ffs(pend) - 1)];
+      const uint64_t W = bstart + warp_min(myW);
       uint32_t go = 0;
-      for (uint32_t j = 0; j < 32; j++)
-        if ((pend >> j) & 1) {
-          uint32_t t = lane + 32 * j;
-          uint32_t ml = g_tml[t];
-          const uint8_t* q = g_offb + w * t;
-          uint64_t S = (uint64_t)q[0] | ((uint64_t)q[1] << 8) | ((uint64_t)q[2] << 16) | ((uint64_t)q[3] << 24);
-          if (w == 5) S |= (uint64_t)q[4] << 32;
-          uint64_t D = bstart + m.tdst[t + 1] - ml;
-          uint64_t rend = S + min((uint64_t)ml, D - S);
-          if (rend <= W) {
-            go |= 1u << j;
-            if (ml <= 64) {  // short: the owning lane copies it
-              copy_match_lane<SEEK>(a, obase + (D - bstart), S, ml);
-              go &= ~(1u << j);
-              pend &= ~(1u << j);
-            }
+      for (uint32_t rest = pend; rest; rest &= rest - 1) {
+        uint32_t q = __ffs(rest) - 1, j = lane + 32 * q;
+        uint64_t S = gS[j], D = bstart + gD[j];
+        if (S + min((uint64_t)gL[j], D - S) <= W) go |= 1u << q;
+      }
+      const uint32_t nready = __reduce_add_sync(kFull, __popc(go));
+      if (nready > 4) {  // many independent matches: each lane copies its own
+        for (uint32_t rest = go; rest; rest &= rest - 1) {
+          uint32_t q = __ffs(rest) - 1, j = lane + 32 * q;
+          uint32_t ml = gL[j];
+          if (ml <= 64) {
+            copy_match_lane<SEEK>(a, obase + gD[j], bstart + gD[j], gS[j], ml);
+            go &= ~(1u << q);
+            pend &= ~(1u << q);
           }
         }
-      uint32_t any_long;
-      while ((any_long = __ballot_sync(kFull, go != 0)) != 0) {  // long: the whole warp
-        uint32_t src_lane = __ffs(any_long) - 1;
-        uint32_t j = __ffs(__shfl_sync(kFull, go, src_lane)) - 1;
-        uint32_t t = src_lane + 32 * j;
-        uint32_t ml = g_tml[t];
-        const uint8_t* q = g_offb + w * t;
-        uint64_t S = (uint64_t)q[0] | ((uint64_t)q[1] << 8) | ((uint64_t)q[2] << 16) | ((uint64_t)q[3] << 24);
-        if (w == 5) S |= (uint64_t)q[4] << 32;
-        uint64_t D = bstart + m.tdst[t + 1] - ml;
-        copy_match_warp<SEEK>(a, obase + (D - bstart), D, S, ml, lane);
+      }
+      uint32_t any;
+      while ((any = __ballot_sync(kFull, go != 0)) != 0) {  // few or long: the whole warp
+        uint32_t src_lane = __ffs(any) - 1;
+        uint32_t q = __ffs(__shfl_sync(kFull, go, src_lane)) - 1;
+        uint32_t j = src_lane + 32 * q;
+        copy_match_warp<SEEK>(a, obase + gD[j], bstart + gD[j], gS[j], gL[j], lane);
         if (lane == src_lane) {
-          go &= ~(1u << j);
-          pend &= ~(1u << j);
+          go &= ~(1u << q);
+          pend &= ~(1u << q);
         }
       }
       __syncwarp();
     }
   }
   if (ok) {
-    bool fin = out_pos == blen && lit_pos == sl.nsym && esc_rank == nesc;
-    fin = fin && stream_finished(st[0]) && stream_finished(st[1]) && stream_finished(st[2]);
+    bool fin = stream_finished(st[0]) && stream_finished(st[1]) && stream_finished(st[2]);
     if (!__all_sync(kFull, fin)) fail(a, ok, ACE_E_CORRUPT, b, 40, lane);
   }
   cp_async_wait<0>();  // no ring fill may land after the next block reuses the rings
@@ -466,10 +518,9 @@ template <bool SEEK>
 __global__ void __launch_bounds__(256, 3) decode_kernel(DecodeArgs a) {
   extern __shared__ __align__(16) uint8_t smem[];
   const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  WarpMem m = carve(smem + (size_t)wid * a.warp_smem, a.chunk);
-  uint8_t* ws = a.warp_scratch + (size_t)(blockIdx.x * (blockDim.x >> 5) + wid) * a.warp_scratch_bytes;
-  uint32_t* g_tml = reinterpret_cast<uint32_t*>(ws);
-  uint8_t* g_offb = ws + 4 * a.chunk;
+  WarpMem m = carve(smem + (size_t)wid * a.warp_smem, a.window);
+  TokRec g = tok_records(a.warp_scratch + (size_t)(blockIdx.x * (blockDim.x >> 5) + wid) * a.warp_scratch_bytes,
+                         a.max_ntok);
   const uint32_t epoch = *(volatile uint32_t*)&a.sh->epoch;
   const uint32_t n_items = SEEK ? *(volatile uint32_t*)&a.sh->n_work : a.n_items;
   while (true) {
@@ -478,7 +529,7 @@ __global__ void __launch_bounds__(256, 3) decode_kernel(DecodeArgs a) {
     it = __shfl_sync(kFull, it, 0);
     if (it >= n_items) break;
     uint32_t b = __ldg(a.items + it);
-    bool ok = decode_block<SEEK>(a, m, g_tml, g_offb, b, lane, epoch);
+    bool ok = decode_block<SEEK>(a, m, g, b, lane, epoch);
     if (SEEK && ok) {
       // copy the part of this block inside [coord, coord + len) to the caller
       uint64_t bs = (uint64_t)b << a.log2B, be = min(bs + ((uint64_t)1 << a.log2B), a.total);
@@ -648,9 +699,12 @@ struct ace_index {
   const uint32_t* d_dep_iv;
   uint64_t n_iv;
   uint32_t n_levels;
+  uint32_t max_ntok;
   int device;
   int num_sms;
   ace_tune tune;
+  // occupancy of the decode kernels, per (seek?, warps per CTA, chunk)
+  mutable int occ_cache[2][9][9];
 };
 
 namespace {
@@ -679,15 +733,15 @@ struct ScratchLayout {
   uint64_t n_warps;  // per-warp token regions available
 };
 
-constexpr uint32_t kMaxChunk = 256;
+constexpr uint32_t kMaxWindow = 256;
 constexpr uint32_t kMaxWarpsPerCta = 8;  // the decode kernel's launch bounds: 256 threads
-constexpr uint32_t kMaxWarpsPerSM = 64;
+constexpr uint32_t kMaxWarpsPerSM = 32;  // per-warp token regions provisioned per SM
 
 // One layout serves every call on a scratch buffer, so whole decodes and
 // seeks may share it: header, ready flags, the seek's slot map, work list,
 // closure marks and frontiers, the per-warp token regions, then (for seeks)
 // the block slots.
-ScratchLayout scratch_layout(uint64_t nb, uint32_t log2B, uint64_t max_seek, int num_sms) {
+ScratchLayout scratch_layout(uint64_t nb, uint32_t log2B, uint64_t max_seek, int num_sms, uint64_t max_ntok) {
   ScratchLayout L;
   uint64_t o = sizeof(ScratchHdr);
   L.ready = o;
@@ -705,7 +759,7 @@ ScratchLayout scratch_layout(uint64_t nb, uint32_t log2B, uint64_t max_seek, int
   uint64_t items = std::max<uint64_t>(nb, max_seek);
   L.n_warps = std::min<uint64_t>((uint64_t)num_sms * kMaxWarpsPerSM, items + 16);
   L.warps = o;
-  o = align256(o + L.n_warps * warp_scratch_bytes(kMaxChunk));
+  o = align256(o + L.n_warps * warp_scratch_bytes(max_ntok));
   L.slots = o;
   o = align256(o + (max_seek << log2B));
   L.total = o;
@@ -749,17 +803,27 @@ ace_status plan_launch(const ace_index* idx, const ace_tune* tune, uint64_t max_
   ace_tune t = tune ? *tune : idx->tune;
   L->warps = t.warps_per_cta ? t.warps_per_cta : 4;
   L->chunk = t.chunk_tokens ? t.chunk_tokens : 128;
-  if (L->warps > kMaxWarpsPerCta || (L->chunk & 31) || L->chunk > kMaxChunk) return ACE_E_INVAL;
+  if (L->warps > kMaxWarpsPerCta || (L->chunk & 31) || L->chunk > kMaxWindow) return ACE_E_INVAL;
   L->timeout = t.wait_timeout_ns ? t.wait_timeout_ns : kDefaultTimeoutNs;
   L->smem_per_warp = warp_smem_bytes(L->chunk, esc_cap(idx->h.log2_block));
   size_t smem = (size_t)L->warps * L->smem_per_warp;
-  int optin = 0;
-  CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, idx->device));
-  if (smem > (size_t)optin) return ACE_E_INVAL;  // this many warps with this chunk do not fit one CTA
-  CUDA_TRY(cudaFuncSetAttribute(decode_kernel<SEEK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  int per_sm = 0;
-  CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, decode_kernel<SEEK>, 32 * L->warps, smem));
-  if (per_sm < 1) return ACE_E_INVAL;
+  int& cached = idx->occ_cache[SEEK][L->warps][L->chunk / 32];
+  if (cached == 0) {
+    int optin = 0;
+    CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, idx->device));
+    if (smem > (size_t)optin) {
+      cached = -1;  // this many warps with this chunk do not fit one CTA
+    } else {
+      // allow every configuration up to the opt-in limit, so launches of
+      // other cached configurations stay valid
+      CUDA_TRY(cudaFuncSetAttribute(decode_kernel<SEEK>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+      int occ = 0;
+      CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, decode_kernel<SEEK>, 32 * L->warps, smem));
+      cached = occ > 0 ? occ : -1;
+    }
+  }
+  if (cached < 0) return ACE_E_INVAL;
+  int per_sm = cached;
   if (t.ctas_per_sm && (int)t.ctas_per_sm < per_sm) per_sm = (int)t.ctas_per_sm;
   L->ctas_per_sm = (uint32_t)per_sm;
   uint64_t grid = (uint64_t)idx->num_sms * per_sm;
@@ -859,6 +923,7 @@ ace_status ace_index_build(const void* d_archive, uint64_t archive_bytes, const 
         cudaStreamSynchronize(s) != cudaSuccess)
       return bail(ACE_E_CUDA);
     if (ih.status) return bail((ace_status)ih.status);
+    idx->max_ntok = ih.max_ntok;
     levels_kernel<<<1, 1024, 0, s>>>(a);
     level_hist_kernel<<<g, 256, 0, s>>>(a);
     level_scan_kernel<<<1, 1024, 0, s>>>(a);
@@ -888,7 +953,7 @@ ace_status ace_index_info(const ace_index* idx, ace_info* info) {
 
 ace_status ace_index_set_tune(ace_index* idx, const ace_tune* tune) {
   if (!idx) return ACE_E_INVAL;
-  if (tune && (tune->warps_per_cta > kMaxWarpsPerCta || (tune->chunk_tokens & 31) || tune->chunk_tokens > kMaxChunk))
+  if (tune && (tune->warps_per_cta > kMaxWarpsPerCta || (tune->chunk_tokens & 31) || tune->chunk_tokens > kMaxWindow))
     return ACE_E_INVAL;
   idx->tune = tune ? *tune : ace_tune{};
   return ACE_OK;
@@ -901,13 +966,13 @@ ace_status ace_index_free(ace_index* idx) {
 
 ace_status ace_scratch_size(const ace_index* idx, uint64_t max_seek_blocks, uint64_t* bytes) {
   if (!idx || !bytes) return ACE_E_INVAL;
-  *bytes = scratch_layout(idx->h.n_blocks, idx->h.log2_block, max_seek_blocks, idx->num_sms).total;
+  *bytes = scratch_layout(idx->h.n_blocks, idx->h.log2_block, max_seek_blocks, idx->num_sms, idx->max_ntok).total;
   return ACE_OK;
 }
 
 ace_status ace_scratch_init(const ace_index* idx, void* d_scratch, uint64_t scratch_bytes, cudaStream_t s) {
   if (!idx || !d_scratch || !aligned(d_scratch, 256)) return ACE_E_INVAL;
-  ScratchLayout L0 = scratch_layout(idx->h.n_blocks, idx->h.log2_block, 0, idx->num_sms);
+  ScratchLayout L0 = scratch_layout(idx->h.n_blocks, idx->h.log2_block, 0, idx->num_sms, idx->max_ntok);
   if (scratch_bytes < L0.total) return ACE_E_NOMEM;
   // header, ready flags, and (when present) slot map, work list and marks
   uint64_t clear = L0.warps;
@@ -920,7 +985,7 @@ ace_status ace_decode_all(const ace_index* idx, void* d_out, uint64_t out_bytes,
   if (!idx || !d_scratch || (!d_out && idx->h.total_size)) return ACE_E_INVAL;
   if (!aligned(d_scratch, 256)) return ACE_E_INVAL;
   if (out_bytes < idx->h.total_size) return ACE_E_NOMEM;
-  ScratchLayout SL = scratch_layout(idx->h.n_blocks, idx->h.log2_block, 0, idx->num_sms);
+  ScratchLayout SL = scratch_layout(idx->h.n_blocks, idx->h.log2_block, 0, idx->num_sms, idx->max_ntok);
   if (scratch_bytes < SL.total) return ACE_E_NOMEM;
   if (!idx->h.n_blocks) return ACE_OK;
   Launch L;
@@ -935,7 +1000,8 @@ ace_status ace_decode_all(const ace_index* idx, void* d_out, uint64_t out_bytes,
   a.nb = idx->h.n_blocks;
   a.log2B = idx->h.log2_block;
   a.w = idx->h.off_width;
-  a.chunk = L.chunk;
+  a.window = L.chunk;
+  a.max_ntok = idx->max_ntok;
   a.esc_cap = esc_cap(a.log2B);
   a.warp_smem = L.smem_per_warp;
   a.n_items = (uint32_t)idx->h.n_blocks;
@@ -945,7 +1011,7 @@ ace_status ace_decode_all(const ace_index* idx, void* d_out, uint64_t out_bytes,
   a.ready = reinterpret_cast<uint32_t*>(static_cast<uint8_t*>(d_scratch) + SL.ready);
   a.timeout_ns = L.timeout;
   a.warp_scratch = static_cast<uint8_t*>(d_scratch) + SL.warps;
-  a.warp_scratch_bytes = warp_scratch_bytes(kMaxChunk);
+  a.warp_scratch_bytes = warp_scratch_bytes(idx->max_ntok);
   begin_call_kernel<<<1, 1, 0, s>>>(sh);
   decode_kernel<false><<<L.grid, 32 * L.warps, (size_t)L.warps * L.smem_per_warp, s>>>(a);
   CUDA_TRY(cudaGetLastError());
@@ -959,13 +1025,11 @@ ace_status ace_seek(const ace_index* idx, uint64_t coord, uint64_t len, void* d_
   if (out_bytes < len) return ACE_E_NOMEM;
   uint64_t nb = idx->h.n_blocks;
   uint32_t log2B = idx->h.log2_block;
-  ScratchLayout S1 = scratch_layout(nb, log2B, 1, idx->num_sms);
+  ScratchLayout S1 = scratch_layout(nb, log2B, 1, idx->num_sms, idx->max_ntok);
   if (scratch_bytes < S1.total) return ACE_E_NOMEM;
-  uint64_t cap = (scratch_bytes - S1.slots) >> log2B;
-  uint64_t max_seek = cap;
-  while (max_seek > 1 && scratch_layout(nb, log2B, max_seek, idx->num_sms).total > scratch_bytes) max_seek--;
-  S1 = scratch_layout(nb, log2B, max_seek, idx->num_sms);
-  cap = (scratch_bytes - S1.slots) >> log2B;
+  // the layout before the slots does not depend on the slot count (a seek
+  // never decodes more than n_blocks blocks)
+  uint64_t cap = std::min<uint64_t>(nb, (scratch_bytes - S1.slots) >> log2B);
   uint64_t first = coord >> log2B, last = (coord + len - 1) >> log2B;
   if (last - first + 1 > cap) return ACE_E_NOMEM;
   uint8_t* base = static_cast<uint8_t*>(d_scratch);
@@ -995,7 +1059,8 @@ ace_status ace_seek(const ace_index* idx, uint64_t coord, uint64_t len, void* d_
   a.nb = nb;
   a.log2B = log2B;
   a.w = idx->h.off_width;
-  a.chunk = L.chunk;
+  a.window = L.chunk;
+  a.max_ntok = idx->max_ntok;
   a.esc_cap = esc_cap(log2B);
   a.warp_smem = L.smem_per_warp;
   a.items = c.work;
@@ -1008,7 +1073,7 @@ ace_status ace_seek(const ace_index* idx, uint64_t coord, uint64_t len, void* d_
   a.len = len;
   a.timeout_ns = L.timeout;
   a.warp_scratch = base + S1.warps;
-  a.warp_scratch_bytes = warp_scratch_bytes(kMaxChunk);
+  a.warp_scratch_bytes = warp_scratch_bytes(idx->max_ntok);
   decode_kernel<true><<<L.grid, 32 * L.warps, (size_t)L.warps * L.smem_per_warp, s>>>(a);
   CUDA_TRY(cudaGetLastError());
   return ACE_OK;

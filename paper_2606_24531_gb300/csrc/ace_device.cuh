@@ -33,7 +33,8 @@ struct IndexHdr {
   uint32_t err_block;
   uint32_t err_where;
   uint32_t n_levels;
-  uint32_t pad[60];
+  uint32_t max_ntok;   // most tokens in any block: sizes the per-warp token records
+  uint32_t pad[59];
 };
 static_assert(sizeof(IndexHdr) == 256, "index header");
 
@@ -258,13 +259,16 @@ __device__ __forceinline__ bool lut_build(const Stream& st, Lut& lut, uint32_t l
 
 // Decodes one round of up to 32 symbols of [st.next, end): symbol i is on
 // lane i mod 32 (interleaved rANS).  slot = x mod 4096, s = sym[slot],
-// x <- f_s floor(x / 4096) + slot - c_s, then x takes k in {0,1,2} bytes,
-// k = [x < 2^15] + [x < 2^23]; bytes are consumed in symbol order, so lane j
+// x <- f_s floor(x / 4096) + slot - c_s; then x takes k in {0,1,2} bytes,
+// k = [x < 2^23] + [x < 2^15].  Bytes are consumed in symbol order, so lane j
 // reads at the running position plus the bytes of lower lanes, high byte
-// first.  Sets act/i for this lane; sets bad (all lanes) if the stream runs
-// out of bytes.  Returns the symbol.
+// first.  Branch-free: every lane fetches the two candidate bytes and
+// selects.  Bytes read past the end of the stream come from the ring and are
+// harmless; the end-of-stream check (all bytes consumed, every state at L)
+// rejects a stream that needed them.  Sets act and i for this lane and
+// returns the symbol.
 __device__ __forceinline__ uint32_t rans_round(Stream& st, uint8_t* ring, const Lut& lut, uint32_t end,
-                                               uint32_t lane, uint32_t lt, bool& act, uint32_t& i, bool& bad) {
+                                               uint32_t lane, uint32_t lt, bool& act, uint32_t& i) {
   if (st.pos >= st.base + kSeg) {  // oldest segment consumed: refill it further on
     ring_issue(st, ring, st.base + kRing, lane);
     st.base += kSeg;
@@ -274,26 +278,19 @@ __device__ __forceinline__ uint32_t rans_round(Stream& st, uint8_t* ring, const 
   uint32_t base = st.next & ~31u;
   i = base + lane;
   act = i >= st.next && i < end;
-  uint32_t x = st.x, k = 0, s = 0;
-  if (act) {
-    uint32_t slot = x & (ACE_SCALE - 1);
-    s = lut.sym[slot];
-    uint32_t fc = lut.fc[s];
-    x = (fc >> 16) * (x >> ACE_SCALE_BITS) + slot - (fc & 0xffffu);
-    k = (x < (1u << 15)) + (x < ACE_RANS_L);
-  }
-  uint32_t b1 = __ballot_sync(kFull, k >= 1), b2 = __ballot_sync(kFull, k == 2);
-  uint32_t pre = __popc(b1 & lt) + __popc(b2 & lt);
-  uint32_t tot = __popc(b1) + __popc(b2);
-  if (st.pos + tot > st.nbytes) {
-    bad = true;
-  } else {
-    uint32_t p = st.pos + pre;
-    if (k >= 1) x = (x << 8) | ring[p & (kRing - 1)];
-    if (k == 2) x = (x << 8) | ring[(p + 1) & (kRing - 1)];
-  }
-  st.pos += tot;
-  if (act) st.x = x;
+  uint32_t x = st.x;
+  uint32_t slot = x & (ACE_SCALE - 1);
+  uint32_t s = lut.sym[slot];
+  uint32_t fc = lut.fc[s];
+  uint32_t xn = (fc >> 16) * (x >> ACE_SCALE_BITS) + slot - (fc & 0xffffu);
+  bool p1 = act && xn < ACE_RANS_L, p2 = act && xn < (1u << 15);
+  uint32_t b1 = __ballot_sync(kFull, p1), b2 = __ballot_sync(kFull, p2);
+  uint32_t p = st.pos + __popc(b1 & lt) + __popc(b2 & lt);
+  uint32_t c0 = ring[p & (kRing - 1)], c1 = ring[(p + 1) & (kRing - 1)];
+  uint32_t x1 = (xn << 8) | c0, x2 = (x1 << 8) | c1;
+  xn = p2 ? x2 : (p1 ? x1 : xn);
+  st.x = act ? xn : x;
+  st.pos += __popc(b1) + __popc(b2);
   st.next = min(base + 32, end);
   return s;
 }
