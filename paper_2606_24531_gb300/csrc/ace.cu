@@ -343,20 +343,15 @@ __device__ bool decode_block(const DecodeArgs& a, const WarpMem& m, const TokRec
   // ---- lengths: escape values, then two codes per token
   if (!lut_build(sn, *m.lut, lane)) fail(a, ok, ACE_E_CORRUPT, b, 30, lane);
   uint8_t* escb = reinterpret_cast<uint8_t*>(m.esc);
-  while (ok && sn.next < 2 * nesc) {
-    bool act;
-    uint32_t i;
-    uint32_t s = rans_round(sn, rn, *m.lut, 2 * nesc, lane, lt, act, i);
-    if (act) escb[i] = (uint8_t)s;
-  }
+  if (ok)
+    rans_run(sn, rn, *m.lut, 2 * nesc, lane, lt, [&](bool act, uint32_t i, uint32_t s) {
+      if (act) escb[i] = (uint8_t)s;
+    });
   __syncwarp();
   uint32_t out_pos = 0, lit_pos = 0, esc_rank = 0;
   bool bad = false;
   const uint32_t cbase = 2 * nesc, cend = cbase + 2 * ntok;
-  while (ok && sn.next < cend) {
-    bool act;
-    uint32_t i;
-    uint32_t s = rans_round(sn, rn, *m.lut, cend, lane, lt, act, i);
+  if (ok) rans_run(sn, rn, *m.lut, cend, lane, lt, [&](bool act, uint32_t i, uint32_t s) {
     bool e = act && s == 255;
     uint32_t eb = __ballot_sync(kFull, e);
     uint32_t r = esc_rank + __popc(eb & lt);
@@ -380,7 +375,7 @@ __device__ bool decode_block(const DecodeArgs& a, const WarpMem& m, const TokRec
     out_pos += __shfl_sync(kFull, io, 31);
     lit_pos += __shfl_sync(kFull, il, 31);
     if (out_pos > blen) bad = true;
-  }
+  });
   if (lane == 0) {
     g.tdst[ntok] = out_pos;
     g.tlit[ntok] = lit_pos;
@@ -393,12 +388,10 @@ __device__ bool decode_block(const DecodeArgs& a, const WarpMem& m, const TokRec
   if (ok && nm) {
     if (!lut_build(so, *m.lut, lane)) fail(a, ok, ACE_E_CORRUPT, b, 33, lane);
     const uint32_t oend = w * nm;
-    while (ok && so.next < oend) {
-      bool act;
-      uint32_t i;
-      uint32_t s = rans_round(so, ro, *m.lut, oend, lane, lt, act, i);
-      if (act) g.offb[i] = (uint8_t)s;
-    }
+    if (ok)
+      rans_run(so, ro, *m.lut, oend, lane, lt, [&](bool act, uint32_t i, uint32_t s) {
+        if (act) g.offb[i] = (uint8_t)s;
+      });
   }
   __syncwarp();
 
@@ -415,10 +408,7 @@ __device__ bool decode_block(const DecodeArgs& a, const WarpMem& m, const TokRec
       __syncwarp();
       const uint32_t lend = m.tlit[wn];
       uint32_t tp = 0, cur_lit = m.tlit[0], cur_dst = m.tdst[0], nxt_lit = m.tlit[1];
-      while (sl.next < lend) {
-        bool act;
-        uint32_t i;
-        uint32_t s = rans_round(sl, rl, *m.lut, lend, lane, lt, act, i);
+      rans_run(sl, rl, *m.lut, lend, lane, lt, [&](bool act, uint32_t i, uint32_t s) {
         if (act) {
           while (nxt_lit <= i) {
             tp++;
@@ -428,7 +418,7 @@ __device__ bool decode_block(const DecodeArgs& a, const WarpMem& m, const TokRec
           }
           obase[cur_dst + (i - cur_lit)] = (uint8_t)s;
         }
-      }
+      });
       __syncwarp();
     }
   }

@@ -188,6 +188,12 @@ __device__ __forceinline__ bool stream_open(const uint8_t* pay, uint32_t sbytes,
   st.head = head;
   st.nbytes = sbytes - head;
   for (uint32_t s = 0; s < kRing / kSeg; s++) ring_issue(st, ring, s * kSeg, lane);
+  // the frequency table (bytes 160 .. head) is read when the stream's tables
+  // are built: bring its lines into L1 now
+  if (lane < 5 && 128 + 128 * lane < head) {
+    const uint8_t* line = pay + 128 + 128 * lane;
+    asm volatile("prefetch.global.L1 [%0];" ::"l"(line));
+  }
   return true;
 }
 
@@ -293,6 +299,56 @@ __device__ __forceinline__ uint32_t rans_round(Stream& st, uint8_t* ring, const 
   st.pos += __popc(b1) + __popc(b2);
   st.next = min(base + 32, end);
   return s;
+}
+
+// A full round: st.next is a multiple of 32 and at least 32 symbols remain,
+// so every lane is active.
+__device__ __forceinline__ uint32_t rans_round_full(Stream& st, uint8_t* ring, const Lut& lut, uint32_t lt) {
+  if (st.pos >= st.base + kSeg) {
+    ring_issue(st, ring, st.base + kRing, threadIdx.x & 31);
+    st.base += kSeg;
+    cp_async_wait<2>();
+    __syncwarp();
+  }
+  uint32_t x = st.x;
+  uint32_t slot = x & (ACE_SCALE - 1);
+  uint32_t s = lut.sym[slot];
+  uint32_t fc = lut.fc[s];
+  uint32_t xn = (fc >> 16) * (x >> ACE_SCALE_BITS) + slot - (fc & 0xffffu);
+  bool p1 = xn < ACE_RANS_L, p2 = xn < (1u << 15);
+  uint32_t b1 = __ballot_sync(kFull, p1), b2 = __ballot_sync(kFull, p2);
+  uint32_t p = st.pos + __popc(b1 & lt) + __popc(b2 & lt);
+  uint32_t c0 = ring[p & (kRing - 1)], c1 = ring[(p + 1) & (kRing - 1)];
+  uint32_t x1 = (xn << 8) | c0, x2 = (x1 << 8) | c1;
+  st.x = p2 ? x2 : (p1 ? x1 : xn);
+  st.pos += __popc(b1) + __popc(b2);
+  st.next += 32;
+  return s;
+}
+
+// Decodes symbols [st.next, end), handing each to sink(act, i, s) per
+// round (act false on lanes without a symbol this round): a partial first
+// round up to the next multiple of 32, full rounds, then a partial last one.
+template <class Sink>
+__device__ __forceinline__ void rans_run(Stream& st, uint8_t* ring, const Lut& lut, uint32_t end, uint32_t lane,
+                                         uint32_t lt, Sink&& sink) {
+  if (st.next < end && ((st.next & 31) || end - st.next < 32)) {
+    bool act;
+    uint32_t i;
+    uint32_t s = rans_round(st, ring, lut, end, lane, lt, act, i);
+    sink(act, i, s);
+  }
+  while (end - st.next >= 32 && st.next < end) {
+    uint32_t i = st.next + lane;
+    uint32_t s = rans_round_full(st, ring, lut, lt);
+    sink(true, i, s);
+  }
+  if (st.next < end) {
+    bool act;
+    uint32_t i;
+    uint32_t s = rans_round(st, ring, lut, end, lane, lt, act, i);
+    sink(act, i, s);
+  }
 }
 
 // All symbols consumed, all bytes consumed and every state back at L.

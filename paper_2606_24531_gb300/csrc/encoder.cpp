@@ -196,7 +196,8 @@ void build_global(const uint8_t* in, uint64_t n, unsigned threads, Global& g) {
 struct Parser {
   static constexpr int kHashBits = 15;
   std::vector<int32_t> head, prev;
-  explicit Parser(uint32_t B) : head(1u << kHashBits), prev(B) {}
+  std::vector<uint32_t> copied;  // prefix count of block bytes written by matches
+  explicit Parser(uint32_t B) : head(1u << kHashBits), prev(B), copied(B + 1) {}
 };
 
 // Where a block may take match sources from: its own earlier bytes, and
@@ -244,23 +245,39 @@ void parse_block(const uint8_t* in, uint64_t n, uint64_t b, uint64_t bstart, uin
       ps.head[h] = (int32_t)(inserted - bstart);
     }
   };
+  // A candidate is "direct" when the bytes it reads inside this block were
+  // all literals: it then depends on no earlier match of the block, and the
+  // decoder resolves it in its first wave.  Near-equal direct candidates are
+  // preferred over longer ones that would chain match on match.
+  auto direct = [&](uint64_t q, uint64_t len, uint64_t p) {
+    if (q + len <= bstart) return true;
+    uint64_t lo = std::max(q, bstart) - bstart, hi = std::min(q + len, p) - bstart;
+    return ps.copied[hi] == ps.copied[lo];
+  };
   uint64_t p = bstart;
   uint32_t lit = 0;
+  ps.copied[0] = 0;
   while (p < bend) {
     insert_upto(p);
-    uint64_t best_len = 0, best_q = 0;
+    uint64_t best_len = 0, best_q = 0, dir_len = 0, dir_q = 0;
     uint64_t room = bend - p;
+    auto consider = [&](uint64_t q, uint64_t l) {
+      if (l > best_len || (l == best_len && l > 0 && q < best_q)) {
+        best_len = l;
+        best_q = q;
+      }
+      if ((l > dir_len || (l == dir_len && l > 0 && q < dir_q)) && direct(q, l, p)) {
+        dir_len = l;
+        dir_q = q;
+      }
+    };
     if (room >= min_match) {
       if (p + 4 <= bend) {  // repeats inside the block, most recent first
         uint32_t depth = 0;
         for (int32_t r = ps.head[hash4(in + p, Parser::kHashBits)]; r >= 0 && depth < max_chain;
              r = ps.prev[r], depth++) {
           uint64_t q = bstart + (uint64_t)r;
-          uint64_t l = common(in + q, in + p, room);
-          if (l > best_len || (l == best_len && q < best_q)) {
-            best_len = l;
-            best_q = q;
-          }
+          consider(q, common(in + q, in + p, room));
         }
       }
       for (int j = 0; j < kStride; j++) {  // earliest occurrence anywhere before p
@@ -270,17 +287,20 @@ void parse_block(const uint8_t* in, uint64_t n, uint64_t b, uint64_t bstart, uin
         if (q >= p) continue;
         uint64_t l = common(in + q, in + p, room);
         if (q < bstart) l = al.span(q, b, l);
-        if (l > best_len || (l == best_len && l > 0 && q < best_q)) {
-          best_len = l;
-          best_q = q;
-        }
+        consider(q, l);
       }
+    }
+    if (dir_len >= min_match && dir_len + std::max<uint64_t>(4, best_len / 8) >= best_len) {
+      best_len = dir_len;
+      best_q = dir_q;
     }
     if (best_len >= min_match) {
       toks.push_back({lit, (uint32_t)best_len, best_q});
       lit = 0;
+      for (uint64_t k = p; k < p + best_len; k++) ps.copied[k - bstart + 1] = ps.copied[k - bstart] + 1;
       p += best_len;
     } else {
+      ps.copied[p - bstart + 1] = ps.copied[p - bstart];
       lit++;
       p++;
     }
