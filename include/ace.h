@@ -236,6 +236,30 @@ ace_status ace_verify(const ace_index *idx, uint64_t coord, uint64_t len, void *
  * Asynchronous. */
 ace_status ace_fnv1a64(const void *d_p, uint64_t n, uint64_t *d_result, cudaStream_t s);
 
+/* ----------------------------------------------- seek without allocation */
+
+/*
+ * ace_seek without any device memory from the caller beyond the output:
+ * for callers that cannot allocate device memory at all (a host application
+ * that owns all device memory through its own pool, a plug-in inside such
+ * an application, a request thread that must never reach the allocator).
+ * The paper has no counterpart; it is a deployment convenience.
+ *
+ * Scratch comes from a fixed 32 MiB array in the library's device image,
+ * held on every GPU that loads the library until the process exits, and
+ * shared by every call on that device: calls that overlap on the GPU race,
+ * so order them (one stream, or events).  The first call on a device looks
+ * up the array's device address; make that first call before any stream
+ * capture.  The index's device must be current.  Archives whose per-block
+ * tables and token records do not fit, or requests covering more blocks
+ * than the remaining slots, return ACE_E_NOMEM.  Calls no allocator.
+ * Synchronises s and returns the seek's device-side status (ACE_OK,
+ * ACE_E_CORRUPT, ACE_E_TIMEOUT, ACE_E_NOMEM when the closure exceeds the
+ * slots); otherwise as ace_seek.
+ */
+ace_status ace_seek_noalloc(const ace_index *idx, uint64_t coord, uint64_t len, void *d_out,
+                            uint64_t out_bytes, cudaStream_t s);
+
 #ifdef __cplusplus
 }
 #endif

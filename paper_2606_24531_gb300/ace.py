@@ -78,6 +78,7 @@ _SIGS = {
     "ace_index_set_tune": ([_vp, _P(ace_tune)], _i32),
     "ace_verify": ([_vp, _u64, _u64, _vp, _u64, _u64, _u32, _vp, _u64, _P(ace_verify_report), _vp], _i32),
     "ace_fnv1a64": ([_vp, _u64, _vp, _vp], _i32),
+    "ace_seek_noalloc": ([_vp, _u64, _u64, _vp, _u64, _vp], _i32),
 }
 
 
@@ -233,3 +234,9 @@ def ace_verify(idx, coord, length, d_buf, guard_bytes, expected_fnv1a64, canary_
 
 def ace_fnv1a64(d_p, n, d_result, stream=None):
     _check(lib().ace_fnv1a64(_ptr(d_p), n, _ptr(d_result), _stream(stream)), "ace_fnv1a64")
+
+
+def ace_seek_noalloc(idx, coord, length, d_out, out_bytes, stream=None):
+    """Seek with the library's fixed device scratch (no caller scratch);
+    synchronous, returns the device-side status without raising."""
+    return lib().ace_seek_noalloc(idx, coord, length, _ptr(d_out), out_bytes, _stream(stream))

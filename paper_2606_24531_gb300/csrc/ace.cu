@@ -7,6 +7,7 @@
 #include <cstdint>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 
 #include "ace.h"
@@ -1135,6 +1136,118 @@ ace_status ace_verify(const ace_index* idx, uint64_t coord, uint64_t len, void* 
   rep->phase2_ok = rep->seek_status == ACE_OK && rep->fnv_after == expected;
   rep->phase3_ok = rep->guard_bad_before == 0 && rep->guard_bad_after == 0;
   return ACE_OK;
+}
+
+// -------------------------------------------------- seek without allocation
+//
+// Some callers cannot allocate device memory at all: a host application
+// that owns every byte of device memory through its own pool, a plug-in
+// loaded into such an application, or a latency-critical request thread
+// that must never reach the allocator.  ace_seek_noalloc serves them: it
+// takes its scratch from a fixed array that lives in this library's device
+// image, so the caller passes only the archive's index and the output.
+//
+// The array is kStaticScratchBytes (32 MiB) on every GPU that loads the
+// library, held until the process exits.  It is shared by every call on a
+// device and keeps the last call's contents; calls that overlap on the GPU
+// race on it and must be ordered by the caller (one stream, or events).
+
+namespace {
+
+constexpr uint64_t kStaticScratchBytes = 32ull << 20;
+constexpr int kStaticWarpSMs = 2;  // per-warp token regions for 2 SMs' worth (64 warps)
+constexpr int kMaxDevices = 64;
+
+__device__ __align__(256) uint8_t g_static_scratch[kStaticScratchBytes];
+
+std::mutex g_static_mu;
+uint8_t* g_static_ptr[kMaxDevices];  // device address of g_static_scratch, per device
+
+// The host-side name g_static_scratch is a stand-in, not a device address:
+// the address is looked up once per device, with that device current.
+ace_status static_scratch(int device, uint8_t** out) {
+  if (device < 0 || device >= kMaxDevices) return ACE_E_INVAL;
+  std::lock_guard<std::mutex> lock(g_static_mu);
+  if (!g_static_ptr[device]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_static_scratch) != cudaSuccess || !p) return ACE_E_CUDA;
+    g_static_ptr[device] = static_cast<uint8_t*>(p);
+  }
+  *out = g_static_ptr[device];
+  return ACE_OK;
+}
+
+}  // namespace
+
+ace_status ace_seek_noalloc(const ace_index* idx, uint64_t coord, uint64_t len, void* d_out, uint64_t out_bytes,
+                            cudaStream_t s) {
+  if (!idx || !d_out) return ACE_E_INVAL;
+  if (len == 0 || coord >= idx->h.total_size || len > idx->h.total_size - coord) return ACE_E_RANGE;
+  if (out_bytes < len) return ACE_E_NOMEM;
+  int cur = -1;
+  CUDA_TRY(cudaGetDevice(&cur));
+  if (cur != idx->device) return ACE_E_INVAL;  // the index's device must be current
+  uint8_t* base = nullptr;
+  ace_status rc = static_scratch(cur, &base);
+  if (rc) return rc;
+  const uint64_t nb = idx->h.n_blocks;
+  const uint32_t log2B = idx->h.log2_block;
+  ScratchLayout S = scratch_layout(nb, log2B, 1, kStaticWarpSMs, idx->max_ntok);
+  if (S.slots > kStaticScratchBytes) return ACE_E_NOMEM;  // archive too large for the fixed scratch
+  uint64_t cap = std::min<uint64_t>(nb, (kStaticScratchBytes - S.slots) >> log2B);
+  uint64_t first = coord >> log2B, last = (coord + len - 1) >> log2B;
+  if (last - first + 1 > cap) return ACE_E_NOMEM;  // more target blocks than slots
+  ScratchHdr* sh = reinterpret_cast<ScratchHdr*>(base);
+  // the closure marks must start clear; the array may hold another archive's layout
+  CUDA_TRY(cudaMemsetAsync(base + S.marks, 0, S.front0 - S.marks, s));
+  CUDA_TRY(cudaMemsetAsync(base, 0, 3 * sizeof(uint32_t), s));  // status word
+  ClosureArgs c;
+  c.dep_ptr = idx->d_dep_ptr;
+  c.dep_iv = idx->d_dep_iv;
+  c.sh = sh;
+  c.marks = reinterpret_cast<uint32_t*>(base + S.marks);
+  c.front0 = reinterpret_cast<uint32_t*>(base + S.front0);
+  c.front1 = reinterpret_cast<uint32_t*>(base + S.front1);
+  c.work = reinterpret_cast<uint32_t*>(base + S.work);
+  c.slot_of = reinterpret_cast<uint32_t*>(base + S.slot_of);
+  c.nb = nb;
+  c.first = first;
+  c.last = last;
+  c.cap = cap;
+  Launch L;
+  rc = plan_launch<true>(idx, nullptr, cap, S.n_warps, &L);
+  if (rc) return rc;
+  closure_kernel<<<1, 1024, 0, s>>>(c);
+  DecodeArgs a{};
+  a.arc = idx->d_arc;
+  a.dir = reinterpret_cast<const ace_block_dir*>(idx->d_arc + idx->h.dir_off);
+  a.payload_off = idx->h.payload_off;
+  a.total = idx->h.total_size;
+  a.nb = nb;
+  a.log2B = log2B;
+  a.w = idx->h.off_width;
+  a.window = L.chunk;
+  a.max_ntok = idx->max_ntok;
+  a.esc_cap = esc_cap(log2B);
+  a.warp_smem = L.smem_per_warp;
+  a.items = c.work;
+  a.out = base + S.slots;
+  a.sh = sh;
+  a.ready = reinterpret_cast<uint32_t*>(base + S.ready);
+  a.slot_of = c.slot_of;
+  a.slice = static_cast<uint8_t*>(d_out);
+  a.coord = coord;
+  a.len = len;
+  a.timeout_ns = L.timeout;
+  a.warp_scratch = base + S.warps;
+  a.warp_scratch_bytes = warp_scratch_bytes(idx->max_ntok);
+  decode_kernel<true><<<L.grid, 32 * L.warps, (size_t)L.warps * L.smem_per_warp, s>>>(a);
+  CUDA_TRY(cudaGetLastError());
+  // the status lives in the shared array, so the call waits for it
+  uint32_t status = 0;
+  CUDA_TRY(cudaMemcpyAsync(&status, base, sizeof status, cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  return (ace_status)status;
 }
 
 }  // extern "C"
