@@ -205,6 +205,37 @@ ace_status ace_index_set_tune(ace_index *idx, const ace_tune *tune);
  * recorded in the scratch status word. */
 ace_status ace_sync(const ace_index *idx, void *d_scratch, cudaStream_t s);
 
+/* ---------------------------------------------------------------- batches */
+
+/*
+ * Many independent archives decoded in one persistent launch (the batching
+ * pattern: thousands of uneven objects with mixed block sizes).  Each
+ * archive's blocks keep their own (level, block) order; warps take
+ * (archive, block) items from one ticket, so a warp only waits on blocks of
+ * its own archive handed out before it (Section 2's dependency rule).
+ *
+ * ace_batch_scratch_size sizes the batch scratch (256-byte aligned).
+ * ace_batch_create records the archives (all on the current device) and
+ * their outputs (out_bytes[i] >= the archive's total size) in the scratch,
+ * plans the launch from tune (NULL = defaults), and synchronises s.  It
+ * allocates no device memory.  ace_decode_batch then enqueues exactly two
+ * kernels on s and no host synchronisation, so it can be captured into a
+ * CUDA graph and replayed; each replay decodes every archive again.
+ * ace_batch_sync synchronises s and returns (then clears) the first device
+ * error.  ace_batch_launch_shape reports the planned grid, warps per CTA and
+ * token window.
+ */
+typedef struct ace_batch ace_batch;
+ace_status ace_batch_scratch_size(const ace_index *const *idx, uint32_t n, uint64_t *bytes);
+ace_status ace_batch_create(const ace_index *const *idx, uint32_t n, void *const *d_outs,
+                            const uint64_t *out_bytes, void *d_scratch, uint64_t scratch_bytes,
+                            const ace_tune *tune, cudaStream_t s, ace_batch **out);
+ace_status ace_decode_batch(const ace_batch *batch, cudaStream_t s);
+ace_status ace_batch_sync(const ace_batch *batch, cudaStream_t s);
+ace_status ace_batch_launch_shape(const ace_batch *batch, uint32_t *grid, uint32_t *warps_per_cta,
+                                  uint32_t *window);
+ace_status ace_batch_free(ace_batch *batch);
+
 /* ---------------------------------------------------------- verification */
 
 typedef struct {

@@ -79,6 +79,12 @@ _SIGS = {
     "ace_verify": ([_vp, _u64, _u64, _vp, _u64, _u64, _u32, _vp, _u64, _P(ace_verify_report), _vp], _i32),
     "ace_fnv1a64": ([_vp, _u64, _vp, _vp], _i32),
     "ace_seek_noalloc": ([_vp, _u64, _u64, _vp, _u64, _vp], _i32),
+    "ace_batch_scratch_size": ([_vp, _u32, _P(_u64)], _i32),
+    "ace_batch_create": ([_vp, _u32, _vp, _vp, _vp, _u64, _P(ace_tune), _vp, _P(_vp)], _i32),
+    "ace_decode_batch": ([_vp, _vp], _i32),
+    "ace_batch_sync": ([_vp, _vp], _i32),
+    "ace_batch_launch_shape": ([_vp, _P(_u32), _P(_u32), _P(_u32)], _i32),
+    "ace_batch_free": ([_vp], _i32),
 }
 
 
@@ -240,3 +246,46 @@ def ace_seek_noalloc(idx, coord, length, d_out, out_bytes, stream=None):
     """Seek with the library's fixed device scratch (no caller scratch);
     synchronous, returns the device-side status without raising."""
     return lib().ace_seek_noalloc(idx, coord, length, _ptr(d_out), out_bytes, _stream(stream))
+
+
+# ------------------------------------------------------------------- batches
+
+def _handles(idxs):
+    arr = (ctypes.c_void_p * len(idxs))(*[i.value if isinstance(i, ctypes.c_void_p) else i for i in idxs])
+    return arr
+
+
+def ace_batch_scratch_size(idxs):
+    out = _u64()
+    _check(lib().ace_batch_scratch_size(_handles(idxs), len(idxs), ctypes.byref(out)), "ace_batch_scratch_size")
+    return out.value
+
+
+def ace_batch_create(idxs, d_outs, out_bytes, d_scratch, scratch_bytes, tune=None, stream=None):
+    n = len(idxs)
+    outs = (ctypes.c_void_p * n)(*[_ptr(o) for o in d_outs])
+    sizes = (ctypes.c_uint64 * n)(*out_bytes)
+    h = _vp()
+    t = ctypes.byref(tune) if tune is not None else None
+    _check(lib().ace_batch_create(_handles(idxs), n, outs, sizes, _ptr(d_scratch), scratch_bytes, t,
+                                  _stream(stream), ctypes.byref(h)), "ace_batch_create")
+    return h
+
+
+def ace_decode_batch(batch, stream=None):
+    _check(lib().ace_decode_batch(batch, _stream(stream)), "ace_decode_batch")
+
+
+def ace_batch_sync(batch, stream=None):
+    return lib().ace_batch_sync(batch, _stream(stream))
+
+
+def ace_batch_launch_shape(batch):
+    g, w, c = _u32(), _u32(), _u32()
+    _check(lib().ace_batch_launch_shape(batch, ctypes.byref(g), ctypes.byref(w), ctypes.byref(c)),
+           "ace_batch_launch_shape")
+    return {"grid": g.value, "warps_per_cta": w.value, "window": c.value}
+
+
+def ace_batch_free(batch):
+    lib().ace_batch_free(batch)

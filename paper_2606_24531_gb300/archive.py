@@ -13,7 +13,7 @@ class DeviceArchive:
     including the blocks its matches read); 0 sizes it for whole decodes only.
     """
 
-    def __init__(self, h_arc, max_seek_blocks=0, device="cuda", stream=None):
+    def __init__(self, h_arc, max_seek_blocks=0, device="cuda", stream=None, scratch=True):
         h_arc = np.ascontiguousarray(h_arc, dtype=np.uint8)
         self.device = torch.device(device)
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
@@ -28,10 +28,13 @@ class DeviceArchive:
         self.info = ace.ace_index_info(self.idx)
         self.total = self.info["total_size"]
         self.block_size = self.info["block_size"]
-        self.scratch_bytes = ace.ace_scratch_size(self.idx, max_seek_blocks)
         self.max_seek_blocks = max_seek_blocks
-        self.d_scratch = torch.empty(self.scratch_bytes, dtype=torch.uint8, device=self.device)
-        ace.ace_scratch_init(self.idx, self.d_scratch, self.scratch_bytes, self.stream)
+        self.scratch_bytes = 0
+        self.d_scratch = None
+        if scratch:
+            self.scratch_bytes = ace.ace_scratch_size(self.idx, max_seek_blocks)
+            self.d_scratch = torch.empty(self.scratch_bytes, dtype=torch.uint8, device=self.device)
+            ace.ace_scratch_init(self.idx, self.d_scratch, self.scratch_bytes, self.stream)
 
     def new_scratch(self, max_seek_blocks):
         """A separate scratch buffer, for calls that overlap on the device."""

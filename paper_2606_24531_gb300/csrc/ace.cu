@@ -9,6 +9,7 @@
 #include <cstring>
 #include <mutex>
 #include <new>
+#include <vector>
 
 #include "ace.h"
 #include "ace_device.cuh"
@@ -532,6 +533,78 @@ __global__ void __launch_bounds__(256, 3) decode_kernel(DecodeArgs a) {
     __threadfence();
     __syncwarp();
     if (lane == 0) st_release(a.ready + b, epoch);
+  }
+}
+
+// ----------------------------------------------------------- batch decode
+
+// One independent archive of a batch, as the batch kernel sees it.
+struct ObjDesc {
+  const uint8_t* arc;
+  const ace_block_dir* dir;
+  uint64_t payload_off;
+  uint64_t total;
+  uint8_t* out;
+  uint32_t* ready;
+  const uint32_t* order;  // the archive's blocks in (level, block) order
+  uint32_t log2B, w, nb, pad;
+};
+
+struct BatchArgs {
+  const ObjDesc* objs;
+  const uint32_t* item_start;  // [n_objs + 1]: first work item of each archive
+  uint32_t n_objs, n_items;
+  uint32_t window, warp_smem, esc_cap, max_ntok;
+  ScratchHdr* sh;
+  uint64_t timeout_ns;
+  uint8_t* warp_scratch;
+  uint64_t warp_scratch_bytes;
+};
+
+// Thousands of independent archives in one persistent launch: warps take
+// (archive, block) items from one ticket; each archive's items are in its
+// own (level, block) order, so a warp only ever waits on blocks of its
+// archive that were handed out before its own.
+__global__ void __launch_bounds__(256, 3) batch_decode_kernel(BatchArgs ba) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  WarpMem m = carve(smem + (size_t)wid * ba.warp_smem, ba.window);
+  TokRec g = tok_records(ba.warp_scratch + (size_t)(blockIdx.x * (blockDim.x >> 5) + wid) * ba.warp_scratch_bytes,
+                         ba.max_ntok);
+  const uint32_t epoch = *(volatile uint32_t*)&ba.sh->epoch;
+  while (true) {
+    uint32_t it = 0;
+    if (lane == 0) it = atomicAdd(&ba.sh->ticket, 1u);
+    it = __shfl_sync(kFull, it, 0);
+    if (it >= ba.n_items) break;
+    uint32_t lo = 0, hi = ba.n_objs;  // the archive o with item_start[o] <= it < item_start[o + 1]
+    while (hi - lo > 1) {
+      uint32_t mid = (lo + hi) >> 1;
+      if (__ldg(ba.item_start + mid) <= it) lo = mid;
+      else hi = mid;
+    }
+    const ObjDesc od = ba.objs[lo];
+    DecodeArgs a{};
+    a.arc = od.arc;
+    a.dir = od.dir;
+    a.payload_off = od.payload_off;
+    a.total = od.total;
+    a.nb = od.nb;
+    a.log2B = od.log2B;
+    a.w = od.w;
+    a.window = ba.window;
+    a.esc_cap = ba.esc_cap;
+    a.warp_smem = ba.warp_smem;
+    a.max_ntok = ba.max_ntok;
+    a.out = od.out;
+    a.sh = ba.sh;
+    a.ready = od.ready;
+    a.timeout_ns = ba.timeout_ns;
+    uint32_t b = __ldg(od.order + (it - __ldg(ba.item_start + lo)));
+    decode_block<false>(a, m, g, b, lane, epoch);
+    __threadfence();
+    __syncwarp();
+    if (lane == 0) st_release(od.ready + b, epoch);
   }
 }
 
@@ -1135,6 +1208,177 @@ ace_status ace_verify(const ace_index* idx, uint64_t coord, uint64_t len, void* 
   if (rc) return rc;
   rep->phase2_ok = rep->seek_status == ACE_OK && rep->fnv_after == expected;
   rep->phase3_ok = rep->guard_bad_before == 0 && rep->guard_bad_after == 0;
+  return ACE_OK;
+}
+
+// ------------------------------------------------------------ batch (host)
+
+struct ace_batch {
+  int device;
+  uint32_t n;
+  uint8_t* d_scratch;
+  uint64_t scratch_bytes;
+  BatchArgs args;
+  Launch L;
+};
+
+namespace {
+
+struct BatchLayout {
+  uint64_t objs, item_start, ready, warps, total, n_warps, max_ntok, items;
+  uint32_t max_log2B;
+};
+
+ace_status batch_layout(const ace_index* const* idx, uint32_t n, BatchLayout* B) {
+  if (!idx || n == 0) return ACE_E_INVAL;
+  uint64_t ready = 0, items = 0, max_ntok = 0;
+  uint32_t max_log2B = 0;
+  int dev = idx[0] ? idx[0]->device : -1, sms = idx[0] ? idx[0]->num_sms : 0;
+  for (uint32_t i = 0; i < n; i++) {
+    if (!idx[i] || idx[i]->device != dev) return ACE_E_INVAL;
+    items += idx[i]->h.n_blocks;
+    ready += align256(4 * idx[i]->h.n_blocks);
+    max_ntok = std::max<uint64_t>(max_ntok, idx[i]->max_ntok);
+    max_log2B = std::max<uint32_t>(max_log2B, idx[i]->h.log2_block);
+  }
+  if (items > 0xFFFFFFF0ull) return ACE_E_INVAL;
+  uint64_t o = sizeof(ScratchHdr);
+  B->objs = o;
+  o = align256(o + n * sizeof(ObjDesc));
+  B->item_start = o;
+  o = align256(o + 4ull * (n + 1));
+  B->ready = o;
+  o += ready;
+  B->n_warps = std::min<uint64_t>((uint64_t)sms * kMaxWarpsPerSM, items + 16);
+  B->warps = o;
+  o = align256(o + B->n_warps * warp_scratch_bytes(max_ntok));
+  B->total = o;
+  B->max_ntok = max_ntok;
+  B->items = items;
+  B->max_log2B = max_log2B;
+  return ACE_OK;
+}
+
+}  // namespace
+
+ace_status ace_batch_scratch_size(const ace_index* const* idx, uint32_t n, uint64_t* bytes) {
+  if (!bytes) return ACE_E_INVAL;
+  BatchLayout B;
+  ace_status rc = batch_layout(idx, n, &B);
+  if (rc) return rc;
+  *bytes = B.total;
+  return ACE_OK;
+}
+
+ace_status ace_batch_create(const ace_index* const* idx, uint32_t n, void* const* d_outs, const uint64_t* out_bytes,
+                            void* d_scratch, uint64_t scratch_bytes, const ace_tune* tune, cudaStream_t s,
+                            ace_batch** out) {
+  if (!out || !d_outs || !out_bytes || !d_scratch || !aligned(d_scratch, 256)) return ACE_E_INVAL;
+  BatchLayout B;
+  ace_status rc = batch_layout(idx, n, &B);
+  if (rc) return rc;
+  if (scratch_bytes < B.total) return ACE_E_NOMEM;
+  uint8_t* base = static_cast<uint8_t*>(d_scratch);
+  std::vector<ObjDesc> od(n);
+  std::vector<uint32_t> start(n + 1);
+  uint64_t ready = B.ready, items = 0;
+  for (uint32_t i = 0; i < n; i++) {
+    const ace_index* x = idx[i];
+    if (out_bytes[i] < x->h.total_size || (!d_outs[i] && x->h.total_size)) return ACE_E_NOMEM;
+    od[i] = ObjDesc{x->d_arc,
+                    reinterpret_cast<const ace_block_dir*>(x->d_arc + x->h.dir_off),
+                    x->h.payload_off,
+                    x->h.total_size,
+                    static_cast<uint8_t*>(d_outs[i]),
+                    reinterpret_cast<uint32_t*>(base + ready),
+                    x->d_order,
+                    x->h.log2_block,
+                    x->h.off_width,
+                    (uint32_t)x->h.n_blocks,
+                    0};
+    start[i] = (uint32_t)items;
+    items += x->h.n_blocks;
+    ready += align256(4 * x->h.n_blocks);
+  }
+  start[n] = (uint32_t)items;
+  ace_batch* b = new (std::nothrow) ace_batch();
+  if (!b) return ACE_E_NOMEM;
+  b->device = idx[0]->device;
+  b->n = n;
+  b->d_scratch = base;
+  b->scratch_bytes = scratch_bytes;
+  // the launch shape uses the largest block size's escape table
+  ace_index probe = *idx[0];
+  probe.h.log2_block = (uint8_t)B.max_log2B;
+  rc = plan_launch<false>(&probe, tune, B.items, B.n_warps, &b->L);
+  if (rc == ACE_OK && B.items) {
+    // the kernel is launched as batch_decode_kernel: same shape, same limits
+    int optin = 0;
+    size_t smem = (size_t)b->L.warps * b->L.smem_per_warp;
+    if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, b->device) != cudaSuccess ||
+        cudaFuncSetAttribute(batch_decode_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin) != cudaSuccess)
+      rc = ACE_E_CUDA;
+    (void)smem;
+  }
+  if (rc == ACE_OK &&
+      (cudaMemsetAsync(base, 0, B.total - B.n_warps * warp_scratch_bytes(B.max_ntok), s) != cudaSuccess ||
+       cudaMemcpyAsync(base + B.objs, od.data(), n * sizeof(ObjDesc), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+       cudaMemcpyAsync(base + B.item_start, start.data(), 4ull * (n + 1), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+       cudaStreamSynchronize(s) != cudaSuccess))
+    rc = ACE_E_CUDA;
+  if (rc) {
+    delete b;
+    return rc;
+  }
+  BatchArgs& a = b->args;
+  a.objs = reinterpret_cast<const ObjDesc*>(base + B.objs);
+  a.item_start = reinterpret_cast<const uint32_t*>(base + B.item_start);
+  a.n_objs = n;
+  a.n_items = (uint32_t)B.items;
+  a.window = b->L.chunk;
+  a.warp_smem = b->L.smem_per_warp;
+  a.esc_cap = esc_cap(B.max_log2B);
+  a.max_ntok = (uint32_t)B.max_ntok;
+  a.sh = reinterpret_cast<ScratchHdr*>(base);
+  a.timeout_ns = b->L.timeout;
+  a.warp_scratch = base + B.warps;
+  a.warp_scratch_bytes = warp_scratch_bytes(B.max_ntok);
+  *out = b;
+  return ACE_OK;
+}
+
+ace_status ace_decode_batch(const ace_batch* b, cudaStream_t s) {
+  if (!b) return ACE_E_INVAL;
+  if (!b->args.n_items) return ACE_OK;
+  begin_call_kernel<<<1, 1, 0, s>>>(b->args.sh);
+  batch_decode_kernel<<<b->L.grid, 32 * b->L.warps, (size_t)b->L.warps * b->L.smem_per_warp, s>>>(b->args);
+  CUDA_TRY(cudaGetLastError());
+  return ACE_OK;
+}
+
+ace_status ace_batch_sync(const ace_batch* b, cudaStream_t s) {
+  if (!b) return ACE_E_INVAL;
+  CUDA_TRY(cudaStreamSynchronize(s));
+  ScratchHdr h;
+  CUDA_TRY(cudaMemcpyAsync(&h, b->d_scratch, sizeof h, cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  if (h.status) {
+    CUDA_TRY(cudaMemsetAsync(b->d_scratch, 0, 3 * sizeof(uint32_t), s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+  }
+  return (ace_status)h.status;
+}
+
+ace_status ace_batch_launch_shape(const ace_batch* b, uint32_t* grid, uint32_t* warps_per_cta, uint32_t* window) {
+  if (!b) return ACE_E_INVAL;
+  if (grid) *grid = b->L.grid;
+  if (warps_per_cta) *warps_per_cta = b->L.warps;
+  if (window) *window = b->L.chunk;
+  return ACE_OK;
+}
+
+ace_status ace_batch_free(ace_batch* b) {
+  delete b;
   return ACE_OK;
 }
 
