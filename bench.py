@@ -300,6 +300,38 @@ def main():
                          "h2d_bytes_per_step": int(arc.size), "d2h_bytes_per_step": int(total),
                          "includes": "H2D archive, index build, decode, D2H output"}
 
+        # batched: 4,096 uneven objects (log-uniform 4 KiB .. 2 MiB, four
+        # profiles, 4/16/64 KiB blocks) in one persistent launch replayed as a
+        # CUDA graph, against one ace_decode_all launch per object
+        from paper_2606_24531_gb300.batch import DeviceBatch, autotune, make_objects, time_per_object
+
+        bdatas, barcs = make_objects(4096, seed=4, max_size=1 << 21)
+        db = DeviceBatch(barcs, device=dev)
+        tuned = autotune(db, reps=2, cache_key=None)
+        graph = db.capture()
+        graph.replay()
+        assert db.sync() == ace.ACE_OK
+        btotal = sum(d.size for d in bdatas)
+        chk = torch.cat([torch.from_numpy(d) for d in bdatas[:64]]).to(dev)
+        assert torch.equal(torch.cat([db.output(i) for i in range(64)]), chk)
+        bt = []
+        for _ in range(5):
+            flush.fill_(1)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            graph.replay()
+            e1.record(stream)
+            e1.synchronize()
+            bt.append(e0.elapsed_time(e1))
+        per_obj_ms = time_per_object(db.items, [db.output(i) for i in range(len(bdatas))], reps=2)
+        result["batched"] = {"objects": len(bdatas), "bytes": btotal, "max_object": 1 << 21,
+                             "graph_ms": float(np.median(bt)),
+                             "graph_GBps": btotal / (float(np.median(bt)) / 1e3) / 1e9,
+                             "per_object_launches_ms": per_obj_ms,
+                             "per_object_GBps": btotal / (per_obj_ms / 1e3) / 1e9,
+                             "tuned": {k: tuned[k] for k in ("warps_per_cta", "window")}}
+        db.close()
+
         # the oracle on the host cores (rank 0 only)
         if rank == 0:
             import oracle

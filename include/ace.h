@@ -236,6 +236,57 @@ ace_status ace_batch_launch_shape(const ace_batch *batch, uint32_t *grid, uint32
                                   uint32_t *window);
 ace_status ace_batch_free(ace_batch *batch);
 
+/* --------------------------------------------- seek batches and the cache */
+
+/*
+ * Many seeks, over several resident archives, in one pass: the serving
+ * pattern.  A decoded-block cache (caller memory) holds n_slots decoded
+ * blocks; every archive attached to it has a small per-archive state (ready
+ * flags, slot map, closure marks; ace_archive_state_size).  A seek batch:
+ *   1. finds every target block that is not cached and, transitively, every
+ *      uncached block their matches read (Section 2), in ascending block
+ *      order per archive, and gives each a free slot;
+ *   2. decodes those blocks through both layers into their slots (Section 3
+ *      entry point, Section 2 match layer), waiting bounded on sources;
+ *   3. copies each request's bytes [coord, coord + len) to d_pool + out_off.
+ * Blocks stay cached across batches until the slots run out: a batch that
+ * needs more free slots than remain records ACE_E_NOMEM and copies nothing;
+ * the caller then calls ace_cache_reset (every block uncached, every slot
+ * free) and resubmits.  After any other error, reset as well.
+ *
+ * All archives of a cache share one device and one block size.  Batches on
+ * one cache must be ordered on one stream; separate caches (each with its
+ * own per-archive states) may run concurrently on separate streams.
+ * ace_seek_batch reads device-resident requests and enqueues three kernels;
+ * ace_seek_batch_host validates host requests against the archives' sizes
+ * (h_totals, may be NULL) and the pool, stages them in the cache memory
+ * (n <= max_reqs) and calls it.  ace_cache_sync returns (then clears) the
+ * first device error; ace_cache_usage reports slots in use.
+ */
+typedef struct {
+    uint32_t archive;  /* position of the archive in the cache's list */
+    uint32_t reserved;
+    uint64_t coord;    /* first absolute byte */
+    uint64_t len;      /* bytes, >= 1 */
+    uint64_t out_off;  /* byte offset of the result in the output pool */
+} ace_seek_req;
+
+typedef struct ace_cache ace_cache;
+ace_status ace_archive_state_size(const ace_index *idx, uint64_t *bytes);
+ace_status ace_cache_size(const ace_index *const *idx, uint32_t n, uint64_t n_slots, uint32_t max_reqs,
+                          uint64_t *bytes);
+ace_status ace_cache_create(const ace_index *const *idx, uint32_t n, void *const *d_states,
+                            uint64_t n_slots, uint32_t max_reqs, void *d_mem, uint64_t bytes,
+                            const ace_tune *tune, cudaStream_t s, ace_cache **out);
+ace_status ace_seek_batch(const ace_cache *cache, const ace_seek_req *d_reqs, uint32_t n, void *d_pool,
+                          uint64_t pool_bytes, cudaStream_t s);
+ace_status ace_seek_batch_host(const ace_cache *cache, const ace_seek_req *h_reqs, const uint64_t *h_totals,
+                               uint32_t n, void *d_pool, uint64_t pool_bytes, cudaStream_t s);
+ace_status ace_cache_sync(const ace_cache *cache, cudaStream_t s);
+ace_status ace_cache_usage(const ace_cache *cache, uint32_t *used_slots, uint32_t *n_slots, cudaStream_t s);
+ace_status ace_cache_reset(const ace_cache *cache, cudaStream_t s);
+ace_status ace_cache_free(ace_cache *cache);
+
 /* ---------------------------------------------------------- verification */
 
 typedef struct {

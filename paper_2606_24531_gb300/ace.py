@@ -85,6 +85,15 @@ _SIGS = {
     "ace_batch_sync": ([_vp, _vp], _i32),
     "ace_batch_launch_shape": ([_vp, _P(_u32), _P(_u32), _P(_u32)], _i32),
     "ace_batch_free": ([_vp], _i32),
+    "ace_archive_state_size": ([_vp, _P(_u64)], _i32),
+    "ace_cache_size": ([_vp, _u32, _u64, _u32, _P(_u64)], _i32),
+    "ace_cache_create": ([_vp, _u32, _vp, _u64, _u32, _vp, _u64, _P(ace_tune), _vp, _P(_vp)], _i32),
+    "ace_seek_batch": ([_vp, _vp, _u32, _vp, _u64, _vp], _i32),
+    "ace_seek_batch_host": ([_vp, _vp, _vp, _u32, _vp, _u64, _vp], _i32),
+    "ace_cache_sync": ([_vp, _vp], _i32),
+    "ace_cache_usage": ([_vp, _P(_u32), _P(_u32), _vp], _i32),
+    "ace_cache_reset": ([_vp, _vp], _i32),
+    "ace_cache_free": ([_vp], _i32),
 }
 
 
@@ -289,3 +298,62 @@ def ace_batch_launch_shape(batch):
 
 def ace_batch_free(batch):
     lib().ace_batch_free(batch)
+
+
+# ------------------------------------------------------ seek batches (cache)
+
+SEEK_REQ = np.dtype([("archive", np.uint32), ("reserved", np.uint32), ("coord", np.uint64),
+                     ("len", np.uint64), ("out_off", np.uint64)])
+
+
+def ace_archive_state_size(idx):
+    out = _u64()
+    _check(lib().ace_archive_state_size(idx, ctypes.byref(out)), "ace_archive_state_size")
+    return out.value
+
+
+def ace_cache_size(idxs, n_slots, max_reqs):
+    out = _u64()
+    _check(lib().ace_cache_size(_handles(idxs), len(idxs), n_slots, max_reqs, ctypes.byref(out)), "ace_cache_size")
+    return out.value
+
+
+def ace_cache_create(idxs, d_states, n_slots, max_reqs, d_mem, mem_bytes, tune=None, stream=None):
+    n = len(idxs)
+    st = (ctypes.c_void_p * n)(*[_ptr(x) for x in d_states])
+    h = _vp()
+    t = ctypes.byref(tune) if tune is not None else None
+    _check(lib().ace_cache_create(_handles(idxs), n, st, n_slots, max_reqs, _ptr(d_mem), mem_bytes, t,
+                                  _stream(stream), ctypes.byref(h)), "ace_cache_create")
+    return h
+
+
+def ace_seek_batch(cache, d_reqs, n, d_pool, pool_bytes, stream=None):
+    _check(lib().ace_seek_batch(cache, _ptr(d_reqs), n, _ptr(d_pool), pool_bytes, _stream(stream)),
+           "ace_seek_batch")
+
+
+def ace_seek_batch_host(cache, h_reqs, h_totals, d_pool, pool_bytes, stream=None):
+    """h_reqs: numpy array of SEEK_REQ; h_totals: numpy uint64 sizes or None."""
+    r = np.ascontiguousarray(h_reqs, dtype=SEEK_REQ)
+    tot = None if h_totals is None else np.ascontiguousarray(h_totals, dtype=np.uint64)
+    _check(lib().ace_seek_batch_host(cache, r.ctypes.data, None if tot is None else tot.ctypes.data, r.size,
+                                     _ptr(d_pool), pool_bytes, _stream(stream)), "ace_seek_batch_host")
+
+
+def ace_cache_sync(cache, stream=None):
+    return lib().ace_cache_sync(cache, _stream(stream))
+
+
+def ace_cache_usage(cache, stream=None):
+    u, n = _u32(), _u32()
+    _check(lib().ace_cache_usage(cache, ctypes.byref(u), ctypes.byref(n), _stream(stream)), "ace_cache_usage")
+    return u.value, n.value
+
+
+def ace_cache_reset(cache, stream=None):
+    _check(lib().ace_cache_reset(cache, _stream(stream)), "ace_cache_reset")
+
+
+def ace_cache_free(cache):
+    lib().ace_cache_free(cache)

@@ -709,6 +709,252 @@ __global__ void closure_kernel(ClosureArgs a) {
   }
 }
 
+// ------------------------------------------------------ seek batches (cache)
+
+// One archive attached to a decoded-block cache.
+struct CacheArc {
+  const uint8_t* arc;
+  const ace_block_dir* dir;
+  uint64_t payload_off;
+  uint64_t total;
+  const uint32_t* dep_ptr;
+  const uint32_t* dep_iv;
+  uint32_t* ready;    // == cache epoch: the block sits decoded in its slot
+  uint32_t* slot_of;
+  uint32_t* marks;    // closure marks, clear between calls
+  uint32_t nb, w, pad0, pad1;
+};
+
+// Header of a cache (first 256 bytes of its memory).
+struct CacheHdr {
+  uint32_t status, err_block, err_where;
+  uint32_t epoch;      // blocks whose ready flag equals it are cached
+  uint32_t ticket;
+  uint32_t n_work;
+  uint32_t next_slot;  // slots handed out in this epoch
+  uint32_t n_front;
+  uint32_t pad[56];
+};
+static_assert(sizeof(CacheHdr) == 256, "cache header");
+static_assert(offsetof(CacheHdr, epoch) == offsetof(ScratchHdr, epoch), "shared header fields");
+static_assert(offsetof(CacheHdr, ticket) == offsetof(ScratchHdr, ticket), "shared header fields");
+static_assert(offsetof(CacheHdr, n_work) == offsetof(ScratchHdr, n_work), "shared header fields");
+
+struct CacheArgs {
+  CacheHdr* h;
+  const CacheArc* arcs;
+  uint32_t n_arcs;
+  uint32_t log2B;
+  uint32_t n_slots;
+  uint32_t front_cap;
+  uint32_t* front0;   // (archive, block) pairs
+  uint32_t* front1;
+  uint32_t* work;     // (archive, block) pairs in decode order
+  uint32_t* arc_minmax;  // per archive: smallest, largest block marked
+  uint8_t* slots;
+  const ace_seek_req* reqs;
+  uint32_t n_reqs;
+};
+
+__device__ __forceinline__ bool cache_mark(const CacheArgs& c, uint32_t a, uint32_t b, uint32_t epoch) {
+  const CacheArc& ca = c.arcs[a];
+  if (ld_acquire(ca.ready + b) == epoch) return false;  // already cached
+  uint32_t bit = 1u << (b & 31);
+  return !(atomicOr(ca.marks + (b >> 5), bit) & bit);
+}
+
+// The blocks a batch of seeks must decode: every target block that is not
+// cached and, transitively, every uncached block their matches read
+// (Section 2), listed archive by archive in ascending block order, each with
+// a fresh slot.  One CTA.
+__global__ void cache_closure_kernel(CacheArgs c) {
+  __shared__ uint32_t n_next, carry, overflow;
+  __shared__ uint32_t wsum[32];
+  const uint32_t tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
+  const uint32_t epoch = c.h->epoch;
+  if (tid == 0) {
+    n_next = 0;
+    overflow = 0;
+  }
+  for (uint32_t a = tid; a < c.n_arcs; a += blockDim.x) {
+    c.arc_minmax[2 * a] = 0xffffffffu;
+    c.arc_minmax[2 * a + 1] = 0;
+  }
+  __syncthreads();
+  // targets: a thread per request
+  for (uint32_t r = tid; r < c.n_reqs; r += blockDim.x) {
+    const ace_seek_req q = c.reqs[r];
+    uint64_t first = q.coord >> c.log2B, last = (q.coord + q.len - 1) >> c.log2B;
+    for (uint64_t b = first; b <= last; b++)
+      if (cache_mark(c, q.archive, (uint32_t)b, epoch)) {
+        uint32_t i = atomicAdd(&n_next, 1u);
+        if (i < c.front_cap) {
+          c.front0[2 * i] = q.archive;
+          c.front0[2 * i + 1] = (uint32_t)b;
+        } else {
+          overflow = 1;
+        }
+        atomicMin(&c.arc_minmax[2 * q.archive], (uint32_t)b);
+        atomicMax(&c.arc_minmax[2 * q.archive + 1], (uint32_t)b);
+      }
+  }
+  __syncthreads();
+  uint32_t n_front = min(n_next, c.front_cap);
+  uint32_t* cur = c.front0;
+  uint32_t* nxt = c.front1;
+  __syncthreads();
+  while (n_front && !overflow) {
+    if (tid == 0) n_next = 0;
+    __syncthreads();
+    for (uint32_t i = tid; i < n_front; i += blockDim.x) {
+      uint32_t a = cur[2 * i], b = cur[2 * i + 1];
+      const CacheArc& ca = c.arcs[a];
+      for (uint32_t e = ca.dep_ptr[b]; e < ca.dep_ptr[b + 1]; e++)
+        for (uint32_t k = ca.dep_iv[2 * e]; k <= ca.dep_iv[2 * e + 1]; k++)
+          if (cache_mark(c, a, k, epoch)) {
+            uint32_t j = atomicAdd(&n_next, 1u);
+            if (j < c.front_cap) {
+              nxt[2 * j] = a;
+              nxt[2 * j + 1] = k;
+            } else {
+              overflow = 1;
+            }
+            atomicMin(&c.arc_minmax[2 * a], k);
+          }
+    }
+    __syncthreads();
+    n_front = min(n_next, c.front_cap);
+    uint32_t* t = cur;
+    cur = nxt;
+    nxt = t;
+    __syncthreads();
+  }
+  // ordered compaction, archive by archive, clearing the marks behind it
+  if (tid == 0) carry = 0;
+  __syncthreads();
+  const uint32_t slot0 = c.h->next_slot;
+  for (uint32_t a = 0; a < c.n_arcs; a++) {
+    uint32_t lo = c.arc_minmax[2 * a], hi = c.arc_minmax[2 * a + 1];
+    if (lo > hi) continue;
+    const CacheArc& ca = c.arcs[a];
+    for (uint32_t c0 = lo >> 5; c0 <= (hi >> 5); c0 += blockDim.x) {
+      uint32_t wi = c0 + tid;
+      uint32_t bits = wi <= (hi >> 5) ? ca.marks[wi] : 0u;
+      uint32_t cnt = __popc(bits);
+      uint32_t incl = warp_incl_sum(cnt, lane);
+      if (lane == 31) wsum[wid] = incl;
+      __syncthreads();
+      if (wid == 0) {
+        uint32_t v = lane < nw ? wsum[lane] : 0;
+        uint32_t vi = warp_incl_sum(v, lane);
+        if (lane < nw) wsum[lane] = vi - v;
+      }
+      __syncthreads();
+      uint32_t pos = carry + wsum[wid] + incl - cnt;
+      while (bits) {
+        uint32_t bit = __ffs(bits) - 1;
+        bits &= bits - 1;
+        uint32_t b = wi * 32 + bit;
+        if (slot0 + pos < c.n_slots) {
+          c.work[2 * pos] = a;
+          c.work[2 * pos + 1] = b;
+          ca.slot_of[b] = slot0 + pos;
+        }
+        pos++;
+      }
+      if (wi <= (hi >> 5)) ca.marks[wi] = 0;
+      __syncthreads();
+      if (tid == blockDim.x - 1) carry = pos;
+      __syncthreads();
+    }
+  }
+  if (tid == 0) {
+    uint32_t n = carry;
+    if (overflow || slot0 + n > c.n_slots) {
+      record_error(&c.h->status, &c.h->err_block, &c.h->err_where, ACE_E_NOMEM, n, 51);
+      n = 0;
+    } else {
+      c.h->next_slot = slot0 + n;
+    }
+    c.h->n_work = n;
+    c.h->ticket = 0;
+  }
+}
+
+struct CacheDecodeArgs {
+  CacheArgs c;
+  uint32_t window, warp_smem, esc_cap, max_ntok;
+  uint64_t timeout_ns;
+  uint8_t* warp_scratch;
+  uint64_t warp_scratch_bytes;
+};
+
+// Decodes a batch's work list into cache slots: the same two-layer block
+// decode as a seek, archive by archive.
+__global__ void __launch_bounds__(256, 3) cache_decode_kernel(CacheDecodeArgs ca) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  WarpMem m = carve(smem + (size_t)wid * ca.warp_smem, ca.window);
+  TokRec g = tok_records(ca.warp_scratch + (size_t)(blockIdx.x * (blockDim.x >> 5) + wid) * ca.warp_scratch_bytes,
+                         ca.max_ntok);
+  const CacheArgs& c = ca.c;
+  const uint32_t epoch = *(volatile uint32_t*)&c.h->epoch;
+  const uint32_t n_items = *(volatile uint32_t*)&c.h->n_work;
+  while (true) {
+    uint32_t it = 0;
+    if (lane == 0) it = atomicAdd(&c.h->ticket, 1u);
+    it = __shfl_sync(kFull, it, 0);
+    if (it >= n_items) break;
+    const uint32_t ai = __ldg(c.work + 2 * it), b = __ldg(c.work + 2 * it + 1);
+    const CacheArc& arc = c.arcs[ai];
+    DecodeArgs a{};
+    a.arc = arc.arc;
+    a.dir = arc.dir;
+    a.payload_off = arc.payload_off;
+    a.total = arc.total;
+    a.nb = arc.nb;
+    a.log2B = c.log2B;
+    a.w = arc.w;
+    a.window = ca.window;
+    a.esc_cap = ca.esc_cap;
+    a.warp_smem = ca.warp_smem;
+    a.max_ntok = ca.max_ntok;
+    a.out = c.slots;
+    a.sh = reinterpret_cast<ScratchHdr*>(c.h);
+    a.ready = arc.ready;
+    a.slot_of = arc.slot_of;
+    a.timeout_ns = ca.timeout_ns;
+    decode_block<true>(a, m, g, b, lane, epoch);
+    __threadfence();
+    __syncwarp();
+    if (lane == 0) st_release(arc.ready + b, epoch);
+  }
+}
+
+// Each request's bytes from the cache slots to its place in the output pool.
+__global__ void cache_copy_kernel(CacheArgs c, uint8_t* pool) {
+  if (*(volatile uint32_t*)&c.h->status) return;  // a failed batch copies nothing
+  const uint64_t B = (uint64_t)1 << c.log2B;
+  for (uint32_t r = blockIdx.x; r < c.n_reqs; r += gridDim.x) {
+    const ace_seek_req q = c.reqs[r];
+    const CacheArc& ca = c.arcs[q.archive];
+    uint8_t* dst = pool + q.out_off;
+    for (uint64_t i = threadIdx.x; i < q.len; i += blockDim.x) {
+      uint64_t p = q.coord + i;
+      uint32_t slot = __ldg(ca.slot_of + (p >> c.log2B));
+      dst[i] = __ldcg(c.slots + ((uint64_t)slot << c.log2B) + (p & (B - 1)));
+    }
+  }
+}
+
+// New cache epoch: every cached block is forgotten, every slot is free.
+__global__ void cache_reset_kernel(CacheHdr* h) {
+  h->epoch += 1;
+  h->next_slot = 0;
+  h->ticket = 0;
+  h->n_work = 0;
+}
+
 // ------------------------------------------------------------ verification
 
 __device__ __forceinline__ uint8_t pattern_byte(uint32_t seed, uint64_t i) {
@@ -1379,6 +1625,236 @@ ace_status ace_batch_launch_shape(const ace_batch* b, uint32_t* grid, uint32_t* 
 
 ace_status ace_batch_free(ace_batch* b) {
   delete b;
+  return ACE_OK;
+}
+
+// ------------------------------------------------------ seek batches (host)
+
+struct ace_cache {
+  int device;
+  uint32_t n_arcs, log2B, n_slots, front_cap, max_reqs;
+  uint8_t* mem;
+  uint64_t bytes;
+  CacheArgs args;
+  CacheDecodeArgs dargs;
+  Launch L;
+  uint64_t req_off;  // requests are staged here by ace_seek_batch_host
+};
+
+namespace {
+
+struct CacheLayout {
+  uint64_t arcs, minmax, front0, front1, work, reqs, warps, slots, total, n_warps, max_ntok;
+};
+
+CacheLayout cache_layout(const ace_index* const* idx, uint32_t n, uint64_t n_slots, uint32_t max_reqs,
+                         uint32_t log2B) {
+  CacheLayout C;
+  uint64_t max_ntok = 0;
+  for (uint32_t i = 0; i < n; i++) max_ntok = std::max<uint64_t>(max_ntok, idx[i]->max_ntok);
+  uint64_t o = sizeof(CacheHdr);
+  C.arcs = o;
+  o = align256(o + n * sizeof(CacheArc));
+  C.minmax = o;
+  o = align256(o + 8ull * n);
+  C.front0 = o;
+  o = align256(o + 8 * n_slots);
+  C.front1 = o;
+  o = align256(o + 8 * n_slots);
+  C.work = o;
+  o = align256(o + 8 * n_slots);
+  C.reqs = o;
+  o = align256(o + sizeof(ace_seek_req) * (uint64_t)max_reqs);
+  C.n_warps = std::min<uint64_t>((uint64_t)idx[0]->num_sms * kMaxWarpsPerSM, n_slots + 16);
+  C.warps = o;
+  o = align256(o + C.n_warps * warp_scratch_bytes(max_ntok));
+  C.slots = o;
+  o = align256(o + (n_slots << log2B));
+  C.total = o;
+  C.max_ntok = max_ntok;
+  return C;
+}
+
+ace_status cache_check(const ace_index* const* idx, uint32_t n) {
+  if (!idx || n == 0) return ACE_E_INVAL;
+  for (uint32_t i = 0; i < n; i++)
+    if (!idx[i] || idx[i]->device != idx[0]->device || idx[i]->h.log2_block != idx[0]->h.log2_block)
+      return ACE_E_INVAL;  // one device, one block size per cache
+  return ACE_OK;
+}
+
+}  // namespace
+
+ace_status ace_cache_size(const ace_index* const* idx, uint32_t n, uint64_t n_slots, uint32_t max_reqs,
+                          uint64_t* bytes) {
+  ace_status rc = cache_check(idx, n);
+  if (rc) return rc;
+  if (!bytes || n_slots == 0 || n_slots > 0xFFFFFFF0ull || max_reqs == 0) return ACE_E_INVAL;
+  *bytes = cache_layout(idx, n, n_slots, max_reqs, idx[0]->h.log2_block).total;
+  return ACE_OK;
+}
+
+ace_status ace_archive_state_size(const ace_index* idx, uint64_t* bytes) {
+  if (!idx || !bytes) return ACE_E_INVAL;
+  uint64_t nb = idx->h.n_blocks;
+  *bytes = align256(4 * nb) * 2 + align256(4 * ((nb + 31) / 32));
+  return ACE_OK;
+}
+
+ace_status ace_cache_create(const ace_index* const* idx, uint32_t n, void* const* d_states, uint64_t n_slots,
+                            uint32_t max_reqs, void* d_mem, uint64_t bytes, const ace_tune* tune, cudaStream_t s,
+                            ace_cache** out) {
+  ace_status rc = cache_check(idx, n);
+  if (rc) return rc;
+  if (!out || !d_states || !d_mem || !aligned(d_mem, 256) || n_slots == 0 || max_reqs == 0) return ACE_E_INVAL;
+  const uint32_t log2B = idx[0]->h.log2_block;
+  CacheLayout C = cache_layout(idx, n, n_slots, max_reqs, log2B);
+  if (bytes < C.total) return ACE_E_NOMEM;
+  uint8_t* base = static_cast<uint8_t*>(d_mem);
+  std::vector<CacheArc> arcs(n);
+  for (uint32_t i = 0; i < n; i++) {
+    const ace_index* x = idx[i];
+    if (!d_states[i] || !aligned(d_states[i], 256)) return ACE_E_INVAL;
+    uint8_t* st = static_cast<uint8_t*>(d_states[i]);
+    uint64_t nb = x->h.n_blocks;
+    arcs[i] = CacheArc{x->d_arc,
+                       reinterpret_cast<const ace_block_dir*>(x->d_arc + x->h.dir_off),
+                       x->h.payload_off,
+                       x->h.total_size,
+                       x->d_dep_ptr,
+                       x->d_dep_iv,
+                       reinterpret_cast<uint32_t*>(st),
+                       reinterpret_cast<uint32_t*>(st + align256(4 * nb)),
+                       reinterpret_cast<uint32_t*>(st + 2 * align256(4 * nb)),
+                       (uint32_t)nb,
+                       x->h.off_width,
+                       0,
+                       0};
+    uint64_t sb = 0;
+    ace_archive_state_size(x, &sb);
+    if (cudaMemsetAsync(st, 0, sb, s) != cudaSuccess) return ACE_E_CUDA;
+  }
+  ace_cache* c = new (std::nothrow) ace_cache();
+  if (!c) return ACE_E_NOMEM;
+  c->device = idx[0]->device;
+  c->n_arcs = n;
+  c->log2B = log2B;
+  c->n_slots = (uint32_t)n_slots;
+  c->front_cap = (uint32_t)n_slots;
+  c->max_reqs = max_reqs;
+  c->mem = base;
+  c->bytes = bytes;
+  c->req_off = C.reqs;
+  rc = plan_launch<true>(idx[0], tune, n_slots, C.n_warps, &c->L);
+  if (rc == ACE_OK) {
+    int optin = 0;
+    if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device) != cudaSuccess ||
+        cudaFuncSetAttribute(cache_decode_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin) != cudaSuccess)
+      rc = ACE_E_CUDA;
+  }
+  // header (epoch 1: no block is cached, since every ready flag starts at 0)
+  CacheHdr h{};
+  h.epoch = 1;
+  if (rc == ACE_OK &&
+      (cudaMemcpyAsync(base, &h, sizeof h, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+       cudaMemcpyAsync(base + C.arcs, arcs.data(), n * sizeof(CacheArc), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+       cudaStreamSynchronize(s) != cudaSuccess))
+    rc = ACE_E_CUDA;
+  if (rc) {
+    delete c;
+    return rc;
+  }
+  CacheArgs& a = c->args;
+  a.h = reinterpret_cast<CacheHdr*>(base);
+  a.arcs = reinterpret_cast<const CacheArc*>(base + C.arcs);
+  a.n_arcs = n;
+  a.log2B = log2B;
+  a.n_slots = (uint32_t)n_slots;
+  a.front_cap = (uint32_t)n_slots;
+  a.front0 = reinterpret_cast<uint32_t*>(base + C.front0);
+  a.front1 = reinterpret_cast<uint32_t*>(base + C.front1);
+  a.work = reinterpret_cast<uint32_t*>(base + C.work);
+  a.arc_minmax = reinterpret_cast<uint32_t*>(base + C.minmax);
+  a.slots = base + C.slots;
+  a.reqs = nullptr;
+  a.n_reqs = 0;
+  CacheDecodeArgs& d = c->dargs;
+  d.window = c->L.chunk;
+  d.warp_smem = c->L.smem_per_warp;
+  d.esc_cap = esc_cap(log2B);
+  d.max_ntok = (uint32_t)C.max_ntok;
+  d.timeout_ns = c->L.timeout;
+  d.warp_scratch = base + C.warps;
+  d.warp_scratch_bytes = warp_scratch_bytes(C.max_ntok);
+  *out = c;
+  return ACE_OK;
+}
+
+ace_status ace_seek_batch(const ace_cache* c, const ace_seek_req* d_reqs, uint32_t n, void* d_pool, uint64_t pool_bytes,
+                          cudaStream_t s) {
+  if (!c || (!d_reqs && n) || (!d_pool && n)) return ACE_E_INVAL;
+  if (n == 0) return ACE_OK;
+  (void)pool_bytes;  // request ranges are validated on the host by ace_seek_batch_host
+  CacheArgs a = c->args;
+  a.reqs = d_reqs;
+  a.n_reqs = n;
+  cache_closure_kernel<<<1, 1024, 0, s>>>(a);
+  CacheDecodeArgs d = c->dargs;
+  d.c = a;
+  cache_decode_kernel<<<c->L.grid, 32 * c->L.warps, (size_t)c->L.warps * c->L.smem_per_warp, s>>>(d);
+  cache_copy_kernel<<<std::min<uint32_t>(n, 1024), 256, 0, s>>>(a, static_cast<uint8_t*>(d_pool));
+  CUDA_TRY(cudaGetLastError());
+  return ACE_OK;
+}
+
+ace_status ace_seek_batch_host(const ace_cache* c, const ace_seek_req* h_reqs, const uint64_t* h_totals, uint32_t n,
+                               void* d_pool, uint64_t pool_bytes, cudaStream_t s) {
+  if (!c || (!h_reqs && n)) return ACE_E_INVAL;
+  if (n > c->max_reqs) return ACE_E_NOMEM;
+  for (uint32_t i = 0; i < n; i++) {
+    const ace_seek_req& q = h_reqs[i];
+    if (q.archive >= c->n_arcs) return ACE_E_INVAL;
+    if (q.len == 0 || (h_totals && (q.coord >= h_totals[q.archive] || q.len > h_totals[q.archive] - q.coord)))
+      return ACE_E_RANGE;
+    if (q.out_off + q.len > pool_bytes) return ACE_E_NOMEM;
+  }
+  ace_seek_req* d = reinterpret_cast<ace_seek_req*>(c->mem + c->req_off);
+  if (n) CUDA_TRY(cudaMemcpyAsync(d, h_reqs, n * sizeof(ace_seek_req), cudaMemcpyHostToDevice, s));
+  return ace_seek_batch(c, d, n, d_pool, pool_bytes, s);
+}
+
+ace_status ace_cache_sync(const ace_cache* c, cudaStream_t s) {
+  if (!c) return ACE_E_INVAL;
+  CUDA_TRY(cudaStreamSynchronize(s));
+  CacheHdr h;
+  CUDA_TRY(cudaMemcpyAsync(&h, c->mem, sizeof h, cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  if (h.status) {
+    CUDA_TRY(cudaMemsetAsync(c->mem, 0, 3 * sizeof(uint32_t), s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+  }
+  return (ace_status)h.status;
+}
+
+ace_status ace_cache_usage(const ace_cache* c, uint32_t* used_slots, uint32_t* n_slots, cudaStream_t s) {
+  if (!c) return ACE_E_INVAL;
+  CacheHdr h;
+  CUDA_TRY(cudaMemcpyAsync(&h, c->mem, sizeof h, cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  if (used_slots) *used_slots = h.next_slot;
+  if (n_slots) *n_slots = c->n_slots;
+  return ACE_OK;
+}
+
+ace_status ace_cache_reset(const ace_cache* c, cudaStream_t s) {
+  if (!c) return ACE_E_INVAL;
+  cache_reset_kernel<<<1, 1, 0, s>>>(c->args.h);
+  CUDA_TRY(cudaGetLastError());
+  return ACE_OK;
+}
+
+ace_status ace_cache_free(ace_cache* c) {
+  delete c;
   return ACE_OK;
 }
 
