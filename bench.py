@@ -159,6 +159,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--seeks", type=int, default=10000)
     ap.add_argument("--no-extras", action="store_true", help="decode steps only (for profiler runs)")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
+    ap.add_argument("--serve-archive-mib", type=int, default=256, help="size of each served archive")
     args = ap.parse_args()
     assert args.warmup >= 3 or args.no_extras, "at least 3 warm-up steps"
 
@@ -270,10 +272,34 @@ def main():
             if i % 997 == 0:
                 assert torch.equal(seek_out, d_data[b * B:(b + 1) * B])
         lat_us = np.array(lat) * 1e6
+        # batched: the same 10,000 seeks in batches of 256 through one
+        # decoded-block cache (one closure, one decode, one copy per batch);
+        # a request's latency runs from its batch's submission to completion
+        from paper_2606_24531_gb300.serve import SeekCache
+
+        sc = SeekCache([da], n_slots=16384, max_reqs=256, pool_bytes=256 * B + 4096, device=dev)
+        blat, bt0 = [], time.perf_counter()
+        for s0 in range(0, len(blocks), 256):
+            chunk = [(0, int(b) * B, B) for b in blocks[s0:s0 + 256]]
+            t0 = time.perf_counter()
+            outs = sc.seek_many(chunk)
+            t1 = time.perf_counter()
+            blat += [t1 - t0] * len(chunk)
+            if s0 % 2560 == 0:
+                b = int(blocks[s0])
+                assert torch.equal(outs[0], d_data[b * B:(b + 1) * B])
+        bwall = time.perf_counter() - bt0
+        blat_us = np.array(blat) * 1e6
+        sc.close()
         result["seek"] = {"kind": "plain: ace_seek + ace_sync per 16 KiB block", "n": len(lat),
                           "p50_us": float(np.percentile(lat_us, 50)),
                           "p99_us": float(np.percentile(lat_us, 99)),
-                          "mean_us": float(lat_us.mean()), "batched": None,
+                          "mean_us": float(lat_us.mean()),
+                          "seeks_per_s": len(lat) / float(np.sum(lat)),
+                          "batched": {"kind": "ace_seek_batch, 256 per batch, decoded-block cache",
+                                      "p50_us": float(np.percentile(blat_us, 50)),
+                                      "p99_us": float(np.percentile(blat_us, 99)),
+                                      "seeks_per_s": len(blat) / bwall},
                           "paper_context_us": 334.0}
 
         # end to end through the C ABI from pinned host memory
@@ -331,6 +357,46 @@ def main():
                              "per_object_GBps": btotal / (per_obj_ms / 1e3) / 1e9,
                              "tuned": {k: tuned[k] for k in ("warps_per_cta", "window")}}
         db.close()
+
+        # serving: 8 resident archives (two per profile, 16 KiB blocks),
+        # Poisson arrivals of seeks at uniform offsets with log-uniform lengths
+        # from one block to 1 MiB, continuous batching on two streams under a
+        # device working-set budget, against one ace_seek per request
+        if not args.no_serve:
+            import synth
+            from paper_2606_24531_gb300.serve import Server, plain_latencies
+
+            profs = ["fastq", "fastq", "genome", "genome", "text", "text", "mixed", "mixed"]
+            mmp = {"fastq": 16, "genome": 20, "text": 4, "mixed": 4}
+            arch_bytes = args.serve_archive_mib << 20
+            sdas = []
+            for k, p in enumerate(profs):
+                dk = synth.generate(p, arch_bytes, 10 + k)
+                sdas.append(DeviceArchive(ace.ace_encode(dk, 14, mmp[p]), max_seek_blocks=1024, device=dev))
+            sizes = np.array([x.total for x in sdas], np.uint64)
+            budget = min(20 << 30, 4 << 30)
+            srv = Server(sdas, budget_bytes=budget, n_streams=2, max_batch=256, pool_bytes=96 << 20, device=dev)
+            rows = []
+            for lam in (1e4, 3e4, 1e5, 3e5, 1e6):
+                nreq = int(min(max(lam * 1.0, 2000), 100000))
+                tq, aq, cq, lq = synth.requests(5, nreq, lam, sizes, 1 << 14, 1 << 20)
+                res = srv.run(tq, aq, cq, lq, time_limit_s=3.0)
+                lt = res["latency_ns"][res["latency_ns"] >= 0] / 1e3
+                rows.append({"rate_per_s": lam, "requests": nreq, "served": res["served"],
+                             "p50_us": float(np.percentile(lt, 50)), "p99_us": float(np.percentile(lt, 99)),
+                             "GBps": res["bytes"] / res["seconds"] / 1e9, "batches": res["batches"],
+                             "cache_resets": res["resets"]})
+            tq, aq, cq, lq = synth.requests(5, 500, 1e4, sizes, 1 << 14, 1 << 20)
+            pl = plain_latencies(sdas, [x.d_scratch for x in sdas], aq, cq, lq) / 1e3
+            srv.close()
+            result["serve"] = {"archives": len(sdas), "archive_bytes": arch_bytes,
+                               "decompressed_total": int(sizes.sum()), "budget_bytes": budget,
+                               "working_set_bytes": srv.working_set_bytes(), "by_rate": rows,
+                               "plain": {"p50_us": float(np.percentile(pl, 50)),
+                                         "p99_us": float(np.percentile(pl, 99)),
+                                         "GBps": float(lq.sum()) / (float(pl.sum()) / 1e6) / 1e9}}
+            for x in sdas:
+                x.close()
 
         # the oracle on the host cores (rank 0 only)
         if rank == 0:
