@@ -256,12 +256,43 @@ __device__ __forceinline__ uint64_t src_index(uint64_t S, uint64_t d, uint32_t l
   return d >= len ? S + i : S + (i % (uint32_t)d);
 }
 
-// One lane copies one match.  Loads go in batches of 8 independent byte
-// loads before their stores, so a batch costs one memory round trip.
+// One lane copies one match.  A source that does not overlap its
+// destination is read as aligned 8-byte words, four per round trip; words
+// never cross a block (blocks are multiples of 8 bytes), and the word that
+// would pass the end of the output is read byte by byte.  An overlapping
+// source goes byte by byte in batches of 8 loads before their stores.
 template <bool SEEK>
 __device__ __forceinline__ void copy_match_lane(const DecodeArgs& a, uint8_t* dst, uint64_t D, uint64_t S,
                                                 uint32_t len) {
   const uint64_t d = D - S;
+  if (d >= len) {
+    const uint64_t a0 = S & ~7ull;
+    const uint32_t off = (uint32_t)(S & 7);
+    for (uint32_t w0 = 0; 8 * w0 < off + len; w0 += 4) {  // words w0 .. w0+3 of the source
+      uint64_t v[4];
+#pragma unroll
+      for (uint32_t j = 0; j < 4; j++) {
+        uint64_t q = a0 + 8ull * (w0 + j);
+        v[j] = 0;
+        if (8 * (w0 + j) < off + len) {
+          if (q + 8 <= a.total) {
+            v[j] = __ldcg(reinterpret_cast<const unsigned long long*>(Addr<SEEK>::at(a, q)));
+          } else {
+            for (uint32_t k = 0; k < 8 && q + k < a.total; k++)
+              v[j] |= (uint64_t)__ldcg(Addr<SEEK>::at(a, q + k)) << (8 * k);
+          }
+        }
+      }
+#pragma unroll
+      for (uint32_t j = 0; j < 4; j++)
+#pragma unroll
+        for (uint32_t k = 0; k < 8; k++) {
+          uint32_t qi = 8 * (w0 + j) + k;  // byte of the word run; destination byte qi - off
+          if (qi >= off && qi < off + len) dst[qi - off] = (uint8_t)(v[j] >> (8 * k));
+        }
+    }
+    return;
+  }
   for (uint32_t i0 = 0; i0 < len; i0 += 8) {
     uint8_t v[8];
 #pragma unroll

@@ -147,6 +147,8 @@ constexpr uint32_t kSeg = 128;
 struct Stream {
   const uint8_t* g;    // renormalisation bytes (16-byte aligned); the payload starts head bytes before
   uint32_t head;       // bytes of states, present bitmap and frequencies
+  uint32_t k;          // search mode: present symbols (0: slot table mode)
+  uint32_t kstep;      // search mode: largest power of two below k
   uint32_t nsym;       // symbols in the stream
   uint32_t nbytes;     // renormalisation bytes
   uint32_t next;       // next symbol index to decode
@@ -174,6 +176,7 @@ __device__ __forceinline__ bool stream_open(const uint8_t* pay, uint32_t sbytes,
   st.x = ACE_RANS_L;
   st.g = pay;
   st.head = 0;
+  st.k = st.kstep = 0;
   st.nbytes = 0;
   if (nsym == 0) return sbytes == 0;
   uint32_t x = reinterpret_cast<const uint32_t*>(pay)[lane];
@@ -197,11 +200,18 @@ __device__ __forceinline__ bool stream_open(const uint8_t* pay, uint32_t sbytes,
   return true;
 }
 
-// Builds the stream's decode tables: fc[s] = f_s << 16 | c_s, and the slot ->
-// symbol table by marking each symbol's first slot and taking a prefix
-// maximum (symbols increase with their slots).  Returns false (all lanes) if
-// the frequencies do not sum to 4096.
-__device__ __forceinline__ bool lut_build(const Stream& st, Lut& lut, uint32_t lane) {
+// Streams this short are decoded by searching the present symbols' ranges
+// instead of building the 4096-entry slot table: fewer rounds than the table
+// costs to build.
+constexpr uint32_t kSearchMaxSymbols = 2048;
+
+// Builds the stream's decode tables.  Slot table mode: fc[s] = f_s << 16 |
+// c_s, and the slot -> symbol table by marking each symbol's first slot and
+// taking a prefix maximum (symbols increase with their slots).  Search mode
+// (short streams): one sorted word per present symbol, c << 20 | (f - 1) << 8
+// | s, searched per symbol.  Returns false (all lanes) if the frequencies do
+// not sum to 4096.
+__device__ __forceinline__ bool lut_build(Stream& st, Lut& lut, uint32_t lane) {
   if (st.nsym == 0) return true;
   const uint8_t* sp = st.g - st.head;
   uint32_t bm = sp[128 + lane];
@@ -224,6 +234,22 @@ __device__ __forceinline__ bool lut_build(const Stream& st, Lut& lut, uint32_t l
   uint32_t cincl = warp_incl_sum(fsum, lane);
   bad |= __shfl_sync(kFull, cincl, 31) != ACE_SCALE;
   if (__any_sync(kFull, bad)) return false;
+  if (st.nsym <= kSearchMaxSymbols) {
+    uint32_t* pk = reinterpret_cast<uint32_t*>(lut.sym);
+    uint32_t c = cincl - fsum, j = first;
+#pragma unroll
+    for (int q = 0; q < 8; q++)
+      if (f[q]) {
+        pk[j++] = (c << 20) | ((f[q] - 1) << 8) | (lane * 8 + q);
+        c += f[q];
+      }
+    uint32_t k = __shfl_sync(kFull, warp_incl_sum(cnt, lane), 31);
+    st.k = k;
+    st.kstep = k > 1 ? 1u << (31 - __clz(k - 1)) : 0u;
+    __syncwarp();
+    return true;
+  }
+  st.k = 0;
   uint4* sym4 = reinterpret_cast<uint4*>(lut.sym);
 #pragma unroll
   for (int j = 0; j < 8; j++) sym4[lane * 8 + j] = make_uint4(0, 0, 0, 0);
@@ -263,6 +289,28 @@ __device__ __forceinline__ bool lut_build(const Stream& st, Lut& lut, uint32_t l
   return true;
 }
 
+// The symbol owning a slot, with its frequency and cumulative frequency.
+__device__ __forceinline__ void lookup(const Stream& st, const Lut& lut, uint32_t slot, uint32_t& s, uint32_t& f,
+                                       uint32_t& c) {
+  if (st.k) {
+    const uint32_t* pk = reinterpret_cast<const uint32_t*>(lut.sym);
+    uint32_t lo = 0;
+    for (uint32_t step = st.kstep; step; step >>= 1) {
+      uint32_t j = lo + step;
+      if (j < st.k && (pk[j] >> 20) <= slot) lo = j;
+    }
+    uint32_t e = pk[lo];
+    s = e & 0xffu;
+    f = ((e >> 8) & 0xfffu) + 1;
+    c = e >> 20;
+  } else {
+    s = lut.sym[slot];
+    uint32_t fc = lut.fc[s];
+    f = fc >> 16;
+    c = fc & 0xffffu;
+  }
+}
+
 // Decodes one round of up to 32 symbols of [st.next, end): symbol i is on
 // lane i mod 32 (interleaved rANS).  slot = x mod 4096, s = sym[slot],
 // x <- f_s floor(x / 4096) + slot - c_s; then x takes k in {0,1,2} bytes,
@@ -286,9 +334,9 @@ __device__ __forceinline__ uint32_t rans_round(Stream& st, uint8_t* ring, const 
   act = i >= st.next && i < end;
   uint32_t x = st.x;
   uint32_t slot = x & (ACE_SCALE - 1);
-  uint32_t s = lut.sym[slot];
-  uint32_t fc = lut.fc[s];
-  uint32_t xn = (fc >> 16) * (x >> ACE_SCALE_BITS) + slot - (fc & 0xffffu);
+  uint32_t s, f, c;
+  lookup(st, lut, slot, s, f, c);
+  uint32_t xn = f * (x >> ACE_SCALE_BITS) + slot - c;
   bool p1 = act && xn < ACE_RANS_L, p2 = act && xn < (1u << 15);
   uint32_t b1 = __ballot_sync(kFull, p1), b2 = __ballot_sync(kFull, p2);
   uint32_t p = st.pos + __popc(b1 & lt) + __popc(b2 & lt);
@@ -312,9 +360,9 @@ __device__ __forceinline__ uint32_t rans_round_full(Stream& st, uint8_t* ring, c
   }
   uint32_t x = st.x;
   uint32_t slot = x & (ACE_SCALE - 1);
-  uint32_t s = lut.sym[slot];
-  uint32_t fc = lut.fc[s];
-  uint32_t xn = (fc >> 16) * (x >> ACE_SCALE_BITS) + slot - (fc & 0xffffu);
+  uint32_t s, f, c;
+  lookup(st, lut, slot, s, f, c);
+  uint32_t xn = f * (x >> ACE_SCALE_BITS) + slot - c;
   bool p1 = xn < ACE_RANS_L, p2 = xn < (1u << 15);
   uint32_t b1 = __ballot_sync(kFull, p1), b2 = __ballot_sync(kFull, p2);
   uint32_t p = st.pos + __popc(b1 & lt) + __popc(b2 & lt);
