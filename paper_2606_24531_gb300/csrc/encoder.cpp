@@ -37,6 +37,7 @@ constexpr int kStride = 8;      // positions inserted into the global table
 constexpr uint64_t kEmpty = ~0ull;
 constexpr uint64_t kWindow = 64;   // blocks parsed together; they take no sources from each other
 constexpr uint32_t kMaxLevel = 3;  // default cap on a block's dependency level
+constexpr uint32_t kMaxWave = 3;   // cap on the in-block resolution wave of a match
 
 inline uint64_t load64(const uint8_t* p) {
   uint64_t v;
@@ -196,8 +197,8 @@ void build_global(const uint8_t* in, uint64_t n, unsigned threads, Global& g) {
 struct Parser {
   static constexpr int kHashBits = 15;
   std::vector<int32_t> head, prev;
-  std::vector<uint32_t> copied;  // prefix count of block bytes written by matches
-  explicit Parser(uint32_t B) : head(1u << kHashBits), prev(B), copied(B + 1) {}
+  std::vector<uint8_t> wave;  // per block byte: the decoder's resolution wave (0: a literal)
+  explicit Parser(uint32_t B) : head(1u << kHashBits), prev(B), wave(B) {}
 };
 
 // Where a block may take match sources from: its own earlier bytes, and
@@ -245,37 +246,52 @@ void parse_block(const uint8_t* in, uint64_t n, uint64_t b, uint64_t bstart, uin
       ps.head[h] = (int32_t)(inserted - bstart);
     }
   };
-  // A candidate is "direct" when the bytes it reads inside this block were
-  // all literals: it then depends on no earlier match of the block, and the
-  // decoder resolves it in its first wave.  Near-equal direct candidates are
-  // preferred over longer ones that would chain match on match.
-  auto direct = [&](uint64_t q, uint64_t len, uint64_t p) {
-    if (q + len <= bstart) return true;
-    uint64_t lo = std::max(q, bstart) - bstart, hi = std::min(q + len, p) - bstart;
-    return ps.copied[hi] == ps.copied[lo];
+  // The decoder resolves a block's matches in waves: a match reading only
+  // literals (or bytes of earlier blocks) resolves in wave 1, one reading
+  // bytes written by wave-k matches in wave k + 1.  Candidates deeper than
+  // kMaxWave are refused, and a shallower candidate within max(4, len/8)
+  // bytes of the longest is preferred, so chains of match on match stay
+  // short.  A source overlapping its own destination reads only [q, p).
+  auto wave_of = [&](uint64_t q, uint64_t len, uint64_t p) -> uint32_t {
+    uint64_t lo = std::max(q, bstart), hi = std::min(q + len, p);
+    uint32_t w = 0;
+    for (uint64_t k = lo; k < hi; k++) w = std::max<uint32_t>(w, ps.wave[k - bstart]);
+    return w + 1;
   };
   uint64_t p = bstart;
   uint32_t lit = 0;
-  ps.copied[0] = 0;
   while (p < bend) {
     insert_upto(p);
-    uint64_t best_len = 0, best_q = 0, dir_len = 0, dir_q = 0;
+    uint64_t best_len = 0, best_q = 0;
+    uint32_t best_w = 0;
     uint64_t room = bend - p;
     auto consider = [&](uint64_t q, uint64_t l) {
-      if (l > best_len || (l == best_len && l > 0 && q < best_q)) {
+      if (l < min_match) return;
+      uint64_t slack = std::max<uint64_t>(4, std::max(l, best_len) / 8);
+      if (best_len && l + slack < best_len) return;  // too short to matter
+      uint32_t w = wave_of(q, l, p);
+      if (w > kMaxWave) return;
+      bool take;
+      if (!best_len) take = true;
+      else if (w < best_w) take = l + slack >= best_len;                // shallower, nearly as long
+      else if (w > best_w) take = l > best_len + std::max<uint64_t>(4, l / 8);  // deeper: only if clearly longer
+      else take = l > best_len || (l == best_len && q < best_q);
+      if (take) {
         best_len = l;
         best_q = q;
-      }
-      if ((l > dir_len || (l == dir_len && l > 0 && q < dir_q)) && direct(q, l, p)) {
-        dir_len = l;
-        dir_q = q;
+        best_w = w;
       }
     };
     if (room >= min_match) {
       if (p + 4 <= bend) {  // repeats inside the block, most recent first
         uint32_t depth = 0;
-        for (int32_t r = ps.head[hash4(in + p, Parser::kHashBits)]; r >= 0 && depth < max_chain;
-             r = ps.prev[r], depth++) {
+        int32_t r = ps.head[hash4(in + p, Parser::kHashBits)];
+        for (; r >= 0 && depth < max_chain; r = ps.prev[r], depth++) {
+          uint64_t q = bstart + (uint64_t)r;
+          consider(q, common(in + q, in + p, room));
+        }
+        // past the usual depth, look further back for a shallower source
+        for (uint32_t extra = 0; r >= 0 && extra < 16 * max_chain && best_w > 1; r = ps.prev[r], extra++) {
           uint64_t q = bstart + (uint64_t)r;
           consider(q, common(in + q, in + p, room));
         }
@@ -290,17 +306,13 @@ void parse_block(const uint8_t* in, uint64_t n, uint64_t b, uint64_t bstart, uin
         consider(q, l);
       }
     }
-    if (dir_len >= min_match && dir_len + std::max<uint64_t>(4, best_len / 8) >= best_len) {
-      best_len = dir_len;
-      best_q = dir_q;
-    }
     if (best_len >= min_match) {
       toks.push_back({lit, (uint32_t)best_len, best_q});
       lit = 0;
-      for (uint64_t k = p; k < p + best_len; k++) ps.copied[k - bstart + 1] = ps.copied[k - bstart] + 1;
+      for (uint64_t k = p; k < p + best_len; k++) ps.wave[k - bstart] = (uint8_t)best_w;
       p += best_len;
     } else {
-      ps.copied[p - bstart + 1] = ps.copied[p - bstart];
+      ps.wave[p - bstart] = 0;
       lit++;
       p++;
     }
