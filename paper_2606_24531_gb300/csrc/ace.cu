@@ -28,6 +28,7 @@ __host__ __device__ inline uint32_t esc_cap(uint32_t log2B) { return 2 * ((1u <<
 // ------------------------------------------------------------ index kernels
 
 struct IndexArgs {
+  uint64_t* match_ptr;  // n_blocks + 1 entries: first match record of each block
   const uint8_t* arc;
   const ace_block_dir* dir;
   const uint32_t* dep_ptr;
@@ -78,6 +79,44 @@ __global__ void validate_kernel(IndexArgs a) {
   }
   if (where) record_error(&a.ih->status, &a.ih->err_block, &a.ih->err_where, ACE_E_CORRUPT, (uint32_t)b, where);
   else atomicMax(&a.ih->max_ntok, d.ntok);
+  a.match_ptr[b + 1] = d.ntok ? d.ntok - 1 : 0;  // this block's matches; scanned below
+}
+
+// Inclusive scan of the per-block match counts into record offsets (one CTA).
+__global__ void match_scan_kernel(IndexArgs a) {
+  __shared__ unsigned long long carry;
+  __shared__ unsigned long long wsum[32];
+  if (threadIdx.x == 0) {
+    carry = 0;
+    a.match_ptr[0] = 0;
+  }
+  __syncthreads();
+  uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (uint64_t c0 = 1; c0 <= a.nb; c0 += blockDim.x) {
+    uint64_t i = c0 + threadIdx.x;
+    unsigned long long v = i <= a.nb ? a.match_ptr[i] : 0, incl = v;
+    for (int d = 1; d < 32; d <<= 1) {
+      unsigned long long u = __shfl_up_sync(kFull, incl, d);
+      if (lane >= (uint32_t)d) incl += u;
+    }
+    if (lane == 31) wsum[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+      unsigned long long x = lane < nw ? wsum[lane] : 0, xi = x;
+      for (int d = 1; d < 32; d <<= 1) {
+        unsigned long long u = __shfl_up_sync(kFull, xi, d);
+        if (lane >= (uint32_t)d) xi += u;
+      }
+      if (lane < nw) wsum[lane] = xi - x;
+    }
+    __syncthreads();
+    unsigned long long out = carry + wsum[wid] + incl;
+    if (i <= a.nb) a.match_ptr[i] = out;
+    __syncthreads();
+    if (threadIdx.x == blockDim.x - 1) carry = out;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) a.ih->n_matches = carry;
 }
 
 // Dependency levels: level[b] = 0 without sources in other blocks, else
@@ -172,6 +211,8 @@ struct DecodeArgs {
   uint64_t timeout_ns;
   uint8_t* warp_scratch;   // per-warp token records
   uint64_t warp_scratch_bytes;
+  MatchRec* recs;          // match records between the two passes
+  const uint64_t* match_ptr;  // whole decode: block -> first record; null: max_ntok records per slot
 };
 
 // Shared memory of one warp: one stream's tables at a time, the three
@@ -331,15 +372,21 @@ __device__ __forceinline__ uint64_t read_src(const uint8_t* q, uint32_t w) {
   return S;
 }
 
-// Decodes one block through both layers (Section 3 entry point, then the
-// Section 2 match layer) into its place, in four phases: the length stream
-// (parsed into token records), the offset stream, the literals (placed
-// straight at their output positions), and the matches (resolved in
-// dependency waves).  Each phase builds its stream's tables once.  Returns
-// false if the block is corrupt or a wait gave up (the error is recorded).
+// The records of block b (slot-addressed modes keep max_ntok per slot).
 template <bool SEEK>
-__device__ bool decode_block(const DecodeArgs& a, const WarpMem& m, const TokRec& g, uint32_t b, uint32_t lane,
-                             uint32_t epoch) {
+__device__ __forceinline__ MatchRec* recs_of(const DecodeArgs& a, uint32_t b) {
+  if (!SEEK) return a.recs + __ldg(a.match_ptr + b);
+  return a.recs + (uint64_t)__ldg(a.slot_of + b) * a.max_ntok;
+}
+
+// Entropy pass of one block (Section 3: the block boundary is the entry
+// point of the entropy layer): the length stream parsed into token
+// positions, the offset stream, and the literals placed straight at their
+// output positions.  The block's matches are left as records for the match
+// pass.  Each stream's tables are built once.  Returns false if the block is
+// corrupt (the error is recorded).
+template <bool SEEK>
+__device__ bool entropy_block(const DecodeArgs& a, const WarpMem& m, const TokRec& g, uint32_t b, uint32_t lane) {
   bool ok = true;
   const uint32_t* dw = reinterpret_cast<const uint32_t*>(a.dir + b);
   uint32_t dv = lane < 16 ? __ldg(dw + lane) : 0u;
@@ -427,6 +474,18 @@ __device__ bool decode_block(const DecodeArgs& a, const WarpMem& m, const TokRec
       });
   }
   __syncwarp();
+  // the match records: absolute source, destination in the block, length
+  if (ok) {
+    MatchRec* rec = recs_of<SEEK>(a, b);
+    for (uint32_t t = lane; t < nm; t += 32) {
+      uint32_t ml = g.tml[t];
+      uint64_t S = read_src(g.offb + w * t, w);
+      uint32_t dl = g.tdst[t + 1] - ml;
+      if (ml && S >= bstart + dl) bad = true;  // a source must precede its destination
+      rec[t] = MatchRec{S, dl, ml};
+    }
+    if (__any_sync(kFull, bad)) fail(a, ok, ACE_E_CORRUPT, b, 37, lane);
+  }
 
   // ---- literals: literal i lands at its token's run start plus its offset in
   // the run; token positions come through a shared-memory window
@@ -456,31 +515,52 @@ __device__ bool decode_block(const DecodeArgs& a, const WarpMem& m, const TokRec
     }
   }
 
-  // ---- matches, in groups whose records sit in shared memory (the window)
-  uint64_t* gS = reinterpret_cast<uint64_t*>(m.tdst);              // [kMatchGroup] sources
-  uint32_t* gD = reinterpret_cast<uint32_t*>(gS + kMatchGroup);     // [kMatchGroup] destinations in the block
-  uint32_t* gL = gD + kMatchGroup;                                  // [kMatchGroup] lengths
+  if (ok) {
+    bool fin = stream_finished(st[0]) && stream_finished(st[1]) && stream_finished(st[2]);
+    if (!__all_sync(kFull, fin)) fail(a, ok, ACE_E_CORRUPT, b, 40, lane);
+  }
+  cp_async_wait<0>();  // no ring fill may land after the next block reuses the rings
+  __syncwarp();
+  return ok;
+}
+
+// Match pass of one block (Section 2: a block decodes once the blocks holding
+// its sources are present): waits, bounded, for the source blocks, then
+// resolves the matches in dependency waves -- a match whose read range ends
+// at or before the destination of the first pending match reads only
+// finished bytes.  Returns false if a record is corrupt or a wait gave up.
+template <bool SEEK>
+__device__ bool match_block(const DecodeArgs& a, MatchRec* gm, uint32_t b, uint32_t lane, uint32_t epoch) {
+  bool ok = true, bad = false;
+  const uint32_t ntok = __ldg(reinterpret_cast<const uint32_t*>(a.dir + b) + 12);
+  const uint32_t nm = ntok ? ntok - 1 : 0;
+  const uint64_t B = (uint64_t)1 << a.log2B, bstart = (uint64_t)b << a.log2B;
+  const uint32_t blen = (uint32_t)min(B, a.total - bstart);
+  uint8_t* obase = SEEK ? a.out + ((uint64_t)__ldg(a.slot_of + b) << a.log2B) : a.out + bstart;
+  const MatchRec* rec = recs_of<SEEK>(a, b);
+  uint64_t* gS = reinterpret_cast<uint64_t*>(gm);                 // [kMatchGroup] sources
+  uint32_t* gD = reinterpret_cast<uint32_t*>(gS + kMatchGroup);   // [kMatchGroup] destinations in the block
+  uint32_t* gL = gD + kMatchGroup;                                // [kMatchGroup] lengths
   for (uint32_t t0 = 0; ok && t0 < nm; t0 += kMatchGroup) {
     const uint32_t gn = min(kMatchGroup, nm - t0);
     bool timeout = false;
     for (uint32_t j = lane; j < gn; j += 32) {
-      uint32_t t = t0 + j;
-      uint32_t ml = g.tml[t];
-      uint64_t S = read_src(g.offb + w * t, w);
-      uint32_t dl = g.tdst[t + 1] - ml;
-      uint64_t D = bstart + dl;
+      const MatchRec r = rec[t0 + j];
+      uint64_t S = r.S, D = bstart + r.D;
+      uint32_t ml = r.L;
       gS[j] = S;
-      gD[j] = dl;
+      gD[j] = r.D;
       gL[j] = ml;
       if (!ml) continue;
-      if (S >= D) {
+      if (S >= D || (uint64_t)r.D + ml > blen) {  // records are checked again: the entropy pass may have failed
         bad = true;
+        gL[j] = 0;
         continue;
       }
       uint64_t rend = S + min((uint64_t)ml, D - S);
       uint64_t k0 = S >> a.log2B, k1 = (rend - 1) >> a.log2B;
       for (uint64_t k = k0; k <= k1 && k < b && !timeout; k++)
-        if (!wait_flag(a.ready + k, epoch, a.timeout_ns)) timeout = true;
+        if (!wait_flag(a.ready + k, epoch, a.timeout_ns, &a.sh->status)) timeout = true;
     }
     if (__any_sync(kFull, bad)) fail(a, ok, ACE_E_CORRUPT, b, 37, lane);
     if (__any_sync(kFull, timeout)) fail(a, ok, ACE_E_TIMEOUT, b, 38, lane);
@@ -528,42 +608,56 @@ __device__ bool decode_block(const DecodeArgs& a, const WarpMem& m, const TokRec
       __syncwarp();
     }
   }
-  if (ok) {
-    bool fin = stream_finished(st[0]) && stream_finished(st[1]) && stream_finished(st[2]);
-    if (!__all_sync(kFull, fin)) fail(a, ok, ACE_E_CORRUPT, b, 40, lane);
-  }
-  cp_async_wait<0>();  // no ring fill may land after the next block reuses the rings
   __syncwarp();
   return ok;
 }
 
-template <bool SEEK>
+enum { PASS_ENTROPY = 0, PASS_MATCH = 1 };
+
+// The match pass keeps only its match-record area in shared memory.
+constexpr uint32_t kMatchSmem = 16 * kMatchGroup;
+
+// Publishes block b (its writes visible device-wide before the flag).
+__device__ __forceinline__ void publish(uint32_t* ready, uint32_t b, uint32_t epoch, uint32_t lane) {
+  __threadfence();
+  __syncwarp();
+  if (lane == 0) st_release(ready + b, epoch);
+}
+
+// One pass over a work list by persistent warps: the entropy pass decodes
+// every block's streams and places its literals; the match pass, launched
+// after it, resolves every block's matches in (level, block) order and
+// publishes the block.
+template <bool SEEK, int PASS>
 __global__ void __launch_bounds__(256, 3) decode_kernel(DecodeArgs a) {
   extern __shared__ __align__(16) uint8_t smem[];
   const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const uint32_t epoch = *(volatile uint32_t*)&a.sh->epoch;
+  const uint32_t n_items = SEEK ? *(volatile uint32_t*)&a.sh->n_work : a.n_items;
+  uint32_t* ticket = PASS == PASS_ENTROPY ? &a.sh->ticket : &a.sh->ticket2;
   WarpMem m = carve(smem + (size_t)wid * a.warp_smem, a.window);
   TokRec g = tok_records(a.warp_scratch + (size_t)(blockIdx.x * (blockDim.x >> 5) + wid) * a.warp_scratch_bytes,
                          a.max_ntok);
-  const uint32_t epoch = *(volatile uint32_t*)&a.sh->epoch;
-  const uint32_t n_items = SEEK ? *(volatile uint32_t*)&a.sh->n_work : a.n_items;
+  MatchRec* gm = reinterpret_cast<MatchRec*>(smem + (size_t)wid * kMatchSmem);
   while (true) {
     uint32_t it = 0;
-    if (lane == 0) it = atomicAdd(&a.sh->ticket, 1u);
+    if (lane == 0) it = atomicAdd(ticket, 1u);
     it = __shfl_sync(kFull, it, 0);
     if (it >= n_items) break;
     uint32_t b = __ldg(a.items + it);
-    bool ok = decode_block<SEEK>(a, m, g, b, lane, epoch);
-    if (SEEK && ok) {
+    if (PASS == PASS_ENTROPY) {
+      entropy_block<SEEK>(a, m, g, b, lane);
+      continue;
+    }
+    bool ok = match_block<SEEK>(a, gm, b, lane, epoch);
+    if (SEEK && ok && a.slice) {
       // copy the part of this block inside [coord, coord + len) to the caller
       uint64_t bs = (uint64_t)b << a.log2B, be = min(bs + ((uint64_t)1 << a.log2B), a.total);
       uint64_t lo = max(bs, a.coord), hi = min(be, a.coord + a.len);
       const uint8_t* src = a.out + ((uint64_t)a.slot_of[b] << a.log2B) - bs;
       for (uint64_t p = lo + lane; p < hi; p += 32) a.slice[p - a.coord] = __ldcg(src + p);
     }
-    // publish: all lanes' writes are visible device-wide before the flag
-    __threadfence();
-    __syncwarp();
-    if (lane == 0) st_release(a.ready + b, epoch);
+    publish(a.ready, b, epoch, lane);
   }
 }
 
@@ -578,6 +672,8 @@ struct ObjDesc {
   uint8_t* out;
   uint32_t* ready;
   const uint32_t* order;  // the archive's blocks in (level, block) order
+  MatchRec* recs;         // the archive's match records
+  const uint64_t* match_ptr;
   uint32_t log2B, w, nb, pad;
 };
 
@@ -592,20 +688,23 @@ struct BatchArgs {
   uint64_t warp_scratch_bytes;
 };
 
-// Thousands of independent archives in one persistent launch: warps take
-// (archive, block) items from one ticket; each archive's items are in its
-// own (level, block) order, so a warp only ever waits on blocks of its
-// archive that were handed out before its own.
+// Thousands of independent archives in one persistent launch per pass:
+// warps take (archive, block) items from one ticket; each archive's items
+// are in its own (level, block) order, so in the match pass a warp only
+// ever waits on blocks of its archive that were handed out before its own.
+template <int PASS>
 __global__ void __launch_bounds__(256, 3) batch_decode_kernel(BatchArgs ba) {
   extern __shared__ __align__(16) uint8_t smem[];
   const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   WarpMem m = carve(smem + (size_t)wid * ba.warp_smem, ba.window);
   TokRec g = tok_records(ba.warp_scratch + (size_t)(blockIdx.x * (blockDim.x >> 5) + wid) * ba.warp_scratch_bytes,
                          ba.max_ntok);
+  MatchRec* gm = reinterpret_cast<MatchRec*>(smem + (size_t)wid * kMatchSmem);
   const uint32_t epoch = *(volatile uint32_t*)&ba.sh->epoch;
+  uint32_t* ticket = PASS == PASS_ENTROPY ? &ba.sh->ticket : &ba.sh->ticket2;
   while (true) {
     uint32_t it = 0;
-    if (lane == 0) it = atomicAdd(&ba.sh->ticket, 1u);
+    if (lane == 0) it = atomicAdd(ticket, 1u);
     it = __shfl_sync(kFull, it, 0);
     if (it >= ba.n_items) break;
     uint32_t lo = 0, hi = ba.n_objs;  // the archive o with item_start[o] <= it < item_start[o + 1]
@@ -631,11 +730,15 @@ __global__ void __launch_bounds__(256, 3) batch_decode_kernel(BatchArgs ba) {
     a.sh = ba.sh;
     a.ready = od.ready;
     a.timeout_ns = ba.timeout_ns;
+    a.recs = od.recs;
+    a.match_ptr = od.match_ptr;
     uint32_t b = __ldg(od.order + (it - __ldg(ba.item_start + lo)));
-    decode_block<false>(a, m, g, b, lane, epoch);
-    __threadfence();
-    __syncwarp();
-    if (lane == 0) st_release(od.ready + b, epoch);
+    if (PASS == PASS_ENTROPY) {
+      entropy_block<false>(a, m, g, b, lane);
+    } else {
+      match_block<false>(a, gm, b, lane, epoch);
+      publish(od.ready, b, epoch, lane);
+    }
   }
 }
 
@@ -666,6 +769,7 @@ __global__ void closure_kernel(ClosureArgs a) {
   if (tid == 0) {
     a.sh->epoch += 1;
     a.sh->ticket = 0;
+    a.sh->ticket2 = 0;
     s_min = (uint32_t)a.first;
   }
   uint32_t ntar = (uint32_t)(a.last - a.first + 1);
@@ -764,9 +868,12 @@ struct CacheHdr {
   uint32_t n_work;
   uint32_t next_slot;  // slots handed out in this epoch
   uint32_t n_front;
-  uint32_t pad[56];
+  uint32_t pad0[4];
+  uint32_t ticket2;    // next work item of the match pass
+  uint32_t pad[51];
 };
 static_assert(sizeof(CacheHdr) == 256, "cache header");
+static_assert(offsetof(CacheHdr, ticket2) == offsetof(ScratchHdr, ticket2), "shared header fields");
 static_assert(offsetof(CacheHdr, epoch) == offsetof(ScratchHdr, epoch), "shared header fields");
 static_assert(offsetof(CacheHdr, ticket) == offsetof(ScratchHdr, ticket), "shared header fields");
 static_assert(offsetof(CacheHdr, n_work) == offsetof(ScratchHdr, n_work), "shared header fields");
@@ -783,6 +890,7 @@ struct CacheArgs {
   uint32_t* work;     // (archive, block) pairs in decode order
   uint32_t* arc_minmax;  // per archive: smallest, largest block marked
   uint8_t* slots;
+  MatchRec* recs;     // max_ntok match records per slot
   const ace_seek_req* reqs;
   uint32_t n_reqs;
 };
@@ -909,6 +1017,7 @@ __global__ void cache_closure_kernel(CacheArgs c) {
     }
     c.h->n_work = n;
     c.h->ticket = 0;
+    c.h->ticket2 = 0;
   }
 }
 
@@ -920,20 +1029,23 @@ struct CacheDecodeArgs {
   uint64_t warp_scratch_bytes;
 };
 
-// Decodes a batch's work list into cache slots: the same two-layer block
-// decode as a seek, archive by archive.
+// Decodes a batch's work list into cache slots: the same two passes as a
+// seek, archive by archive.
+template <int PASS>
 __global__ void __launch_bounds__(256, 3) cache_decode_kernel(CacheDecodeArgs ca) {
   extern __shared__ __align__(16) uint8_t smem[];
   const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   WarpMem m = carve(smem + (size_t)wid * ca.warp_smem, ca.window);
   TokRec g = tok_records(ca.warp_scratch + (size_t)(blockIdx.x * (blockDim.x >> 5) + wid) * ca.warp_scratch_bytes,
                          ca.max_ntok);
+  MatchRec* gm = reinterpret_cast<MatchRec*>(smem + (size_t)wid * kMatchSmem);
   const CacheArgs& c = ca.c;
   const uint32_t epoch = *(volatile uint32_t*)&c.h->epoch;
   const uint32_t n_items = *(volatile uint32_t*)&c.h->n_work;
+  uint32_t* ticket = PASS == PASS_ENTROPY ? &c.h->ticket : &c.h->ticket2;
   while (true) {
     uint32_t it = 0;
-    if (lane == 0) it = atomicAdd(&c.h->ticket, 1u);
+    if (lane == 0) it = atomicAdd(ticket, 1u);
     it = __shfl_sync(kFull, it, 0);
     if (it >= n_items) break;
     const uint32_t ai = __ldg(c.work + 2 * it), b = __ldg(c.work + 2 * it + 1);
@@ -955,10 +1067,14 @@ __global__ void __launch_bounds__(256, 3) cache_decode_kernel(CacheDecodeArgs ca
     a.ready = arc.ready;
     a.slot_of = arc.slot_of;
     a.timeout_ns = ca.timeout_ns;
-    decode_block<true>(a, m, g, b, lane, epoch);
-    __threadfence();
-    __syncwarp();
-    if (lane == 0) st_release(arc.ready + b, epoch);
+    a.recs = c.recs;
+    a.match_ptr = nullptr;
+    if (PASS == PASS_ENTROPY) {
+      entropy_block<true>(a, m, g, b, lane);
+    } else {
+      match_block<true>(a, gm, b, lane, epoch);
+      publish(arc.ready, b, epoch, lane);
+    }
   }
 }
 
@@ -983,6 +1099,7 @@ __global__ void cache_reset_kernel(CacheHdr* h) {
   h->epoch += 1;
   h->next_slot = 0;
   h->ticket = 0;
+  h->ticket2 = 0;
   h->n_work = 0;
 }
 
@@ -1011,6 +1128,7 @@ __global__ void count_pattern_mismatch_kernel(const uint8_t* p, uint64_t n, uint
 __global__ void begin_call_kernel(ScratchHdr* sh) {
   sh->epoch += 1;
   sh->ticket = 0;
+  sh->ticket2 = 0;
 }
 
 // FNV-1a 64 (Fowler/Noll/Vo): sequential by definition, one thread.
@@ -1041,17 +1159,19 @@ struct ace_index {
   uint64_t n_iv;
   uint32_t n_levels;
   uint32_t max_ntok;
+  uint64_t n_matches;
+  uint64_t* d_match_ptr;
   int device;
   int num_sms;
   ace_tune tune;
-  // occupancy of the decode kernels, per (seek?, warps per CTA, chunk)
-  mutable int occ_cache[2][9][9];
+  // occupancy of the decode kernels, per (seek?, pass, warps per CTA, window)
+  mutable int occ_cache[2][2][9][9];
 };
 
 namespace {
 
 struct IndexLayout {
-  uint64_t level, order, lv_count, lv_cursor, total;
+  uint64_t level, order, lv_count, lv_cursor, match_ptr, total;
 };
 
 IndexLayout index_layout(uint64_t nb) {
@@ -1065,14 +1185,21 @@ IndexLayout index_layout(uint64_t nb) {
   o = align256(o + 4 * (nb + 1));
   L.lv_cursor = o;
   o = align256(o + 4 * (nb + 1));
+  L.match_ptr = o;
+  o = align256(o + 8 * (nb + 1));
   L.total = o;
   return L;
 }
 
 struct ScratchLayout {
-  uint64_t ready, slot_of, work, marks, front0, front1, warps, slots, total;
+  uint64_t ready, slot_of, work, marks, front0, front1, warps, tail, total;
   uint64_t n_warps;  // per-warp token regions available
 };
+
+// Bytes one seek slot needs: the decoded block and its match records.
+inline uint64_t slot_bytes(uint32_t log2B, uint64_t max_ntok) {
+  return (1ull << log2B) + 16 * max_ntok;
+}
 
 constexpr uint32_t kMaxWindow = 256;
 constexpr uint32_t kMaxWarpsPerCta = 8;  // the decode kernel's launch bounds: 256 threads
@@ -1080,9 +1207,11 @@ constexpr uint32_t kMaxWarpsPerSM = 32;  // per-warp token regions provisioned p
 
 // One layout serves every call on a scratch buffer, so whole decodes and
 // seeks may share it: header, ready flags, the seek's slot map, work list,
-// closure marks and frontiers, the per-warp token regions, then (for seeks)
-// the block slots.
-ScratchLayout scratch_layout(uint64_t nb, uint32_t log2B, uint64_t max_seek, int num_sms, uint64_t max_ntok) {
+// closure marks and frontiers, the per-warp token regions, then a tail that a
+// whole decode uses for the archive's match records and a seek for its block
+// slots followed by their match records.
+ScratchLayout scratch_layout(uint64_t nb, uint32_t log2B, uint64_t max_seek, int num_sms, uint64_t max_ntok,
+                             uint64_t n_matches) {
   ScratchLayout L;
   uint64_t o = sizeof(ScratchHdr);
   L.ready = o;
@@ -1101,8 +1230,8 @@ ScratchLayout scratch_layout(uint64_t nb, uint32_t log2B, uint64_t max_seek, int
   L.n_warps = std::min<uint64_t>((uint64_t)num_sms * kMaxWarpsPerSM, items + 16);
   L.warps = o;
   o = align256(o + L.n_warps * warp_scratch_bytes(max_ntok));
-  L.slots = o;
-  o = align256(o + (max_seek << log2B));
+  L.tail = o;
+  o = align256(o + std::max<uint64_t>(16 * n_matches, max_seek * slot_bytes(log2B, max_ntok)));
   L.total = o;
   return L;
 }
@@ -1133,46 +1262,76 @@ inline bool aligned(const void* p, uintptr_t a) { return (reinterpret_cast<uintp
     if ((x) != cudaSuccess) return ACE_E_CUDA; \
   } while (0)
 
+// Launch shape of one two-pass decode: the entropy pass (tables, rings and
+// token window in shared memory) and the match pass (match records only).
 struct Launch {
-  uint32_t warps, ctas_per_sm, chunk, smem_per_warp, grid;
+  uint32_t warps, chunk;
+  uint32_t smem_e, smem_m;  // shared memory per warp
+  uint32_t grid_e, grid_m;
   uint64_t timeout;
 };
 
-template <bool SEEK>
-ace_status plan_launch(const ace_index* idx, const ace_tune* tune, uint64_t max_items, uint64_t max_warps,
-                       Launch* L) {
+template <class K>
+ace_status occupancy(K kernel, int device, uint32_t warps, size_t smem, int* occ) {
+  int optin = 0;
+  CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device));
+  if (smem > (size_t)optin) {
+    *occ = -1;  // this many warps with this much shared memory do not fit one CTA
+    return ACE_OK;
+  }
+  // allow every configuration up to the opt-in limit, so launches planned
+  // earlier with other shapes stay valid
+  CUDA_TRY(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+  int o = 0;
+  CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kernel, 32 * warps, smem));
+  *occ = o > 0 ? o : -1;
+  return ACE_OK;
+}
+
+// occ_cache: 2 x 9 x 9 ints (pass, warps per CTA, window / 32), 0 = unknown
+template <class KE, class KM>
+ace_status plan_launch(const ace_index* idx, const ace_tune* tune, uint32_t log2B, uint64_t max_items,
+                       uint64_t max_warps, KE ke, KM km, int* occ_cache, Launch* L) {
   ace_tune t = tune ? *tune : idx->tune;
   L->warps = t.warps_per_cta ? t.warps_per_cta : 4;
   L->chunk = t.chunk_tokens ? t.chunk_tokens : 128;
   if (L->warps > kMaxWarpsPerCta || (L->chunk & 31) || L->chunk > kMaxWindow) return ACE_E_INVAL;
   L->timeout = t.wait_timeout_ns ? t.wait_timeout_ns : kDefaultTimeoutNs;
-  L->smem_per_warp = warp_smem_bytes(L->chunk, esc_cap(idx->h.log2_block));
-  size_t smem = (size_t)L->warps * L->smem_per_warp;
-  int& cached = idx->occ_cache[SEEK][L->warps][L->chunk / 32];
-  if (cached == 0) {
-    int optin = 0;
-    CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, idx->device));
-    if (smem > (size_t)optin) {
-      cached = -1;  // this many warps with this chunk do not fit one CTA
-    } else {
-      // allow every configuration up to the opt-in limit, so launches of
-      // other cached configurations stay valid
-      CUDA_TRY(cudaFuncSetAttribute(decode_kernel<SEEK>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
-      int occ = 0;
-      CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, decode_kernel<SEEK>, 32 * L->warps, smem));
-      cached = occ > 0 ? occ : -1;
-    }
+  L->smem_e = warp_smem_bytes(L->chunk, esc_cap(log2B));
+  L->smem_m = kMatchSmem;
+  int& ce = occ_cache[(0 * 9 + L->warps) * 9 + L->chunk / 32];
+  int& cm = occ_cache[(1 * 9 + L->warps) * 9 + L->chunk / 32];
+  if (ce == 0) {
+    ace_status rc = occupancy(ke, idx->device, L->warps, (size_t)L->warps * L->smem_e, &ce);
+    if (rc) return rc;
   }
-  if (cached < 0) return ACE_E_INVAL;
-  int per_sm = cached;
-  if (t.ctas_per_sm && (int)t.ctas_per_sm < per_sm) per_sm = (int)t.ctas_per_sm;
-  L->ctas_per_sm = (uint32_t)per_sm;
-  uint64_t grid = (uint64_t)idx->num_sms * per_sm;
-  uint64_t need = (max_items + L->warps - 1) / L->warps;
-  grid = std::min(grid, max_warps / L->warps);
-  if (grid < 1) return ACE_E_NOMEM;
-  L->grid = (uint32_t)std::min(grid, std::max<uint64_t>(1, need));
+  if (cm == 0) {
+    ace_status rc = occupancy(km, idx->device, L->warps, (size_t)L->warps * L->smem_m, &cm);
+    if (rc) return rc;
+  }
+  if (ce < 0 || cm < 0) return ACE_E_INVAL;
+  int per_e = ce, per_m = cm;
+  if (t.ctas_per_sm && (int)t.ctas_per_sm < per_e) per_e = (int)t.ctas_per_sm;
+  if (t.ctas_per_sm && (int)t.ctas_per_sm < per_m) per_m = (int)t.ctas_per_sm;
+  uint64_t need = std::max<uint64_t>(1, (max_items + L->warps - 1) / L->warps);
+  uint64_t ge = std::min<uint64_t>((uint64_t)idx->num_sms * per_e, max_warps / L->warps);
+  if (ge < 1) return ACE_E_NOMEM;
+  L->grid_e = (uint32_t)std::min(ge, need);
+  L->grid_m = (uint32_t)std::min<uint64_t>((uint64_t)idx->num_sms * per_m, need);
   return ACE_OK;
+}
+
+template <bool SEEK>
+ace_status plan_index_launch(const ace_index* idx, const ace_tune* tune, uint64_t max_items, uint64_t max_warps,
+                             Launch* L) {
+  return plan_launch(idx, tune, idx->h.log2_block, max_items, max_warps, decode_kernel<SEEK, PASS_ENTROPY>,
+                     decode_kernel<SEEK, PASS_MATCH>, &idx->occ_cache[SEEK][0][0][0], L);
+}
+
+template <bool SEEK>
+void launch_two_pass(const Launch& L, const DecodeArgs& a, cudaStream_t s) {
+  decode_kernel<SEEK, PASS_ENTROPY><<<L.grid_e, 32 * L.warps, (size_t)L.warps * L.smem_e, s>>>(a);
+  decode_kernel<SEEK, PASS_MATCH><<<L.grid_m, 32 * L.warps, (size_t)L.warps * L.smem_m, s>>>(a);
 }
 
 }  // namespace
@@ -1249,6 +1408,8 @@ ace_status ace_index_build(const void* d_archive, uint64_t archive_bytes, const 
   a.order = idx->d_order;
   a.lv_count = reinterpret_cast<uint32_t*>(idx->d_mem + L.lv_count);
   a.lv_cursor = reinterpret_cast<uint32_t*>(idx->d_mem + L.lv_cursor);
+  a.match_ptr = reinterpret_cast<uint64_t*>(idx->d_mem + L.match_ptr);
+  idx->d_match_ptr = a.match_ptr;
   a.nb = h.n_blocks;
   a.total = h.total_size;
   a.payload_off = h.payload_off;
@@ -1265,6 +1426,7 @@ ace_status ace_index_build(const void* d_archive, uint64_t archive_bytes, const 
       return bail(ACE_E_CUDA);
     if (ih.status) return bail((ace_status)ih.status);
     idx->max_ntok = ih.max_ntok;
+    match_scan_kernel<<<1, 1024, 0, s>>>(a);
     levels_kernel<<<1, 1024, 0, s>>>(a);
     level_hist_kernel<<<g, 256, 0, s>>>(a);
     level_scan_kernel<<<1, 1024, 0, s>>>(a);
@@ -1274,6 +1436,7 @@ ace_status ace_index_build(const void* d_archive, uint64_t archive_bytes, const 
       return bail(ACE_E_CUDA);
     if (ih.status) return bail((ace_status)ih.status);
     idx->n_levels = ih.n_levels;
+    idx->n_matches = ih.n_matches;
   }
   *out = idx;
   return ACE_OK;
@@ -1307,13 +1470,13 @@ ace_status ace_index_free(ace_index* idx) {
 
 ace_status ace_scratch_size(const ace_index* idx, uint64_t max_seek_blocks, uint64_t* bytes) {
   if (!idx || !bytes) return ACE_E_INVAL;
-  *bytes = scratch_layout(idx->h.n_blocks, idx->h.log2_block, max_seek_blocks, idx->num_sms, idx->max_ntok).total;
+  *bytes = scratch_layout(idx->h.n_blocks, idx->h.log2_block, max_seek_blocks, idx->num_sms, idx->max_ntok, idx->n_matches).total;
   return ACE_OK;
 }
 
 ace_status ace_scratch_init(const ace_index* idx, void* d_scratch, uint64_t scratch_bytes, cudaStream_t s) {
   if (!idx || !d_scratch || !aligned(d_scratch, 256)) return ACE_E_INVAL;
-  ScratchLayout L0 = scratch_layout(idx->h.n_blocks, idx->h.log2_block, 0, idx->num_sms, idx->max_ntok);
+  ScratchLayout L0 = scratch_layout(idx->h.n_blocks, idx->h.log2_block, 0, idx->num_sms, idx->max_ntok, idx->n_matches);
   if (scratch_bytes < L0.total) return ACE_E_NOMEM;
   // header, ready flags, and (when present) slot map, work list and marks
   uint64_t clear = L0.warps;
@@ -1326,11 +1489,11 @@ ace_status ace_decode_all(const ace_index* idx, void* d_out, uint64_t out_bytes,
   if (!idx || !d_scratch || (!d_out && idx->h.total_size)) return ACE_E_INVAL;
   if (!aligned(d_scratch, 256)) return ACE_E_INVAL;
   if (out_bytes < idx->h.total_size) return ACE_E_NOMEM;
-  ScratchLayout SL = scratch_layout(idx->h.n_blocks, idx->h.log2_block, 0, idx->num_sms, idx->max_ntok);
+  ScratchLayout SL = scratch_layout(idx->h.n_blocks, idx->h.log2_block, 0, idx->num_sms, idx->max_ntok, idx->n_matches);
   if (scratch_bytes < SL.total) return ACE_E_NOMEM;
   if (!idx->h.n_blocks) return ACE_OK;
   Launch L;
-  ace_status rc = plan_launch<false>(idx, tune, idx->h.n_blocks, SL.n_warps, &L);
+  ace_status rc = plan_index_launch<false>(idx, tune, idx->h.n_blocks, SL.n_warps, &L);
   if (rc) return rc;
   ScratchHdr* sh = static_cast<ScratchHdr*>(d_scratch);
   DecodeArgs a{};
@@ -1344,7 +1507,7 @@ ace_status ace_decode_all(const ace_index* idx, void* d_out, uint64_t out_bytes,
   a.window = L.chunk;
   a.max_ntok = idx->max_ntok;
   a.esc_cap = esc_cap(a.log2B);
-  a.warp_smem = L.smem_per_warp;
+  a.warp_smem = L.smem_e;
   a.n_items = (uint32_t)idx->h.n_blocks;
   a.items = idx->d_order;
   a.out = static_cast<uint8_t*>(d_out);
@@ -1353,8 +1516,10 @@ ace_status ace_decode_all(const ace_index* idx, void* d_out, uint64_t out_bytes,
   a.timeout_ns = L.timeout;
   a.warp_scratch = static_cast<uint8_t*>(d_scratch) + SL.warps;
   a.warp_scratch_bytes = warp_scratch_bytes(idx->max_ntok);
+  a.recs = reinterpret_cast<MatchRec*>(static_cast<uint8_t*>(d_scratch) + SL.tail);
+  a.match_ptr = idx->d_match_ptr;
   begin_call_kernel<<<1, 1, 0, s>>>(sh);
-  decode_kernel<false><<<L.grid, 32 * L.warps, (size_t)L.warps * L.smem_per_warp, s>>>(a);
+  launch_two_pass<false>(L, a, s);
   CUDA_TRY(cudaGetLastError());
   return ACE_OK;
 }
@@ -1366,11 +1531,11 @@ ace_status ace_seek(const ace_index* idx, uint64_t coord, uint64_t len, void* d_
   if (out_bytes < len) return ACE_E_NOMEM;
   uint64_t nb = idx->h.n_blocks;
   uint32_t log2B = idx->h.log2_block;
-  ScratchLayout S1 = scratch_layout(nb, log2B, 1, idx->num_sms, idx->max_ntok);
+  ScratchLayout S1 = scratch_layout(nb, log2B, 1, idx->num_sms, idx->max_ntok, 0);
   if (scratch_bytes < S1.total) return ACE_E_NOMEM;
   // the layout before the slots does not depend on the slot count (a seek
   // never decodes more than n_blocks blocks)
-  uint64_t cap = std::min<uint64_t>(nb, (scratch_bytes - S1.slots) >> log2B);
+  uint64_t cap = std::min<uint64_t>(nb, (scratch_bytes - S1.tail) / slot_bytes(log2B, idx->max_ntok));
   uint64_t first = coord >> log2B, last = (coord + len - 1) >> log2B;
   if (last - first + 1 > cap) return ACE_E_NOMEM;
   uint8_t* base = static_cast<uint8_t*>(d_scratch);
@@ -1388,10 +1553,10 @@ ace_status ace_seek(const ace_index* idx, uint64_t coord, uint64_t len, void* d_
   c.first = first;
   c.last = last;
   c.cap = cap;
-  closure_kernel<<<1, 1024, 0, s>>>(c);
   Launch L;
-  ace_status rc = plan_launch<true>(idx, nullptr, cap, S1.n_warps, &L);
+  ace_status rc = plan_index_launch<true>(idx, nullptr, cap, S1.n_warps, &L);
   if (rc) return rc;
+  closure_kernel<<<1, 1024, 0, s>>>(c);
   DecodeArgs a{};
   a.arc = idx->d_arc;
   a.dir = reinterpret_cast<const ace_block_dir*>(idx->d_arc + idx->h.dir_off);
@@ -1403,9 +1568,9 @@ ace_status ace_seek(const ace_index* idx, uint64_t coord, uint64_t len, void* d_
   a.window = L.chunk;
   a.max_ntok = idx->max_ntok;
   a.esc_cap = esc_cap(log2B);
-  a.warp_smem = L.smem_per_warp;
+  a.warp_smem = L.smem_e;
   a.items = c.work;
-  a.out = base + S1.slots;
+  a.out = base + S1.tail;
   a.sh = sh;
   a.ready = reinterpret_cast<uint32_t*>(base + S1.ready);
   a.slot_of = c.slot_of;
@@ -1415,7 +1580,9 @@ ace_status ace_seek(const ace_index* idx, uint64_t coord, uint64_t len, void* d_
   a.timeout_ns = L.timeout;
   a.warp_scratch = base + S1.warps;
   a.warp_scratch_bytes = warp_scratch_bytes(idx->max_ntok);
-  decode_kernel<true><<<L.grid, 32 * L.warps, (size_t)L.warps * L.smem_per_warp, s>>>(a);
+  a.recs = reinterpret_cast<MatchRec*>(base + S1.tail + (cap << log2B));
+  a.match_ptr = nullptr;
+  launch_two_pass<true>(L, a, s);
   CUDA_TRY(cudaGetLastError());
   return ACE_OK;
 }
@@ -1497,24 +1664,26 @@ struct ace_batch {
   uint64_t scratch_bytes;
   BatchArgs args;
   Launch L;
+  int occ[2][9][9];
 };
 
 namespace {
 
 struct BatchLayout {
-  uint64_t objs, item_start, ready, warps, total, n_warps, max_ntok, items;
+  uint64_t objs, item_start, ready, warps, recs, total, n_warps, max_ntok, items, n_matches;
   uint32_t max_log2B;
 };
 
 ace_status batch_layout(const ace_index* const* idx, uint32_t n, BatchLayout* B) {
   if (!idx || n == 0) return ACE_E_INVAL;
-  uint64_t ready = 0, items = 0, max_ntok = 0;
+  uint64_t ready = 0, items = 0, max_ntok = 0, matches = 0;
   uint32_t max_log2B = 0;
   int dev = idx[0] ? idx[0]->device : -1, sms = idx[0] ? idx[0]->num_sms : 0;
   for (uint32_t i = 0; i < n; i++) {
     if (!idx[i] || idx[i]->device != dev) return ACE_E_INVAL;
     items += idx[i]->h.n_blocks;
     ready += align256(4 * idx[i]->h.n_blocks);
+    matches += idx[i]->n_matches;
     max_ntok = std::max<uint64_t>(max_ntok, idx[i]->max_ntok);
     max_log2B = std::max<uint32_t>(max_log2B, idx[i]->h.log2_block);
   }
@@ -1529,7 +1698,10 @@ ace_status batch_layout(const ace_index* const* idx, uint32_t n, BatchLayout* B)
   B->n_warps = std::min<uint64_t>((uint64_t)sms * kMaxWarpsPerSM, items + 16);
   B->warps = o;
   o = align256(o + B->n_warps * warp_scratch_bytes(max_ntok));
+  B->recs = o;
+  o = align256(o + 16 * matches);
   B->total = o;
+  B->n_matches = matches;
   B->max_ntok = max_ntok;
   B->items = items;
   B->max_log2B = max_log2B;
@@ -1558,7 +1730,7 @@ ace_status ace_batch_create(const ace_index* const* idx, uint32_t n, void* const
   uint8_t* base = static_cast<uint8_t*>(d_scratch);
   std::vector<ObjDesc> od(n);
   std::vector<uint32_t> start(n + 1);
-  uint64_t ready = B.ready, items = 0;
+  uint64_t ready = B.ready, items = 0, recs = B.recs;
   for (uint32_t i = 0; i < n; i++) {
     const ace_index* x = idx[i];
     if (out_bytes[i] < x->h.total_size || (!d_outs[i] && x->h.total_size)) return ACE_E_NOMEM;
@@ -1569,6 +1741,8 @@ ace_status ace_batch_create(const ace_index* const* idx, uint32_t n, void* const
                     static_cast<uint8_t*>(d_outs[i]),
                     reinterpret_cast<uint32_t*>(base + ready),
                     x->d_order,
+                    reinterpret_cast<MatchRec*>(base + recs),
+                    x->d_match_ptr,
                     x->h.log2_block,
                     x->h.off_width,
                     (uint32_t)x->h.n_blocks,
@@ -1576,6 +1750,7 @@ ace_status ace_batch_create(const ace_index* const* idx, uint32_t n, void* const
     start[i] = (uint32_t)items;
     items += x->h.n_blocks;
     ready += align256(4 * x->h.n_blocks);
+    recs += 16 * x->n_matches;
   }
   start[n] = (uint32_t)items;
   ace_batch* b = new (std::nothrow) ace_batch();
@@ -1585,20 +1760,10 @@ ace_status ace_batch_create(const ace_index* const* idx, uint32_t n, void* const
   b->d_scratch = base;
   b->scratch_bytes = scratch_bytes;
   // the launch shape uses the largest block size's escape table
-  ace_index probe = *idx[0];
-  probe.h.log2_block = (uint8_t)B.max_log2B;
-  rc = plan_launch<false>(&probe, tune, B.items, B.n_warps, &b->L);
-  if (rc == ACE_OK && B.items) {
-    // the kernel is launched as batch_decode_kernel: same shape, same limits
-    int optin = 0;
-    size_t smem = (size_t)b->L.warps * b->L.smem_per_warp;
-    if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, b->device) != cudaSuccess ||
-        cudaFuncSetAttribute(batch_decode_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin) != cudaSuccess)
-      rc = ACE_E_CUDA;
-    (void)smem;
-  }
+  rc = plan_launch(idx[0], tune, B.max_log2B, B.items, B.n_warps, batch_decode_kernel<PASS_ENTROPY>,
+                   batch_decode_kernel<PASS_MATCH>, &b->occ[0][0][0], &b->L);
   if (rc == ACE_OK &&
-      (cudaMemsetAsync(base, 0, B.total - B.n_warps * warp_scratch_bytes(B.max_ntok), s) != cudaSuccess ||
+      (cudaMemsetAsync(base, 0, B.warps, s) != cudaSuccess ||
        cudaMemcpyAsync(base + B.objs, od.data(), n * sizeof(ObjDesc), cudaMemcpyHostToDevice, s) != cudaSuccess ||
        cudaMemcpyAsync(base + B.item_start, start.data(), 4ull * (n + 1), cudaMemcpyHostToDevice, s) != cudaSuccess ||
        cudaStreamSynchronize(s) != cudaSuccess))
@@ -1613,7 +1778,7 @@ ace_status ace_batch_create(const ace_index* const* idx, uint32_t n, void* const
   a.n_objs = n;
   a.n_items = (uint32_t)B.items;
   a.window = b->L.chunk;
-  a.warp_smem = b->L.smem_per_warp;
+  a.warp_smem = b->L.smem_e;
   a.esc_cap = esc_cap(B.max_log2B);
   a.max_ntok = (uint32_t)B.max_ntok;
   a.sh = reinterpret_cast<ScratchHdr*>(base);
@@ -1627,8 +1792,10 @@ ace_status ace_batch_create(const ace_index* const* idx, uint32_t n, void* const
 ace_status ace_decode_batch(const ace_batch* b, cudaStream_t s) {
   if (!b) return ACE_E_INVAL;
   if (!b->args.n_items) return ACE_OK;
+  const Launch& L = b->L;
   begin_call_kernel<<<1, 1, 0, s>>>(b->args.sh);
-  batch_decode_kernel<<<b->L.grid, 32 * b->L.warps, (size_t)b->L.warps * b->L.smem_per_warp, s>>>(b->args);
+  batch_decode_kernel<PASS_ENTROPY><<<L.grid_e, 32 * L.warps, (size_t)L.warps * L.smem_e, s>>>(b->args);
+  batch_decode_kernel<PASS_MATCH><<<L.grid_m, 32 * L.warps, (size_t)L.warps * L.smem_m, s>>>(b->args);
   CUDA_TRY(cudaGetLastError());
   return ACE_OK;
 }
@@ -1648,7 +1815,7 @@ ace_status ace_batch_sync(const ace_batch* b, cudaStream_t s) {
 
 ace_status ace_batch_launch_shape(const ace_batch* b, uint32_t* grid, uint32_t* warps_per_cta, uint32_t* window) {
   if (!b) return ACE_E_INVAL;
-  if (grid) *grid = b->L.grid;
+  if (grid) *grid = b->L.grid_e;
   if (warps_per_cta) *warps_per_cta = b->L.warps;
   if (window) *window = b->L.chunk;
   return ACE_OK;
@@ -1670,12 +1837,13 @@ struct ace_cache {
   CacheDecodeArgs dargs;
   Launch L;
   uint64_t req_off;  // requests are staged here by ace_seek_batch_host
+  int occ[2][9][9];
 };
 
 namespace {
 
 struct CacheLayout {
-  uint64_t arcs, minmax, front0, front1, work, reqs, warps, slots, total, n_warps, max_ntok;
+  uint64_t arcs, minmax, front0, front1, work, reqs, warps, slots, recs, total, n_warps, max_ntok;
 };
 
 CacheLayout cache_layout(const ace_index* const* idx, uint32_t n, uint64_t n_slots, uint32_t max_reqs,
@@ -1701,6 +1869,8 @@ CacheLayout cache_layout(const ace_index* const* idx, uint32_t n, uint64_t n_slo
   o = align256(o + C.n_warps * warp_scratch_bytes(max_ntok));
   C.slots = o;
   o = align256(o + (n_slots << log2B));
+  C.recs = o;
+  o = align256(o + 16 * max_ntok * n_slots);
   C.total = o;
   C.max_ntok = max_ntok;
   return C;
@@ -1776,13 +1946,8 @@ ace_status ace_cache_create(const ace_index* const* idx, uint32_t n, void* const
   c->mem = base;
   c->bytes = bytes;
   c->req_off = C.reqs;
-  rc = plan_launch<true>(idx[0], tune, n_slots, C.n_warps, &c->L);
-  if (rc == ACE_OK) {
-    int optin = 0;
-    if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device) != cudaSuccess ||
-        cudaFuncSetAttribute(cache_decode_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin) != cudaSuccess)
-      rc = ACE_E_CUDA;
-  }
+  rc = plan_launch(idx[0], tune, log2B, n_slots, C.n_warps, cache_decode_kernel<PASS_ENTROPY>,
+                   cache_decode_kernel<PASS_MATCH>, &c->occ[0][0][0], &c->L);
   // header (epoch 1: no block is cached, since every ready flag starts at 0)
   CacheHdr h{};
   h.epoch = 1;
@@ -1807,11 +1972,12 @@ ace_status ace_cache_create(const ace_index* const* idx, uint32_t n, void* const
   a.work = reinterpret_cast<uint32_t*>(base + C.work);
   a.arc_minmax = reinterpret_cast<uint32_t*>(base + C.minmax);
   a.slots = base + C.slots;
+  a.recs = reinterpret_cast<MatchRec*>(base + C.recs);
   a.reqs = nullptr;
   a.n_reqs = 0;
   CacheDecodeArgs& d = c->dargs;
   d.window = c->L.chunk;
-  d.warp_smem = c->L.smem_per_warp;
+  d.warp_smem = c->L.smem_e;
   d.esc_cap = esc_cap(log2B);
   d.max_ntok = (uint32_t)C.max_ntok;
   d.timeout_ns = c->L.timeout;
@@ -1832,7 +1998,9 @@ ace_status ace_seek_batch(const ace_cache* c, const ace_seek_req* d_reqs, uint32
   cache_closure_kernel<<<1, 1024, 0, s>>>(a);
   CacheDecodeArgs d = c->dargs;
   d.c = a;
-  cache_decode_kernel<<<c->L.grid, 32 * c->L.warps, (size_t)c->L.warps * c->L.smem_per_warp, s>>>(d);
+  const Launch& L = c->L;
+  cache_decode_kernel<PASS_ENTROPY><<<L.grid_e, 32 * L.warps, (size_t)L.warps * L.smem_e, s>>>(d);
+  cache_decode_kernel<PASS_MATCH><<<L.grid_m, 32 * L.warps, (size_t)L.warps * L.smem_m, s>>>(d);
   cache_copy_kernel<<<std::min<uint32_t>(n, 1024), 256, 0, s>>>(a, static_cast<uint8_t*>(d_pool));
   CUDA_TRY(cudaGetLastError());
   return ACE_OK;
@@ -1943,9 +2111,9 @@ ace_status ace_seek_noalloc(const ace_index* idx, uint64_t coord, uint64_t len, 
   if (rc) return rc;
   const uint64_t nb = idx->h.n_blocks;
   const uint32_t log2B = idx->h.log2_block;
-  ScratchLayout S = scratch_layout(nb, log2B, 1, kStaticWarpSMs, idx->max_ntok);
-  if (S.slots > kStaticScratchBytes) return ACE_E_NOMEM;  // archive too large for the fixed scratch
-  uint64_t cap = std::min<uint64_t>(nb, (kStaticScratchBytes - S.slots) >> log2B);
+  ScratchLayout S = scratch_layout(nb, log2B, 1, kStaticWarpSMs, idx->max_ntok, 0);
+  if (S.tail > kStaticScratchBytes) return ACE_E_NOMEM;  // archive too large for the fixed scratch
+  uint64_t cap = std::min<uint64_t>(nb, (kStaticScratchBytes - S.tail) / slot_bytes(log2B, idx->max_ntok));
   uint64_t first = coord >> log2B, last = (coord + len - 1) >> log2B;
   if (last - first + 1 > cap) return ACE_E_NOMEM;  // more target blocks than slots
   ScratchHdr* sh = reinterpret_cast<ScratchHdr*>(base);
@@ -1966,7 +2134,7 @@ ace_status ace_seek_noalloc(const ace_index* idx, uint64_t coord, uint64_t len, 
   c.last = last;
   c.cap = cap;
   Launch L;
-  rc = plan_launch<true>(idx, nullptr, cap, S.n_warps, &L);
+  rc = plan_index_launch<true>(idx, nullptr, cap, S.n_warps, &L);
   if (rc) return rc;
   closure_kernel<<<1, 1024, 0, s>>>(c);
   DecodeArgs a{};
@@ -1980,9 +2148,9 @@ ace_status ace_seek_noalloc(const ace_index* idx, uint64_t coord, uint64_t len, 
   a.window = L.chunk;
   a.max_ntok = idx->max_ntok;
   a.esc_cap = esc_cap(log2B);
-  a.warp_smem = L.smem_per_warp;
+  a.warp_smem = L.smem_e;
   a.items = c.work;
-  a.out = base + S.slots;
+  a.out = base + S.tail;
   a.sh = sh;
   a.ready = reinterpret_cast<uint32_t*>(base + S.ready);
   a.slot_of = c.slot_of;
@@ -1992,7 +2160,9 @@ ace_status ace_seek_noalloc(const ace_index* idx, uint64_t coord, uint64_t len, 
   a.timeout_ns = L.timeout;
   a.warp_scratch = base + S.warps;
   a.warp_scratch_bytes = warp_scratch_bytes(idx->max_ntok);
-  decode_kernel<true><<<L.grid, 32 * L.warps, (size_t)L.warps * L.smem_per_warp, s>>>(a);
+  a.recs = reinterpret_cast<MatchRec*>(base + S.tail + (cap << log2B));
+  a.match_ptr = nullptr;
+  launch_two_pass<true>(L, a, s);
   CUDA_TRY(cudaGetLastError());
   // the status lives in the shared array, so the call waits for it
   uint32_t status = 0;

@@ -23,7 +23,8 @@ struct ScratchHdr {
   uint32_t min_block;  // seek: smallest block reached by the closure
   uint64_t fnv;        // verify: last FNV-1a 64 computed
   uint64_t guard_bad;  // verify: guard bytes that differ from the canary
-  uint32_t pad[52];
+  uint32_t ticket2;    // next work item of the match pass
+  uint32_t pad[51];
 };
 static_assert(sizeof(ScratchHdr) == 256, "scratch header");
 
@@ -34,9 +35,21 @@ struct IndexHdr {
   uint32_t err_where;
   uint32_t n_levels;
   uint32_t max_ntok;   // most tokens in any block: sizes the per-warp token records
-  uint32_t pad[59];
+  uint32_t pad0;
+  uint64_t n_matches;  // matches in the archive: sizes a whole decode's match records
+  uint32_t pad[56];
 };
 static_assert(sizeof(IndexHdr) == 256, "index header");
+
+// One match of a block, between the entropy pass that finds it and the
+// match pass that resolves it: absolute source, destination within the
+// block, length.
+struct MatchRec {
+  uint64_t S;
+  uint32_t D;
+  uint32_t L;
+};
+static_assert(sizeof(MatchRec) == 16, "match record");
 
 // One stream's decode tables: slot -> symbol, and symbol -> (freq << 16 | cum).
 struct Lut {
@@ -69,7 +82,10 @@ __device__ __forceinline__ void st_release(uint32_t* p, uint32_t v) {
 }
 
 // Spins until *flag == want or timeout_ns passes; false on timeout.
-__device__ __forceinline__ bool wait_flag(const uint32_t* flag, uint32_t want, uint64_t timeout_ns) {
+// Gives up after timeout_ns, or as soon as *abort (a call's status word)
+// records an error: the block waited for may then never be published.
+__device__ __forceinline__ bool wait_flag(const uint32_t* flag, uint32_t want, uint64_t timeout_ns,
+                                          const uint32_t* abort = nullptr) {
   if (ld_acquire(flag) == want) return true;
   uint64_t t0 = globaltimer();
   uint32_t ns = 32;
@@ -77,6 +93,7 @@ __device__ __forceinline__ bool wait_flag(const uint32_t* flag, uint32_t want, u
     __nanosleep(ns);
     if (ld_acquire(flag) == want) return true;
     if (globaltimer() - t0 > timeout_ns) return false;
+    if (abort && *(volatile const uint32_t*)abort) return false;
     if (ns < 1024) ns <<= 1;
   }
 }
