@@ -14,6 +14,7 @@ import numpy as np
 from . import build as _build
 
 ACE_OK, ACE_E_INVAL, ACE_E_CORRUPT, ACE_E_RANGE, ACE_E_NOMEM, ACE_E_TIMEOUT, ACE_E_CUDA = range(7)
+ACE_PASS_ENTROPY, ACE_PASS_MATCH = 0, 1
 
 
 class AceError(RuntimeError):
@@ -73,6 +74,7 @@ _SIGS = {
     "ace_scratch_size": ([_vp, _u64, _P(_u64)], _i32),
     "ace_scratch_init": ([_vp, _vp, _u64, _vp], _i32),
     "ace_decode_all": ([_vp, _vp, _u64, _vp, _u64, _P(ace_tune), _vp], _i32),
+    "ace_decode_pass": ([_vp, _i32, _vp, _u64, _vp, _u64, _P(ace_tune), _vp], _i32),
     "ace_seek": ([_vp, _u64, _u64, _vp, _u64, _vp, _u64, _vp], _i32),
     "ace_sync": ([_vp, _vp, _vp], _i32),
     "ace_index_set_tune": ([_vp, _P(ace_tune)], _i32),
@@ -222,6 +224,12 @@ def ace_decode_all(idx, d_out, out_bytes, d_scratch, scratch_bytes, tune=None, s
     t = ctypes.byref(tune) if tune is not None else None
     _check(lib().ace_decode_all(idx, _ptr(d_out), out_bytes, _ptr(d_scratch), scratch_bytes, t,
                                 _stream(stream)), "ace_decode_all")
+
+
+def ace_decode_pass(idx, pass_, d_out, out_bytes, d_scratch, scratch_bytes, tune=None, stream=None):
+    t = ctypes.byref(tune) if tune is not None else None
+    _check(lib().ace_decode_pass(idx, pass_, _ptr(d_out), out_bytes, _ptr(d_scratch), scratch_bytes, t,
+                                 _stream(stream)), "ace_decode_pass")
 
 
 def ace_seek(idx, coord, length, d_out, out_bytes, d_scratch, scratch_bytes, stream=None):

@@ -20,6 +20,7 @@ using namespace ace;
 namespace {
 
 constexpr uint64_t kDefaultTimeoutNs = 2000000000ull;
+constexpr uint32_t kMaxLevelLaunches = 32;  // whole decodes with more levels wait on flags instead
 
 inline uint64_t align256(uint64_t v) { return (v + 255) & ~255ull; }
 
@@ -213,6 +214,8 @@ struct DecodeArgs {
   uint64_t warp_scratch_bytes;
   MatchRec* recs;          // match records between the two passes
   const uint64_t* match_ptr;  // whole decode: block -> first record; null: max_ntok records per slot
+  const uint32_t* level;   // whole decode by levels: each block's dependency level
+  uint32_t cur_level;      // whole decode by levels: the level this launch resolves
 };
 
 // Shared memory of one warp: one stream's tables at a time, the three
@@ -295,75 +298,6 @@ __device__ __forceinline__ void fail(const DecodeArgs& a, bool& ok, ace_status c
 // every byte read precedes D and is final when the copy starts.
 __device__ __forceinline__ uint64_t src_index(uint64_t S, uint64_t d, uint32_t len, uint32_t i) {
   return d >= len ? S + i : S + (i % (uint32_t)d);
-}
-
-// One lane copies one match.  A source that does not overlap its
-// destination is read as aligned 8-byte words, four per round trip; words
-// never cross a block (blocks are multiples of 8 bytes), and the word that
-// would pass the end of the output is read byte by byte.  An overlapping
-// source goes byte by byte in batches of 8 loads before their stores.
-template <bool SEEK>
-__device__ __forceinline__ void copy_match_lane(const DecodeArgs& a, uint8_t* dst, uint64_t D, uint64_t S,
-                                                uint32_t len) {
-  const uint64_t d = D - S;
-  if (d >= len) {
-    const uint64_t a0 = S & ~7ull;
-    const uint32_t off = (uint32_t)(S & 7);
-    for (uint32_t w0 = 0; 8 * w0 < off + len; w0 += 4) {  // words w0 .. w0+3 of the source
-      uint64_t v[4];
-#pragma unroll
-      for (uint32_t j = 0; j < 4; j++) {
-        uint64_t q = a0 + 8ull * (w0 + j);
-        v[j] = 0;
-        if (8 * (w0 + j) < off + len) {
-          if (q + 8 <= a.total) {
-            v[j] = __ldcg(reinterpret_cast<const unsigned long long*>(Addr<SEEK>::at(a, q)));
-          } else {
-            for (uint32_t k = 0; k < 8 && q + k < a.total; k++)
-              v[j] |= (uint64_t)__ldcg(Addr<SEEK>::at(a, q + k)) << (8 * k);
-          }
-        }
-      }
-#pragma unroll
-      for (uint32_t j = 0; j < 4; j++)
-#pragma unroll
-        for (uint32_t k = 0; k < 8; k++) {
-          uint32_t qi = 8 * (w0 + j) + k;  // byte of the word run; destination byte qi - off
-          if (qi >= off && qi < off + len) dst[qi - off] = (uint8_t)(v[j] >> (8 * k));
-        }
-    }
-    return;
-  }
-  for (uint32_t i0 = 0; i0 < len; i0 += 8) {
-    uint8_t v[8];
-#pragma unroll
-    for (uint32_t u = 0; u < 8; u++)
-      if (i0 + u < len) v[u] = __ldcg(Addr<SEEK>::at(a, src_index(S, d, len, i0 + u)));
-#pragma unroll
-    for (uint32_t u = 0; u < 8; u++)
-      if (i0 + u < len) dst[i0 + u] = v[u];
-  }
-}
-
-// The whole warp copies one match, four independent byte loads per lane per
-// round trip (128 bytes).
-template <bool SEEK>
-__device__ __forceinline__ void copy_match_warp(const DecodeArgs& a, uint8_t* dst, uint64_t D, uint64_t S,
-                                                uint32_t len, uint32_t lane) {
-  const uint64_t d = D - S;
-  for (uint32_t i0 = 0; i0 < len; i0 += 128) {
-    uint8_t v[4];
-#pragma unroll
-    for (uint32_t u = 0; u < 4; u++) {
-      uint32_t i = i0 + 32 * u + lane;
-      if (i < len) v[u] = __ldcg(Addr<SEEK>::at(a, src_index(S, d, len, i)));
-    }
-#pragma unroll
-    for (uint32_t u = 0; u < 4; u++) {
-      uint32_t i = i0 + 32 * u + lane;
-      if (i < len) dst[i] = v[u];
-    }
-  }
 }
 
 __device__ __forceinline__ uint64_t read_src(const uint8_t* q, uint32_t w) {
@@ -524,87 +458,376 @@ __device__ bool entropy_block(const DecodeArgs& a, const WarpMem& m, const TokRe
   return ok;
 }
 
-// Match pass of one block (Section 2: a block decodes once the blocks holding
-// its sources are present): waits, bounded, for the source blocks, then
-// resolves the matches in dependency waves -- a match whose read range ends
-// at or before the destination of the first pending match reads only
-// finished bytes.  Returns false if a record is corrupt or a wait gave up.
+// Matches per lane in a group: match j of the group is on lane j mod 32.
+constexpr uint32_t kLaneMatches = kMatchGroup / 32;
+// Bytes in flight per lane in the bytewise copy of a round's matches.
+constexpr uint32_t kCopyUnroll = 8;
+// Copy classes: a non-overlapping match of at most kShortMax bytes is copied
+// by one lane, one of at least kLongMin bytes by the whole warp in 16-byte
+// pieces, every other one bytewise with the round's other such matches.
+constexpr uint32_t kShortMax = 32;
+constexpr uint32_t kLongMin = 512;
+
+// Source of a short match: the aligned 8-byte words covering [S, S + len).
 template <bool SEEK>
-__device__ bool match_block(const DecodeArgs& a, MatchRec* gm, uint32_t b, uint32_t lane, uint32_t epoch) {
+__device__ __forceinline__ void short_load(const DecodeArgs& a, uint64_t S, uint32_t len, uint64_t (&w)[5]) {
+  const uint64_t a0 = S & ~7ull;
+  const uint32_t off = (uint32_t)(S & 7);
+#pragma unroll
+  for (uint32_t k = 0; k < 5; k++) {
+    const uint64_t q = a0 + 8ull * k;
+    w[k] = 0;
+    if (8 * k < off + len) {
+      if (q + 8 <= a.total) {
+        w[k] = __ldcg(reinterpret_cast<const unsigned long long*>(Addr<SEEK>::at(a, q)));
+      } else {
+        for (uint32_t t = 0; t < 8 && q + t < a.total; t++)
+          w[k] |= (uint64_t)__ldcg(Addr<SEEK>::at(a, q + t)) << (8 * t);
+      }
+    }
+  }
+}
+
+// Bytes sh .. sh + 7 of hi:lo (sh < 8).
+__device__ __forceinline__ uint64_t funnel64(uint64_t lo, uint64_t hi, uint32_t sh) {
+  return sh ? (lo >> (8 * sh)) | (hi << (64 - 8 * sh)) : lo;
+}
+
+// Destination of a short match: aligned 8-byte words where the match covers
+// them, single bytes at its two ends.  Source byte off + i (off = S mod 8,
+// counted from the first source word) lands at dp[i].
+__device__ __forceinline__ void short_store(uint8_t* dp, uint32_t off, uint32_t len, const uint64_t (&w)[5]) {
+  const uint32_t hd = (uint32_t)(reinterpret_cast<uintptr_t>(dp) & 7);
+  uint8_t* dal = dp - hd;
+  const bool same = off >= hd;  // destination word i starts in source word i, else in word i - 1
+  const uint32_t sh = (off - hd) & 7;
+#pragma unroll
+  for (uint32_t i = 0; i < 5; i++) {
+    const int first = 8 * (int)i - (int)hd;  // match byte held by the word's first byte
+    if (first >= (int)len) break;
+    const uint64_t lo = same ? w[i] : (i ? w[i - 1] : 0ull);
+    const uint64_t hi = same ? (i + 1 < 5 ? w[i + 1] : 0ull) : w[i];
+    const uint64_t word = funnel64(lo, hi, sh);
+    if (first >= 0 && first + 8 <= (int)len) {
+      *reinterpret_cast<uint64_t*>(dal + 8 * i) = word;
+    } else {
+#pragma unroll 1
+      for (uint32_t k = 0; k < 8; k++) {
+        const int di = first + (int)k;
+        if (di >= 0 && di < (int)len) dal[8 * i + k] = (uint8_t)(word >> (8 * k));
+      }
+    }
+  }
+}
+
+// 16 bytes at p, bytes outside [lo, hi) read as zero.
+__device__ __forceinline__ uint4 ld16_in(const uint8_t* p, const uint8_t* lo, const uint8_t* hi) {
+  if (p >= lo && p + 16 <= hi) return __ldcg(reinterpret_cast<const uint4*>(p));
+  uint4 v = make_uint4(0, 0, 0, 0);
+#pragma unroll 1
+  for (uint32_t k = 0; k < 16; k++) {
+    if (p + k < lo || p + k >= hi) continue;
+    const uint32_t x = (uint32_t)__ldcg(p + k) << (8 * (k & 3));
+    if (k < 4) v.x |= x;
+    else if (k < 8) v.y |= x;
+    else if (k < 12) v.z |= x;
+    else v.w |= x;
+  }
+  return v;
+}
+
+// Bytes r .. r + 15 of B:A (r < 16, the same on every lane).
+__device__ __forceinline__ uint4 funnel128(uint4 A, uint4 B, uint32_t r) {
+  const uint32_t t = 8 * (r & 3);
+  uint32_t y0, y1, y2, y3, y4;
+  switch (r >> 2) {
+    case 0: y0 = A.x; y1 = A.y; y2 = A.z; y3 = A.w; y4 = B.x; break;
+    case 1: y0 = A.y; y1 = A.z; y2 = A.w; y3 = B.x; y4 = B.y; break;
+    case 2: y0 = A.z; y1 = A.w; y2 = B.x; y3 = B.y; y4 = B.z; break;
+    default: y0 = A.w; y1 = B.x; y2 = B.y; y3 = B.z; y4 = B.w; break;
+  }
+  return make_uint4(__funnelshift_r(y0, y1, t), __funnelshift_r(y1, y2, t), __funnelshift_r(y2, y3, t),
+                    __funnelshift_r(y3, y4, t));
+}
+
+__device__ __forceinline__ uint4 shfl_down16(uint4 v, uint32_t d) {
+  return make_uint4(__shfl_down_sync(kFull, v.x, d), __shfl_down_sync(kFull, v.y, d), __shfl_down_sync(kFull, v.z, d),
+                    __shfl_down_sync(kFull, v.w, d));
+}
+
+// The whole warp copies one long non-overlapping match from sp to dp within
+// [lo, hi) (whole-decode addressing): lane l of a step writes the aligned
+// 16-byte destination piece c = 32 u + l, two pieces per lane in flight,
+// each built from the aligned source piece it starts in and the next one
+// (the next lane's, or one more load on lane 31).  Pieces the match covers
+// go out as 16-byte stores, the two end pieces bytewise.
+__device__ __forceinline__ void copy_long(uint8_t* dp, const uint8_t* sp, uint32_t len, const uint8_t* lo,
+                                          const uint8_t* hi, uint32_t lane) {
+  const uint32_t hd = (uint32_t)(reinterpret_cast<uintptr_t>(dp) & 15);
+  uint8_t* dal = dp - hd;
+  const uint8_t* s0 = sp - hd;  // source of dal[0]
+  const uint32_t r = (uint32_t)(reinterpret_cast<uintptr_t>(s0) & 15);
+  const uint8_t* sal = s0 - r;
+  const uint32_t nch = (hd + len + 15) >> 4;
+  for (uint32_t c0 = 0; c0 < nch; c0 += 64) {
+    uint4 A[2], Bn[2];
+#pragma unroll
+    for (uint32_t u = 0; u < 2; u++) {
+      const uint32_t c = c0 + 32 * u + lane;
+      A[u] = c <= nch ? ld16_in(sal + 16ull * c, lo, hi) : make_uint4(0, 0, 0, 0);
+      Bn[u] = (lane == 31 && c + 1 <= nch) ? ld16_in(sal + 16ull * (c + 1), lo, hi) : make_uint4(0, 0, 0, 0);
+    }
+#pragma unroll
+    for (uint32_t u = 0; u < 2; u++) {
+      const uint32_t c = c0 + 32 * u + lane;
+      const uint4 nb = shfl_down16(A[u], 1);
+      const uint4 B = lane == 31 ? Bn[u] : nb;
+      if (c >= nch) continue;
+      const uint4 v = funnel128(A[u], B, r);
+      const int first = 16 * (int)c - (int)hd;  // match byte held by the piece's first byte
+      if (first >= 0 && first + 16 <= (int)len) {
+        *reinterpret_cast<uint4*>(dal + 16ull * c) = v;
+      } else {
+#pragma unroll 1
+        for (uint32_t k = 0; k < 16; k++) {
+          const int di = first + (int)k;
+          const uint32_t x = k < 4 ? v.x : k < 8 ? v.y : k < 12 ? v.z : v.w;
+          if (di >= 0 && di < (int)len) dal[16ull * c + k] = (uint8_t)(x >> (8 * (k & 3)));
+        }
+      }
+    }
+  }
+}
+
+// Whether a bit of the 128-bit mask (P0, P1, P2, P3) is set in [lo, hi].
+__device__ __forceinline__ bool any_in(uint32_t P0, uint32_t P1, uint32_t P2, uint32_t P3, uint32_t lo,
+                                       uint32_t hi) {
+  bool any = false;
+#pragma unroll
+  for (uint32_t w = 0; w < 4; w++) {
+    const uint32_t P = w == 0 ? P0 : w == 1 ? P1 : w == 2 ? P2 : P3;
+    const uint32_t wlo = 32 * w, whi = wlo + 31;
+    if (lo > hi || hi < wlo || lo > whi) continue;
+    uint32_t m = P;
+    if (lo > wlo) m &= ~0u << (lo - wlo);
+    if (hi < whi) m &= (2u << (hi - wlo)) - 1u;
+    any |= m != 0;
+  }
+  return any;
+}
+
+// First index i in [0, n) with key(i) > x, for keys that never decrease.
+template <class Key>
+__device__ __forceinline__ uint32_t upper_bound(uint32_t n, uint32_t x, Key key) {
+  uint32_t lo = 0, len = n;
+  while (len) {
+    const uint32_t h = len >> 1;
+    if (key(lo + h) <= x) {
+      lo += h + 1;
+      len -= h + 1;
+    } else {
+      len = h;
+    }
+  }
+  return lo;
+}
+
+// Match pass of one block (Section 2: a block decodes once the blocks holding
+// its sources are present).  Groups of up to 128 matches: their records are
+// loaded together; with WAIT the source blocks before this one are checked
+// with overlapping relaxed loads (a bounded wait only for one not yet
+// published); without it (one launch per dependency level) each source
+// block's level must be below this launch's level, else the archive's
+// dependency lists disagree with its matches.  Then the group resolves in
+// rounds.  A match is ready in a round when no
+// pending match of its block writes a byte its source reads; literal bytes
+// are final after the entropy pass.  The first pending match is always ready,
+// so every round makes progress, and a round's ready matches read no byte
+// another one writes.  Returns false if a record is corrupt or a wait gave up.
+template <bool SEEK, bool WAIT>
+__device__ bool match_block(const DecodeArgs& a, MatchRec* gm, uint32_t b, uint32_t lane, uint32_t epoch,
+                            uint32_t nm) {
   bool ok = true, bad = false;
-  const uint32_t ntok = __ldg(reinterpret_cast<const uint32_t*>(a.dir + b) + 12);
-  const uint32_t nm = ntok ? ntok - 1 : 0;
   const uint64_t B = (uint64_t)1 << a.log2B, bstart = (uint64_t)b << a.log2B;
   const uint32_t blen = (uint32_t)min(B, a.total - bstart);
   uint8_t* obase = SEEK ? a.out + ((uint64_t)__ldg(a.slot_of + b) << a.log2B) : a.out + bstart;
-  const MatchRec* rec = recs_of<SEEK>(a, b);
+  const uint4* rec = reinterpret_cast<const uint4*>(recs_of<SEEK>(a, b));
   uint64_t* gS = reinterpret_cast<uint64_t*>(gm);                 // [kMatchGroup] sources
   uint32_t* gD = reinterpret_cast<uint32_t*>(gS + kMatchGroup);   // [kMatchGroup] destinations in the block
   uint32_t* gL = gD + kMatchGroup;                                // [kMatchGroup] lengths
+  uint32_t* gX = gL + kMatchGroup;                                // [kMatchGroup + 1] starts in a round's copy
   for (uint32_t t0 = 0; ok && t0 < nm; t0 += kMatchGroup) {
     const uint32_t gn = min(kMatchGroup, nm - t0);
-    bool timeout = false;
-    for (uint32_t j = lane; j < gn; j += 32) {
-      const MatchRec r = rec[t0 + j];
-      uint64_t S = r.S, D = bstart + r.D;
-      uint32_t ml = r.L;
-      gS[j] = S;
-      gD[j] = r.D;
-      gL[j] = ml;
-      if (!ml) continue;
-      if (S >= D || (uint64_t)r.D + ml > blen) {  // records are checked again: the entropy pass may have failed
+    uint4 r[kLaneMatches];
+#pragma unroll
+    for (uint32_t q = 0; q < kLaneMatches; q++) {
+      const uint32_t j = lane + 32 * q;
+      r[q] = j < gn ? __ldcg(rec + t0 + j) : make_uint4(0, 0, 0, 0);
+    }
+    uint32_t pend = 0;
+#pragma unroll
+    for (uint32_t q = 0; q < kLaneMatches; q++) {
+      const uint32_t j = lane + 32 * q;
+      if (j >= gn) continue;
+      const uint64_t S = (uint64_t)r[q].x | ((uint64_t)r[q].y << 32);
+      uint32_t ml = r[q].w;
+      if (ml && (S >= bstart + r[q].z || (uint64_t)r[q].z + ml > blen)) {  // checked again: the entropy pass may have failed
         bad = true;
-        gL[j] = 0;
-        continue;
+        ml = 0;
       }
-      uint64_t rend = S + min((uint64_t)ml, D - S);
-      uint64_t k0 = S >> a.log2B, k1 = (rend - 1) >> a.log2B;
-      for (uint64_t k = k0; k <= k1 && k < b && !timeout; k++)
-        if (!wait_flag(a.ready + k, epoch, a.timeout_ns, &a.sh->status)) timeout = true;
+      gS[j] = S;
+      gD[j] = r[q].z;
+      gL[j] = ml;
+      if (ml) pend |= 1u << q;
     }
     if (__any_sync(kFull, bad)) fail(a, ok, ACE_E_CORRUPT, b, 37, lane);
-    if (__any_sync(kFull, timeout)) fail(a, ok, ACE_E_TIMEOUT, b, 38, lane);
     if (!ok) break;
     __syncwarp();
-    // lane owns matches j = lane + 32 q, q < 4; pending bits track them
-    uint32_t pend = 0;
-    for (uint32_t q = 0, j = lane; j < gn; q++, j += 32)
-      if (gL[j]) pend |= 1u << q;
-    while (__any_sync(kFull, pend != 0)) {
-      // W: destination of the first pending match; a match whose read range
-      // ends at or before W reads only finished bytes
-      uint32_t myW = 0xffffffffu;
-      if (pend) myW = gD[lane + 32 * (__ffs(pend) - 1)];
-      const uint64_t W = bstart + warp_min(myW);
-      uint32_t go = 0;
-      for (uint32_t rest = pend; rest; rest &= rest - 1) {
-        uint32_t q = __ffs(rest) - 1, j = lane + 32 * q;
-        uint64_t S = gS[j], D = bstart + gD[j];
-        if (S + min((uint64_t)gL[j], D - S) <= W) go |= 1u << q;
+
+    // source blocks before this one: all flags loaded, then compared
+    uint32_t f0[kLaneMatches], f1[kLaneMatches], rng[kLaneMatches];
+    uint32_t ext = 0;
+#pragma unroll
+    for (uint32_t q = 0; q < kLaneMatches; q++) {
+      f0[q] = f1[q] = epoch;
+      rng[q] = 1;  // lo = 1 > hi = 0: no match of the group feeds this one
+      if (!(pend >> q & 1)) continue;
+      const uint32_t j = lane + 32 * q;
+      const uint64_t S = gS[j], D = bstart + gD[j];
+      const uint64_t rend = S + min((uint64_t)gL[j], D - S);
+      const uint64_t k0 = S >> a.log2B;
+      if (k0 < b) {  // blocks k0 .. k1 hold the bytes before this block
+        const uint64_t k1 = min((rend - 1) >> a.log2B, (uint64_t)b - 1);
+        ext |= 1u << q;
+        const uint32_t* flags = WAIT ? a.ready : a.level;
+        f0[q] = ld_relaxed(flags + k0);
+        f1[q] = k1 != k0 ? ld_relaxed(flags + k1) : f0[q];
       }
-      const uint32_t nready = __reduce_add_sync(kFull, __popc(go));
-      if (nready > 4) {  // many independent matches: each lane copies its own
-        for (uint32_t rest = go; rest; rest &= rest - 1) {
-          uint32_t q = __ffs(rest) - 1, j = lane + 32 * q;
-          uint32_t ml = gL[j];
-          if (ml <= 64) {
-            copy_match_lane<SEEK>(a, obase + gD[j], bstart + gD[j], gS[j], ml);
-            go &= ~(1u << q);
-            pend &= ~(1u << q);
+      if (rend > bstart) {  // bytes of this block: the group's matches writing them
+        const uint32_t s_rel = S > bstart ? (uint32_t)(S - bstart) : 0u, e_rel = (uint32_t)(rend - bstart);
+        const uint32_t lo = upper_bound(j, s_rel, [&](uint32_t i) { return gD[i] + gL[i]; });
+        const uint32_t hi = upper_bound(j, e_rel - 1, [&](uint32_t i) { return gD[i]; });  // first with gD >= e_rel
+        rng[q] = hi > lo ? (lo | ((hi - 1) << 8)) : 1u;
+      }
+    }
+    if (WAIT) {
+      bool timeout = false;
+#pragma unroll
+      for (uint32_t q = 0; q < kLaneMatches; q++) {
+        if (!(ext >> q & 1)) continue;
+        const uint32_t j = lane + 32 * q;
+        const uint64_t S = gS[j], D = bstart + gD[j];
+        const uint64_t rend = S + min((uint64_t)gL[j], D - S);
+        const uint64_t k0 = S >> a.log2B, k1 = min((rend - 1) >> a.log2B, (uint64_t)b - 1);
+        if (f0[q] == epoch && f1[q] == epoch && k1 <= k0 + 1) continue;  // blocks between them: the bounded wait
+        for (uint64_t k = k0; k <= k1 && !timeout; k++)
+          if (!wait_flag(a.ready + k, epoch, a.timeout_ns, &a.sh->status)) timeout = true;
+      }
+      if (__any_sync(kFull, timeout)) fail(a, ok, ACE_E_TIMEOUT, b, 38, lane);
+      if (!ok) break;
+      if (__any_sync(kFull, ext != 0)) fence_acquire();
+      __syncwarp();  // any lane may copy a match whose flags another lane checked
+    }
+    // without WAIT the level check below need not hold up the copies: a
+    // corrupt archive fails the call whatever bytes they wrote
+    uint32_t chk = ext;
+
+    while (__any_sync(kFull, pend != 0)) {
+      const uint32_t P0 = __ballot_sync(kFull, pend & 1u), P1 = __ballot_sync(kFull, pend & 2u);
+      const uint32_t P2 = __ballot_sync(kFull, pend & 4u), P3 = __ballot_sync(kFull, pend & 8u);
+      uint32_t go = 0;
+#pragma unroll
+      for (uint32_t q = 0; q < kLaneMatches; q++)
+        if ((pend >> q & 1) && !any_in(P0, P1, P2, P3, rng[q] & 0xffu, rng[q] >> 8)) go |= 1u << q;
+      // classes: short (one lane), long (the warp), the rest bytewise
+      uint32_t sgo = 0, lgo = 0;
+#pragma unroll
+      for (uint32_t q = 0; q < kLaneMatches; q++) {
+        if (!(go >> q & 1)) continue;
+        const uint32_t j = lane + 32 * q, ml = gL[j];
+        if (bstart + gD[j] - gS[j] < ml) continue;  // overlapping: bytewise
+        if (ml <= kShortMax) sgo |= 1u << q;
+        else if (!SEEK && ml >= kLongMin) lgo |= 1u << q;
+      }
+      if (sgo) {  // short: the next match's loads go out before the previous one's stores
+        uint64_t cur[5], nxt[5];
+        uint32_t jc = lane + 32 * (__ffs(sgo) - 1), rest = sgo & (sgo - 1);
+        short_load<SEEK>(a, gS[jc], gL[jc], cur);
+        while (true) {
+          const uint32_t jn = rest ? lane + 32 * (__ffs(rest) - 1) : 0u;
+          if (rest) short_load<SEEK>(a, gS[jn], gL[jn], nxt);
+          short_store(obase + gD[jc], (uint32_t)(gS[jc] & 7), gL[jc], cur);
+          if (!rest) break;
+          rest &= rest - 1;
+          jc = jn;
+#pragma unroll
+          for (uint32_t k = 0; k < 5; k++) cur[k] = nxt[k];
+        }
+      }
+      {  // long: one match at a time
+        uint32_t rest = lgo, any;
+        while ((any = __ballot_sync(kFull, rest != 0)) != 0) {
+          const uint32_t src_lane = __ffs(any) - 1;
+          const uint32_t q = __ffs(__shfl_sync(kFull, rest, src_lane)) - 1;
+          const uint32_t j = src_lane + 32 * q;
+          copy_long(obase + gD[j], a.out + gS[j], gL[j], a.out, a.out + a.total, lane);
+          if (lane == src_lane) rest &= ~(1u << q);
+        }
+      }
+      // the rest laid end to end in group order: gX[j] is where match j
+      // starts, gX[kMatchGroup] the total
+      const uint32_t bgo = go & ~sgo & ~lgo;
+      uint32_t carry = 0;
+#pragma unroll
+      for (uint32_t q = 0; q < kLaneMatches; q++) {
+        const uint32_t j = lane + 32 * q;
+        const uint32_t len = (bgo >> q & 1) ? gL[j] : 0u;
+        const uint32_t incl = warp_incl_sum(len, lane);
+        gX[j] = carry + incl - len;
+        carry += __shfl_sync(kFull, incl, 31);
+      }
+      if (lane == 0) gX[kMatchGroup] = carry;
+      __syncwarp();
+      // lane l copies bytes c + 32 u + l: consecutive lanes read and write
+      // consecutive bytes of a match, kCopyUnroll loads in flight before
+      // their stores (a round's ready matches read no byte it writes); the
+      // lane's match index only moves forward
+      uint32_t jc = 0;
+      for (uint32_t c = 0; c < carry; c += 32 * kCopyUnroll) {
+        uint8_t v[kCopyUnroll];
+        uint8_t* dp[kCopyUnroll];
+#pragma unroll
+        for (uint32_t u = 0; u < kCopyUnroll; u++) {
+          const uint32_t p = c + 32 * u + lane;
+          dp[u] = nullptr;
+          if (p < carry) {
+            while (gX[jc + 1] <= p) jc++;
+            const uint32_t i = p - gX[jc], ml = gL[jc];
+            const uint64_t S = gS[jc], d = bstart + gD[jc] - S;
+            v[u] = __ldcg(Addr<SEEK>::at(a, src_index(S, d, ml, i)));
+            dp[u] = obase + gD[jc] + i;
           }
         }
+#pragma unroll
+        for (uint32_t u = 0; u < kCopyUnroll; u++)
+          if (dp[u]) *dp[u] = v[u];
       }
-      uint32_t any;
-      while ((any = __ballot_sync(kFull, go != 0)) != 0) {  // few or long: the whole warp
-        uint32_t src_lane = __ffs(any) - 1;
-        uint32_t q = __ffs(__shfl_sync(kFull, go, src_lane)) - 1;
-        uint32_t j = src_lane + 32 * q;
-        copy_match_warp<SEEK>(a, obase + gD[j], bstart + gD[j], gS[j], gL[j], lane);
-        if (lane == src_lane) {
-          go &= ~(1u << q);
-          pend &= ~(1u << q);
-        }
+      pend &= ~go;
+      __syncwarp();
+    }
+    if (!WAIT) {
+#pragma unroll
+      for (uint32_t q = 0; q < kLaneMatches; q++) {
+        if (!(chk >> q & 1)) continue;
+        if (f0[q] >= a.cur_level || f1[q] >= a.cur_level) bad = true;
+        const uint32_t j = lane + 32 * q;
+        const uint64_t S = gS[j], D = bstart + gD[j];
+        const uint64_t rend = S + min((uint64_t)gL[j], D - S);
+        const uint64_t k0 = S >> a.log2B, k1 = min((rend - 1) >> a.log2B, (uint64_t)b - 1);
+        for (uint64_t k = k0 + 1; k < k1; k++)  // a source spanning more than two earlier blocks
+          if (__ldg(a.level + k) >= a.cur_level) bad = true;
       }
+      if (__any_sync(kFull, bad)) fail(a, ok, ACE_E_CORRUPT, b, 39, lane);
       __syncwarp();
     }
   }
@@ -612,10 +835,13 @@ __device__ bool match_block(const DecodeArgs& a, MatchRec* gm, uint32_t b, uint3
   return ok;
 }
 
+// PASS_MATCH resolves blocks in (level, block) order with bounded waits on
+// their source blocks (match_level_kernel resolves one level of a whole
+// decode without them).
 enum { PASS_ENTROPY = 0, PASS_MATCH = 1 };
 
 // The match pass keeps only its match-record area in shared memory.
-constexpr uint32_t kMatchSmem = 16 * kMatchGroup;
+constexpr uint32_t kMatchSmem = 20 * kMatchGroup + 16;
 
 // Publishes block b (its writes visible device-wide before the flag).
 __device__ __forceinline__ void publish(uint32_t* ready, uint32_t b, uint32_t epoch, uint32_t lane) {
@@ -629,7 +855,7 @@ __device__ __forceinline__ void publish(uint32_t* ready, uint32_t b, uint32_t ep
 // after it, resolves every block's matches in (level, block) order and
 // publishes the block.
 template <bool SEEK, int PASS>
-__global__ void __launch_bounds__(256, 3) decode_kernel(DecodeArgs a) {
+__global__ void __launch_bounds__(256, PASS == PASS_ENTROPY ? 3 : 2) decode_kernel(DecodeArgs a) {
   extern __shared__ __align__(16) uint8_t smem[];
   const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const uint32_t epoch = *(volatile uint32_t*)&a.sh->epoch;
@@ -649,7 +875,8 @@ __global__ void __launch_bounds__(256, 3) decode_kernel(DecodeArgs a) {
       entropy_block<SEEK>(a, m, g, b, lane);
       continue;
     }
-    bool ok = match_block<SEEK>(a, gm, b, lane, epoch);
+    const uint32_t ntok = __ldg(reinterpret_cast<const uint32_t*>(a.dir + b) + 12);
+    bool ok = match_block<SEEK, true>(a, gm, b, lane, epoch, ntok ? ntok - 1 : 0);
     if (SEEK && ok && a.slice) {
       // copy the part of this block inside [coord, coord + len) to the caller
       uint64_t bs = (uint64_t)b << a.log2B, be = min(bs + ((uint64_t)1 << a.log2B), a.total);
@@ -658,6 +885,38 @@ __global__ void __launch_bounds__(256, 3) decode_kernel(DecodeArgs a) {
       for (uint64_t p = lo + lane; p < hi; p += 32) a.slice[p - a.coord] = __ldcg(src + p);
     }
     publish(a.ready, b, epoch, lane);
+  }
+}
+
+// The match pass of one dependency level of a whole decode: every lower
+// level was finished by the launches before, so blocks need no flags or
+// waits.  Blocks are dealt out statically (block k of the level to warp
+// k mod the warps in the grid), and each warp fetches its next block's
+// number and record range while it resolves the current one.
+__global__ void __launch_bounds__(256, 2) match_level_kernel(DecodeArgs a) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const uint32_t nw = gridDim.x * (blockDim.x >> 5);
+  MatchRec* gm = reinterpret_cast<MatchRec*>(smem + (size_t)wid * kMatchSmem);
+  uint32_t it = blockIdx.x * (blockDim.x >> 5) + wid;
+  if (it >= a.n_items) return;
+  uint32_t b = __ldg(a.items + it);
+  uint64_t p0 = __ldg(a.match_ptr + b), p1 = __ldg(a.match_ptr + b + 1);
+  while (true) {
+    const uint32_t nx = it + nw;
+    uint32_t bn = 0;
+    uint64_t q0 = 0, q1 = 0;
+    if (nx < a.n_items) {
+      bn = __ldg(a.items + nx);
+      q0 = __ldg(a.match_ptr + bn);
+      q1 = __ldg(a.match_ptr + bn + 1);
+    }
+    match_block<false, false>(a, gm, b, lane, 0, (uint32_t)(p1 - p0));
+    if (nx >= a.n_items) break;
+    it = nx;
+    b = bn;
+    p0 = q0;
+    p1 = q1;
   }
 }
 
@@ -693,7 +952,7 @@ struct BatchArgs {
 // are in its own (level, block) order, so in the match pass a warp only
 // ever waits on blocks of its archive that were handed out before its own.
 template <int PASS>
-__global__ void __launch_bounds__(256, 3) batch_decode_kernel(BatchArgs ba) {
+__global__ void __launch_bounds__(256, PASS == PASS_ENTROPY ? 3 : 2) batch_decode_kernel(BatchArgs ba) {
   extern __shared__ __align__(16) uint8_t smem[];
   const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   WarpMem m = carve(smem + (size_t)wid * ba.warp_smem, ba.window);
@@ -736,7 +995,8 @@ __global__ void __launch_bounds__(256, 3) batch_decode_kernel(BatchArgs ba) {
     if (PASS == PASS_ENTROPY) {
       entropy_block<false>(a, m, g, b, lane);
     } else {
-      match_block<false>(a, gm, b, lane, epoch);
+      const uint32_t ntok = __ldg(reinterpret_cast<const uint32_t*>(a.dir + b) + 12);
+      match_block<false, true>(a, gm, b, lane, epoch, ntok ? ntok - 1 : 0);
       publish(od.ready, b, epoch, lane);
     }
   }
@@ -1032,7 +1292,7 @@ struct CacheDecodeArgs {
 // Decodes a batch's work list into cache slots: the same two passes as a
 // seek, archive by archive.
 template <int PASS>
-__global__ void __launch_bounds__(256, 3) cache_decode_kernel(CacheDecodeArgs ca) {
+__global__ void __launch_bounds__(256, PASS == PASS_ENTROPY ? 3 : 2) cache_decode_kernel(CacheDecodeArgs ca) {
   extern __shared__ __align__(16) uint8_t smem[];
   const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   WarpMem m = carve(smem + (size_t)wid * ca.warp_smem, ca.window);
@@ -1072,7 +1332,8 @@ __global__ void __launch_bounds__(256, 3) cache_decode_kernel(CacheDecodeArgs ca
     if (PASS == PASS_ENTROPY) {
       entropy_block<true>(a, m, g, b, lane);
     } else {
-      match_block<true>(a, gm, b, lane, epoch);
+      const uint32_t ntok = __ldg(reinterpret_cast<const uint32_t*>(a.dir + b) + 12);
+      match_block<true, true>(a, gm, b, lane, epoch, ntok ? ntok - 1 : 0);
       publish(arc.ready, b, epoch, lane);
     }
   }
@@ -1166,6 +1427,12 @@ struct ace_index {
   ace_tune tune;
   // occupancy of the decode kernels, per (seek?, pass, warps per CTA, window)
   mutable int occ_cache[2][2][9][9];
+  mutable int occ_level[9][9];  // the per-level match kernel
+  // whole decodes resolve matches with one launch per level when there are
+  // at most kMaxLevelLaunches levels: level L's blocks are
+  // order[level_start[L] .. level_start[L + 1])
+  bool by_levels;
+  uint32_t level_start[kMaxLevelLaunches + 1];
 };
 
 namespace {
@@ -1437,6 +1704,16 @@ ace_status ace_index_build(const void* d_archive, uint64_t archive_bytes, const 
     if (ih.status) return bail((ace_status)ih.status);
     idx->n_levels = ih.n_levels;
     idx->n_matches = ih.n_matches;
+    idx->by_levels = ih.n_levels <= kMaxLevelLaunches;
+    if (idx->by_levels) {
+      uint32_t cnt[kMaxLevelLaunches];
+      if (cudaMemcpyAsync(cnt, a.lv_count, 4ull * ih.n_levels, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+          cudaStreamSynchronize(s) != cudaSuccess)
+        return bail(ACE_E_CUDA);
+      idx->level_start[0] = 0;
+      for (uint32_t l = 0; l < ih.n_levels; l++) idx->level_start[l + 1] = idx->level_start[l] + cnt[l];
+      if (idx->level_start[ih.n_levels] != h.n_blocks) return bail(ACE_E_CORRUPT);
+    }
   }
   *out = idx;
   return ACE_OK;
@@ -1484,8 +1761,14 @@ ace_status ace_scratch_init(const ace_index* idx, void* d_scratch, uint64_t scra
   return ACE_OK;
 }
 
-ace_status ace_decode_all(const ace_index* idx, void* d_out, uint64_t out_bytes, void* d_scratch,
-                          uint64_t scratch_bytes, const ace_tune* tune, cudaStream_t s) {
+}  // extern "C"
+
+namespace {
+
+// passes: bit 0 the entropy pass (with the call's header reset before it),
+// bit 1 the match pass.
+ace_status decode_all_passes(const ace_index* idx, uint32_t passes, void* d_out, uint64_t out_bytes, void* d_scratch,
+                             uint64_t scratch_bytes, const ace_tune* tune, cudaStream_t s) {
   if (!idx || !d_scratch || (!d_out && idx->h.total_size)) return ACE_E_INVAL;
   if (!aligned(d_scratch, 256)) return ACE_E_INVAL;
   if (out_bytes < idx->h.total_size) return ACE_E_NOMEM;
@@ -1518,10 +1801,51 @@ ace_status ace_decode_all(const ace_index* idx, void* d_out, uint64_t out_bytes,
   a.warp_scratch_bytes = warp_scratch_bytes(idx->max_ntok);
   a.recs = reinterpret_cast<MatchRec*>(static_cast<uint8_t*>(d_scratch) + SL.tail);
   a.match_ptr = idx->d_match_ptr;
-  begin_call_kernel<<<1, 1, 0, s>>>(sh);
-  launch_two_pass<false>(L, a, s);
+  if (passes & 1) {
+    begin_call_kernel<<<1, 1, 0, s>>>(sh);
+    decode_kernel<false, PASS_ENTROPY><<<L.grid_e, 32 * L.warps, (size_t)L.warps * L.smem_e, s>>>(a);
+  }
+  if ((passes & 2) && !idx->by_levels)
+    decode_kernel<false, PASS_MATCH><<<L.grid_m, 32 * L.warps, (size_t)L.warps * L.smem_m, s>>>(a);
+  if ((passes & 2) && idx->by_levels) {
+    int& occ = idx->occ_level[L.warps][L.chunk / 32];
+    if (occ == 0) {
+      rc = occupancy(match_level_kernel, idx->device, L.warps, (size_t)L.warps * L.smem_m, &occ);
+      if (rc) return rc;
+    }
+    if (occ < 0) return ACE_E_INVAL;
+    uint32_t per_sm = (uint32_t)occ;
+    const ace_tune t = tune ? *tune : idx->tune;
+    if (t.ctas_per_sm && t.ctas_per_sm < per_sm) per_sm = t.ctas_per_sm;
+    a.level = idx->d_level;
+    for (uint32_t l = 0; l < idx->n_levels; l++) {
+      const uint32_t n = idx->level_start[l + 1] - idx->level_start[l];
+      if (!n) continue;
+      a.items = idx->d_order + idx->level_start[l];
+      a.n_items = n;
+      a.cur_level = l;
+      const uint32_t grid = (uint32_t)std::min<uint64_t>((uint64_t)idx->num_sms * per_sm, (n + L.warps - 1) / L.warps);
+      match_level_kernel<<<grid, 32 * L.warps, (size_t)L.warps * L.smem_m, s>>>(a);
+    }
+  }
   CUDA_TRY(cudaGetLastError());
   return ACE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+ace_status ace_decode_all(const ace_index* idx, void* d_out, uint64_t out_bytes, void* d_scratch,
+                          uint64_t scratch_bytes, const ace_tune* tune, cudaStream_t s) {
+  return decode_all_passes(idx, 3, d_out, out_bytes, d_scratch, scratch_bytes, tune, s);
+}
+
+ace_status ace_decode_pass(const ace_index* idx, int pass, void* d_out, uint64_t out_bytes, void* d_scratch,
+                           uint64_t scratch_bytes, const ace_tune* tune, cudaStream_t s) {
+  if (pass != ACE_PASS_ENTROPY && pass != ACE_PASS_MATCH) return ACE_E_INVAL;
+  return decode_all_passes(idx, pass == ACE_PASS_ENTROPY ? 1u : 2u, d_out, out_bytes, d_scratch, scratch_bytes, tune,
+                           s);
 }
 
 ace_status ace_seek(const ace_index* idx, uint64_t coord, uint64_t len, void* d_out, uint64_t out_bytes,

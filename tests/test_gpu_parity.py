@@ -97,6 +97,23 @@ def test_edge_sizes_and_empty():
     da.close()
 
 
+def test_separate_passes_equal_decode_all():
+    """ace_decode_pass(ENTROPY) then ace_decode_pass(MATCH) on one stream is
+    ace_decode_all; a pass number outside the two is rejected."""
+    data = synth.generate("text", 1_500_000, 21)
+    arc = ace.ace_encode(data, 14, 4)
+    da = DeviceArchive(arc)
+    out = torch.zeros(da.total, dtype=torch.uint8, device="cuda")
+    for p in (ace.ACE_PASS_ENTROPY, ace.ACE_PASS_MATCH):
+        ace.ace_decode_pass(da.idx, p, out, da.total, da.d_scratch, da.scratch_bytes, None, da.stream)
+    assert da.sync() == ace.ACE_OK
+    assert np.array_equal(out.cpu().numpy(), data)
+    with pytest.raises(ace.AceError) as e:
+        ace.ace_decode_pass(da.idx, 2, out, da.total, da.d_scratch, da.scratch_bytes, None, da.stream)
+    assert e.value.status == ace.ACE_E_INVAL
+    da.close()
+
+
 def test_tunings_agree():
     data = synth.generate("text", 2_000_000, 9)
     arc = ace.ace_encode(data, 14, 4)
@@ -219,6 +236,26 @@ def test_wait_gives_up_with_timeout_status():
     assert da.sync() == ace.ACE_OK
     assert np.array_equal(out.cpu().numpy(), data[:4096])
     da.close()
+
+
+def test_decode_all_with_a_dependency_removed():
+    """Whole decodes resolve matches one dependency level per launch; a
+    dependency list that no longer covers a block's sources either leaves
+    its levels valid (exact output) or is reported as corrupt."""
+    data = synth.generate("text", 200_000, 12)
+    for log2b, b in ((12, 30), (14, 9)):
+        arc = oracle.encode(data, log2b, 4, 16)
+        deps = oracle.deps(arc)[b]
+        assert deps and deps != [(0, 0)]
+        bad = _with_dep_removed(arc, b)
+        da = DeviceArchive(bad)
+        ace.ace_index_set_tune(da.idx, ace.make_tune(wait_timeout_ns=20_000_000))
+        out = da.decode_all()
+        st = da.sync()
+        assert st in (ace.ACE_OK, ace.ACE_E_CORRUPT, ace.ACE_E_TIMEOUT), ace.ace_status_str(st)
+        if st == ace.ACE_OK:
+            assert np.array_equal(out.cpu().numpy(), data)
+        da.close()
 
 
 def test_corrupt_payloads_are_reported_not_faulted():
