@@ -36,7 +36,7 @@ SEEK_SEED = 2
 WORKLOAD = "fastq-256MiB-16KiB-blocks"
 METRIC = "decompressed GB/s (% HBM roofline); 16KB seek p50/p99 us, batched vs plain"
 KERNEL_SOURCES = ["paper_2606_24531_gb300/csrc/ace.cu", "paper_2606_24531_gb300/csrc/ace_device.cuh"]
-PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "entropy_pass_fastq256.txt")
+PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "literal_pass_fastq256.txt")
 
 
 def kernel_sha():
@@ -48,7 +48,7 @@ def kernel_sha():
 
 
 def profiled_traffic():
-    """dram read+write bytes per entropy-pass launch from the committed ncu summary,
+    """dram read+write bytes per literal-pass launch from the committed ncu summary,
     if it was taken on the current kernel sources."""
     try:
         kv = {}
@@ -210,26 +210,25 @@ def main():
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    # one step = ace_decode_all, issued as its two passes so that an event
-    # between them times the entropy pass (the dominant kernel) on its own
-    ev = [tuple(torch.cuda.Event(enable_timing=True) for _ in range(3)) for _ in range(args.steps)]
+    # one step = ace_decode_all, issued as its three passes so that events
+    # between them time each pass on its own
+    ev = [tuple(torch.cuda.Event(enable_timing=True) for _ in range(4)) for _ in range(args.steps)]
+    passes = (ace.ACE_PASS_TOKENS, ace.ACE_PASS_LITERALS, ace.ACE_PASS_MATCH)
     for k in range(args.steps):
         flush.fill_(k & 255)  # L2 flush between timed steps, outside the events
         ev[k][0].record(stream)
-        ace.ace_decode_pass(da.idx, ace.ACE_PASS_ENTROPY, out, total, da.d_scratch, da.scratch_bytes, None, stream)
-        ev[k][1].record(stream)
-        ace.ace_decode_pass(da.idx, ace.ACE_PASS_MATCH, out, total, da.d_scratch, da.scratch_bytes, None, stream)
-        ev[k][2].record(stream)
+        for p in passes:
+            ace.ace_decode_pass(da.idx, p, out, total, da.d_scratch, da.scratch_bytes, None, stream)
+            ev[k][p + 1].record(stream)
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
     clocks = sampler.stop()
     st = da.sync()
     assert st == ace.ACE_OK, ace.ace_status_str(st)
-    times = [a.elapsed_time(c) for a, _, c in ev]
+    times = [e[0].elapsed_time(e[3]) for e in ev]
     ms = statistics.mean(times)
-    ms_entropy = statistics.mean(a.elapsed_time(b) for a, b, _ in ev)
-    ms_match = statistics.mean(b.elapsed_time(c) for _, b, c in ev)
+    ms_pass = [statistics.mean(e[p].elapsed_time(e[p + 1]) for e in ev) for p in range(3)]
     if dist:
         t = torch.tensor([ms], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -239,20 +238,27 @@ def main():
     peaks, peak_kind = measured_peaks()
     hdr = arc[:64].view(np.uint64)
     deps_bytes = int(hdr[6]) - int(hdr[5])  # payload_off - deps_off: not read by a whole decode
-    # the dominant kernel is the entropy pass: it reads the directory and
-    # stream payload, writes every literal to the output and one 16-byte
-    # record per match
-    alg_e = (arc.size - deps_bytes) + stats["literal_bytes"] + 16 * stats["n_matches"]
-    # the match pass reads the records and every match's source bytes and
-    # writes the matched bytes
-    alg_m = 16 * stats["n_matches"] + stats["match_src_bytes"] + stats["match_bytes"]
-    achieved = alg_e / (ms_entropy / 1e3) / 1e9
+    # algorithmic bytes per pass: the token pass reads the directory and the
+    # length and offset streams and writes a 16-byte record per match; the
+    # literal pass reads the directory, the literal streams and the records
+    # and writes every literal; the match pass reads the records and every
+    # match's source bytes and writes the matched bytes
+    nb = info["n_blocks"]
+    dir_off = int(hdr[4])
+    sb = arc[dir_off:dir_off + 64 * nb].view(np.uint32).reshape(nb, 16)[:, 6:9].astype(np.int64).sum(axis=0)
+    rec_b = 16 * stats["n_matches"]
+    alg = [64 * nb + int(sb[1] + sb[2]) + rec_b,
+           64 * nb + int(sb[0]) + rec_b + stats["literal_bytes"],
+           rec_b + stats["match_src_bytes"] + stats["match_bytes"]]
+    names = ["decode_kernel<false, PASS_TOKENS>", "decode_kernel<false, PASS_LITERALS>", "match_level_kernel"]
+    top = max(range(3), key=lambda p: ms_pass[p])
+    achieved = alg[top] / (ms_pass[top] / 1e3) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": achieved / peaks["hbm_gbs"], "traffic": profiled_traffic(),
-                "kernel": "decode_kernel<false, PASS_ENTROPY>", "algorithmic_bytes": alg_e,
-                "peak_kind": peak_kind,
-                "passes": {"entropy_ms": ms_entropy, "match_ms": ms_match,
-                           "match_achieved_gbs": alg_m / (ms_match / 1e3) / 1e9, "match_algorithmic_bytes": alg_m}}
+                "frac": achieved / peaks["hbm_gbs"], "traffic": profiled_traffic() if top == 1 else None,
+                "kernel": names[top], "algorithmic_bytes": alg[top], "peak_kind": peak_kind,
+                "passes": {n: {"ms": ms_pass[p], "algorithmic_bytes": alg[p],
+                               "achieved_gbs": alg[p] / (ms_pass[p] / 1e3) / 1e9}
+                           for p, n in enumerate(["tokens", "literals", "matches"])}}
 
     result = {
         "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
@@ -263,7 +269,7 @@ def main():
                    "literal_fraction": stats["literal_bytes"] / total, "matches": stats["n_matches"],
                    "l2": "flushed between timed steps (256 MiB fill)", "parallelism": "replicas"},
         "roofline": roofline,
-        "gpu_launches": 3 * args.steps,  # per step: header reset, entropy pass, match pass
+        "gpu_launches": (3 + info["n_levels"]) * args.steps,  # per step: header reset, tokens, literals, a match launch per level
         "clocks": clocks,
         "index_build_ms": index_ms,
     }

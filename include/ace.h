@@ -173,24 +173,26 @@ typedef struct {
 } ace_tune;
 
 /*
- * Whole-archive decode through both layers (Sections 2-3), in two
- * persistent launches on s.  The entropy pass rANS-decodes every block's
- * three streams, writes its literals straight into d_out (out_bytes >=
- * total_size) and leaves one record per match in scratch.  The match pass
- * then resolves every block's absolute-offset matches in (level, block)
- * order, waiting, bounded, only for the blocks a match reads.  tune may be
- * NULL.  Asynchronous; check with ace_sync.
+ * Whole-archive decode through both layers (Sections 2-3), in three
+ * persistent passes on s.  The token pass rANS-decodes every block's length
+ * and offset streams and leaves one record per match (absolute source,
+ * destination, length) in scratch; the literal pass decodes every block's
+ * literal stream straight to its positions in d_out (out_bytes >=
+ * total_size); the match pass resolves every block's absolute-offset matches
+ * in (level, block) order, each level after the blocks its matches read.
+ * tune may be NULL.  Asynchronous; check with ace_sync.
  */
 ace_status ace_decode_all(const ace_index *idx, void *d_out, uint64_t out_bytes, void *d_scratch,
                           uint64_t scratch_bytes, const ace_tune *tune, cudaStream_t s);
 
 /*
- * The two passes of ace_decode_all as separate calls, so that a caller can
- * time each one with events on s.  ACE_PASS_ENTROPY (which also resets the
- * call's status) then ACE_PASS_MATCH, same arguments, same stream: together
- * they are exactly ace_decode_all.  Any other pass value: ACE_E_INVAL.
+ * The passes of ace_decode_all as separate calls, so that a caller can time
+ * each one with events on s: ACE_PASS_TOKENS (which also resets the call's
+ * status), ACE_PASS_LITERALS, then ACE_PASS_MATCH, same arguments, same
+ * stream; together they are exactly ace_decode_all.  Any other pass value:
+ * ACE_E_INVAL.
  */
-enum { ACE_PASS_ENTROPY = 0, ACE_PASS_MATCH = 1 };
+enum { ACE_PASS_TOKENS = 0, ACE_PASS_LITERALS = 1, ACE_PASS_MATCH = 2 };
 ace_status ace_decode_pass(const ace_index *idx, int pass, void *d_out, uint64_t out_bytes, void *d_scratch,
                            uint64_t scratch_bytes, const ace_tune *tune, cudaStream_t s);
 

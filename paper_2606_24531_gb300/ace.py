@@ -14,7 +14,7 @@ import numpy as np
 from . import build as _build
 
 ACE_OK, ACE_E_INVAL, ACE_E_CORRUPT, ACE_E_RANGE, ACE_E_NOMEM, ACE_E_TIMEOUT, ACE_E_CUDA = range(7)
-ACE_PASS_ENTROPY, ACE_PASS_MATCH = 0, 1
+ACE_PASS_TOKENS, ACE_PASS_LITERALS, ACE_PASS_MATCH = 0, 1, 2
 
 
 class AceError(RuntimeError):

@@ -218,58 +218,68 @@ struct DecodeArgs {
   uint32_t cur_level;      // whole decode by levels: the level this launch resolves
 };
 
-// Shared memory of one warp: one stream's tables at a time, the three
-// renormalisation rings, a window of token positions (reused for match
-// records in the match phase), and the escape values.
-struct WarpMem {
+// Shared memory of one warp in the token pass: one stream's tables at a
+// time, the length and offset streams' renormalisation rings, and the block's
+// escape values.
+struct TokMem {
   Lut* lut;
-  uint8_t* ring;   // [3][kRing]
-  uint32_t* tdst;  // [window + 1] start of each token's literal run, within the block
-  uint32_t* tlit;  // [window + 1] index of each token's first literal among the block's literals
+  uint8_t* ring;   // [2][kRing]: lengths, offsets
   uint16_t* esc;   // [esc_cap]
 };
 
+// Shared memory of one warp in the literal pass: the literal stream's tables
+// and ring, and a window of token positions.
+struct LitMem {
+  Lut* lut;
+  uint8_t* ring;   // [kRing]
+  uint32_t* tdst;  // [window + 1] start of each token's literal run, within the block
+  uint32_t* tlit;  // [window + 1] index of each token's first literal among the block's literals
+};
+
 // Token records of the block a warp is decoding, in global scratch: for
-// every token the start of its literal run and of its literals, its match
-// length, and its match's offset bytes.
+// every token the start of its literal run, its match length, and its
+// match's offset bytes.
 struct TokRec {
   uint32_t* tdst;  // [max_ntok + 1]
-  uint32_t* tlit;  // [max_ntok + 1]
   uint32_t* tml;   // [max_ntok]
   uint8_t* offb;   // [5 max_ntok]
 };
 
 constexpr uint32_t kMatchGroup = 128;  // matches whose records sit in shared memory at a time
 
-// the token window doubles as the match-record area, so it holds either
-__host__ __device__ inline uint32_t window_area_bytes(uint32_t window) {
-  return max(8 * (window + 1), 16 * kMatchGroup);
+__host__ __device__ inline uint32_t tok_smem_bytes(uint32_t escn) {
+  return (sizeof(Lut) + 2 * kRing + 2 * escn + 15) & ~15u;
 }
 
-__host__ __device__ inline uint32_t warp_smem_bytes(uint32_t window, uint32_t escn) {
-  uint32_t b = sizeof(Lut) + 3 * kRing + window_area_bytes(window) + 2 * escn;
-  return (b + 15) & ~15u;
+__host__ __device__ inline uint32_t lit_smem_bytes(uint32_t window) {
+  return (sizeof(Lut) + kRing + 8 * (window + 1) + 15) & ~15u;
 }
 
 __host__ __device__ inline uint64_t warp_scratch_bytes(uint64_t max_ntok) {
-  return (4 * (max_ntok + 1) * 3 + 5 * max_ntok + 255) & ~255ull;
+  return (4 * (max_ntok + 1) * 2 + 5 * max_ntok + 255) & ~255ull;
 }
 
-__device__ inline WarpMem carve(uint8_t* base, uint32_t window) {
-  WarpMem m;
+__device__ inline TokMem carve_tok(uint8_t* base) {
+  TokMem m;
   m.lut = reinterpret_cast<Lut*>(base);
   m.ring = base + sizeof(Lut);
-  m.tdst = reinterpret_cast<uint32_t*>(m.ring + 3 * kRing);
+  m.esc = reinterpret_cast<uint16_t*>(m.ring + 2 * kRing);
+  return m;
+}
+
+__device__ inline LitMem carve_lit(uint8_t* base, uint32_t window) {
+  LitMem m;
+  m.lut = reinterpret_cast<Lut*>(base);
+  m.ring = base + sizeof(Lut);
+  m.tdst = reinterpret_cast<uint32_t*>(m.ring + kRing);
   m.tlit = m.tdst + (window + 1);
-  m.esc = reinterpret_cast<uint16_t*>(m.ring + 3 * kRing + window_area_bytes(window));
   return m;
 }
 
 __device__ inline TokRec tok_records(uint8_t* base, uint64_t max_ntok) {
   TokRec r;
   r.tdst = reinterpret_cast<uint32_t*>(base);
-  r.tlit = r.tdst + (max_ntok + 1);
-  r.tml = r.tlit + (max_ntok + 1);
+  r.tml = r.tdst + (max_ntok + 1);
   r.offb = reinterpret_cast<uint8_t*>(r.tml + (max_ntok + 1));
   return r;
 }
@@ -313,14 +323,14 @@ __device__ __forceinline__ MatchRec* recs_of(const DecodeArgs& a, uint32_t b) {
   return a.recs + (uint64_t)__ldg(a.slot_of + b) * a.max_ntok;
 }
 
-// Entropy pass of one block (Section 3: the block boundary is the entry
-// point of the entropy layer): the length stream parsed into token
-// positions, the offset stream, and the literals placed straight at their
-// output positions.  The block's matches are left as records for the match
-// pass.  Each stream's tables are built once.  Returns false if the block is
-// corrupt (the error is recorded).
+// Token pass of one block (Section 3: the block boundary is the entry point
+// of the entropy layer): the length stream parsed into token positions, the
+// offset stream, and one record per match -- absolute source, destination in
+// the block, length -- for the match pass; the literal pass rebuilds the
+// token positions from these records.  Returns false if the block is corrupt
+// (the error is recorded).
 template <bool SEEK>
-__device__ bool entropy_block(const DecodeArgs& a, const WarpMem& m, const TokRec& g, uint32_t b, uint32_t lane) {
+__device__ bool token_block(const DecodeArgs& a, const TokMem& m, const TokRec& g, uint32_t b, uint32_t lane) {
   bool ok = true;
   const uint32_t* dw = reinterpret_cast<const uint32_t*>(a.dir + b);
   uint32_t dv = lane < 16 ? __ldg(dw + lane) : 0u;
@@ -328,15 +338,16 @@ __device__ bool entropy_block(const DecodeArgs& a, const WarpMem& m, const TokRe
   const uint32_t blen = (uint32_t)min(B, a.total - bstart);
   const uint32_t w = a.w;
   const uint32_t ntok = __shfl_sync(kFull, dv, 12), nesc = __shfl_sync(kFull, dv, 13);
-  uint8_t* obase = SEEK ? a.out + ((uint64_t)__ldg(a.slot_of + b) << a.log2B) : a.out + bstart;
+  const uint32_t nlit = __shfl_sync(kFull, dv, 9 + ACE_S_LIT);
   const uint32_t lt = lanemask_lt();
 
-  Stream st[3];
+  Stream sn, so;
 #pragma unroll
-  for (int k = 0; k < 3; k++) {
+  for (int k = ACE_S_LEN; k <= ACE_S_OFF; k++) {
     uint64_t soff = (uint64_t)__shfl_sync(kFull, dv, 2 * k) | ((uint64_t)__shfl_sync(kFull, dv, 2 * k + 1) << 32);
     uint32_t sbytes = __shfl_sync(kFull, dv, 6 + k), nsym = __shfl_sync(kFull, dv, 9 + k);
-    if (!stream_open(a.arc + a.payload_off + soff, sbytes, nsym, m.ring + k * kRing, st[k], lane))
+    if (!stream_open(a.arc + a.payload_off + soff, sbytes, nsym, m.ring + (k - ACE_S_LEN) * kRing,
+                     k == ACE_S_LEN ? sn : so, lane))
       fail(a, ok, ACE_E_CORRUPT, b, 20 + k, lane);
   }
   if (!ok || ntok > a.max_ntok) {
@@ -347,12 +358,8 @@ __device__ bool entropy_block(const DecodeArgs& a, const WarpMem& m, const TokRe
   }
   cp_async_wait<2>();
   __syncwarp();
-  Stream& sl = st[ACE_S_LIT];
-  Stream& sn = st[ACE_S_LEN];
-  Stream& so = st[ACE_S_OFF];
-  uint8_t* rl = m.ring + ACE_S_LIT * kRing;
-  uint8_t* rn = m.ring + ACE_S_LEN * kRing;
-  uint8_t* ro = m.ring + ACE_S_OFF * kRing;
+  uint8_t* rn = m.ring;
+  uint8_t* ro = m.ring + kRing;
 
   // ---- lengths: escape values, then two codes per token
   if (!lut_build(sn, *m.lut, lane)) fail(a, ok, ACE_E_CORRUPT, b, 30, lane);
@@ -382,7 +389,6 @@ __device__ bool entropy_block(const DecodeArgs& a, const WarpMem& m, const TokRe
     if (own) {
       uint32_t t = (i - cbase) >> 1;
       g.tdst[t] = out_pos + io - to;
-      g.tlit[t] = lit_pos + il - tl;
       g.tml[t] = ml;
       if (t == ntok - 1 && ml) bad = true;  // the block's last token carries no match
     }
@@ -390,11 +396,8 @@ __device__ bool entropy_block(const DecodeArgs& a, const WarpMem& m, const TokRe
     lit_pos += __shfl_sync(kFull, il, 31);
     if (out_pos > blen) bad = true;
   });
-  if (lane == 0) {
-    g.tdst[ntok] = out_pos;
-    g.tlit[ntok] = lit_pos;
-  }
-  bad |= out_pos != blen || lit_pos != sl.nsym || esc_rank != nesc;
+  if (lane == 0) g.tdst[ntok] = out_pos;
+  bad |= out_pos != blen || lit_pos != nlit || esc_rank != nesc;
   if (__any_sync(kFull, bad)) fail(a, ok, ACE_E_CORRUPT, b, 32, lane);
 
   // ---- absolute offsets: off_width bytes for every token but the last
@@ -420,21 +423,80 @@ __device__ bool entropy_block(const DecodeArgs& a, const WarpMem& m, const TokRe
     }
     if (__any_sync(kFull, bad)) fail(a, ok, ACE_E_CORRUPT, b, 37, lane);
   }
+  if (ok) {
+    bool fin = stream_finished(sn) && stream_finished(so);
+    if (!__all_sync(kFull, fin)) fail(a, ok, ACE_E_CORRUPT, b, 40, lane);
+  }
+  cp_async_wait<0>();  // no ring fill may land after the next block reuses the rings
+  __syncwarp();
+  return ok;
+}
 
-  // ---- literals: literal i lands at its token's run start plus its offset in
-  // the run; token positions come through a shared-memory window
-  if (ok && lit_pos) {
+// Literal pass of one block, after the token pass of every block succeeded:
+// literal i lands at its token's run start plus its place in the run.  Token
+// positions come into a shared-memory window from the match records: token
+// t's run starts where the previous match ended and ends at its own match's
+// destination (the last token's at the block end).  Returns false if the
+// literal stream is corrupt.
+template <bool SEEK>
+__device__ bool literal_block(const DecodeArgs& a, const LitMem& m, uint32_t b, uint32_t lane) {
+  bool ok = true;
+  const uint32_t* dw = reinterpret_cast<const uint32_t*>(a.dir + b);
+  uint32_t dv = lane < 16 ? __ldg(dw + lane) : 0u;
+  const uint64_t B = (uint64_t)1 << a.log2B, bstart = (uint64_t)b << a.log2B;
+  const uint32_t blen = (uint32_t)min(B, a.total - bstart);
+  const uint32_t ntok = __shfl_sync(kFull, dv, 12);
+  const uint32_t nm = ntok ? ntok - 1 : 0;
+  uint8_t* obase = SEEK ? a.out + ((uint64_t)__ldg(a.slot_of + b) << a.log2B) : a.out + bstart;
+  const uint32_t lt = lanemask_lt();
+  Stream sl;
+  {
+    const int k = ACE_S_LIT;
+    uint64_t soff = (uint64_t)__shfl_sync(kFull, dv, 2 * k) | ((uint64_t)__shfl_sync(kFull, dv, 2 * k + 1) << 32);
+    uint32_t sbytes = __shfl_sync(kFull, dv, 6 + k), nsym = __shfl_sync(kFull, dv, 9 + k);
+    if (!stream_open(a.arc + a.payload_off + soff, sbytes, nsym, m.ring, sl, lane)) fail(a, ok, ACE_E_CORRUPT, b, 20, lane);
+  }
+  cp_async_wait<2>();
+  __syncwarp();
+  if (ok && sl.nsym) {
     if (!lut_build(sl, *m.lut, lane)) fail(a, ok, ACE_E_CORRUPT, b, 35, lane);
+    const uint4* rec = reinterpret_cast<const uint4*>(recs_of<SEEK>(a, b));
+    uint32_t cdst = 0, clit = 0;  // run start and first literal of the window's first token
     for (uint32_t w0 = 0; ok && w0 < ntok; w0 += a.window) {
       const uint32_t wn = min(a.window, ntok - w0);
-      for (uint32_t k = lane; k <= wn; k += 32) {
-        m.tdst[k] = g.tdst[w0 + k];
-        m.tlit[k] = g.tlit[w0 + k];
+      for (uint32_t k0 = 0; k0 < wn; k0 += 32) {
+        const uint32_t k = k0 + lane, t = w0 + k;
+        uint32_t D = blen, L = 0;  // the last token's run ends at the block end
+        if (k < wn && t < nm) {
+          const uint4 r = __ldcg(rec + t);
+          D = r.z;
+          L = r.w;
+        }
+        const uint32_t end = D + L;  // where the next token's run starts
+        const uint32_t prev = __shfl_up_sync(kFull, end, 1);
+        const uint32_t st0 = lane ? prev : cdst;
+        const uint32_t lr = k < wn ? D - st0 : 0u;
+        const uint32_t incl = warp_incl_sum(lr, lane);
+        if (k < wn) {
+          m.tdst[k] = st0;
+          m.tlit[k] = clit + incl - lr;
+        }
+        const uint32_t last = min(31u, wn - 1 - k0);
+        cdst = __shfl_sync(kFull, end, last);
+        clit += __shfl_sync(kFull, incl, last);
+      }
+      if (lane == 0) {
+        m.tdst[wn] = cdst;
+        m.tlit[wn] = clit;
       }
       __syncwarp();
       const uint32_t lend = m.tlit[wn];
+      if (lend > sl.nsym) {  // the token pass checked these counts: only a changed archive gets here
+        fail(a, ok, ACE_E_CORRUPT, b, 36, lane);
+        break;
+      }
       uint32_t tp = 0, cur_lit = m.tlit[0], cur_dst = m.tdst[0], nxt_lit = m.tlit[1];
-      rans_run(sl, rl, *m.lut, lend, lane, lt, [&](bool act, uint32_t i, uint32_t s) {
+      rans_run(sl, m.ring, *m.lut, lend, lane, lt, [&](bool act, uint32_t i, uint32_t s) {
         if (act) {
           while (nxt_lit <= i) {
             tp++;
@@ -448,12 +510,11 @@ __device__ bool entropy_block(const DecodeArgs& a, const WarpMem& m, const TokRe
       __syncwarp();
     }
   }
-
   if (ok) {
-    bool fin = stream_finished(st[0]) && stream_finished(st[1]) && stream_finished(st[2]);
-    if (!__all_sync(kFull, fin)) fail(a, ok, ACE_E_CORRUPT, b, 40, lane);
+    bool fin = stream_finished(sl);
+    if (!__all_sync(kFull, fin)) fail(a, ok, ACE_E_CORRUPT, b, 41, lane);
   }
-  cp_async_wait<0>();  // no ring fill may land after the next block reuses the rings
+  cp_async_wait<0>();
   __syncwarp();
   return ok;
 }
@@ -835,10 +896,15 @@ __device__ bool match_block(const DecodeArgs& a, MatchRec* gm, uint32_t b, uint3
   return ok;
 }
 
+// The three passes of a decode, each a persistent launch over the blocks:
+// tokens (lengths, offsets, match records), literals, and matches.
 // PASS_MATCH resolves blocks in (level, block) order with bounded waits on
 // their source blocks (match_level_kernel resolves one level of a whole
 // decode without them).
-enum { PASS_ENTROPY = 0, PASS_MATCH = 1 };
+enum { PASS_TOKENS = 0, PASS_LITERALS = 1, PASS_MATCH = 2 };
+
+// Registers per thread allowed by each pass's launch bounds (256 threads).
+#define ACE_PASS_MIN_CTAS(P) ((P) == PASS_TOKENS ? 3 : (P) == PASS_LITERALS ? 4 : 2)
 
 // The match pass keeps only its match-record area in shared memory.
 constexpr uint32_t kMatchSmem = 20 * kMatchGroup + 16;
@@ -855,28 +921,33 @@ __device__ __forceinline__ void publish(uint32_t* ready, uint32_t b, uint32_t ep
 // after it, resolves every block's matches in (level, block) order and
 // publishes the block.
 template <bool SEEK, int PASS>
-__global__ void __launch_bounds__(256, PASS == PASS_ENTROPY ? 3 : 2) decode_kernel(DecodeArgs a) {
+__global__ void __launch_bounds__(256, ACE_PASS_MIN_CTAS(PASS)) decode_kernel(DecodeArgs a) {
   extern __shared__ __align__(16) uint8_t smem[];
   const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const uint32_t epoch = *(volatile uint32_t*)&a.sh->epoch;
   const uint32_t n_items = SEEK ? *(volatile uint32_t*)&a.sh->n_work : a.n_items;
-  uint32_t* ticket = PASS == PASS_ENTROPY ? &a.sh->ticket : &a.sh->ticket2;
-  WarpMem m = carve(smem + (size_t)wid * a.warp_smem, a.window);
-  TokRec g = tok_records(a.warp_scratch + (size_t)(blockIdx.x * (blockDim.x >> 5) + wid) * a.warp_scratch_bytes,
-                         a.max_ntok);
-  MatchRec* gm = reinterpret_cast<MatchRec*>(smem + (size_t)wid * kMatchSmem);
+  // the literal and match passes run only after every block's tokens decoded
+  if (PASS != PASS_TOKENS && *(volatile uint32_t*)&a.sh->status) return;
+  uint32_t* ticket = PASS == PASS_TOKENS ? &a.sh->ticket : PASS == PASS_LITERALS ? &a.sh->ticket2 : &a.sh->ticket3;
+  uint8_t* wsm = smem + (size_t)wid * a.warp_smem;
   while (true) {
     uint32_t it = 0;
     if (lane == 0) it = atomicAdd(ticket, 1u);
     it = __shfl_sync(kFull, it, 0);
     if (it >= n_items) break;
     uint32_t b = __ldg(a.items + it);
-    if (PASS == PASS_ENTROPY) {
-      entropy_block<SEEK>(a, m, g, b, lane);
+    if (PASS == PASS_TOKENS) {
+      TokRec g = tok_records(a.warp_scratch + (size_t)(blockIdx.x * (blockDim.x >> 5) + wid) * a.warp_scratch_bytes,
+                             a.max_ntok);
+      token_block<SEEK>(a, carve_tok(wsm), g, b, lane);
+      continue;
+    }
+    if (PASS == PASS_LITERALS) {
+      literal_block<SEEK>(a, carve_lit(wsm, a.window), b, lane);
       continue;
     }
     const uint32_t ntok = __ldg(reinterpret_cast<const uint32_t*>(a.dir + b) + 12);
-    bool ok = match_block<SEEK, true>(a, gm, b, lane, epoch, ntok ? ntok - 1 : 0);
+    bool ok = match_block<SEEK, true>(a, reinterpret_cast<MatchRec*>(wsm), b, lane, epoch, ntok ? ntok - 1 : 0);
     if (SEEK && ok && a.slice) {
       // copy the part of this block inside [coord, coord + len) to the caller
       uint64_t bs = (uint64_t)b << a.log2B, be = min(bs + ((uint64_t)1 << a.log2B), a.total);
@@ -897,6 +968,7 @@ __global__ void __launch_bounds__(256, 2) match_level_kernel(DecodeArgs a) {
   extern __shared__ __align__(16) uint8_t smem[];
   const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const uint32_t nw = gridDim.x * (blockDim.x >> 5);
+  if (*(volatile uint32_t*)&a.sh->status) return;
   MatchRec* gm = reinterpret_cast<MatchRec*>(smem + (size_t)wid * kMatchSmem);
   uint32_t it = blockIdx.x * (blockDim.x >> 5) + wid;
   if (it >= a.n_items) return;
@@ -952,15 +1024,13 @@ struct BatchArgs {
 // are in its own (level, block) order, so in the match pass a warp only
 // ever waits on blocks of its archive that were handed out before its own.
 template <int PASS>
-__global__ void __launch_bounds__(256, PASS == PASS_ENTROPY ? 3 : 2) batch_decode_kernel(BatchArgs ba) {
+__global__ void __launch_bounds__(256, ACE_PASS_MIN_CTAS(PASS)) batch_decode_kernel(BatchArgs ba) {
   extern __shared__ __align__(16) uint8_t smem[];
   const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  WarpMem m = carve(smem + (size_t)wid * ba.warp_smem, ba.window);
-  TokRec g = tok_records(ba.warp_scratch + (size_t)(blockIdx.x * (blockDim.x >> 5) + wid) * ba.warp_scratch_bytes,
-                         ba.max_ntok);
-  MatchRec* gm = reinterpret_cast<MatchRec*>(smem + (size_t)wid * kMatchSmem);
+  if (PASS != PASS_TOKENS && *(volatile uint32_t*)&ba.sh->status) return;
+  uint8_t* wsm = smem + (size_t)wid * ba.warp_smem;
   const uint32_t epoch = *(volatile uint32_t*)&ba.sh->epoch;
-  uint32_t* ticket = PASS == PASS_ENTROPY ? &ba.sh->ticket : &ba.sh->ticket2;
+  uint32_t* ticket = PASS == PASS_TOKENS ? &ba.sh->ticket : PASS == PASS_LITERALS ? &ba.sh->ticket2 : &ba.sh->ticket3;
   while (true) {
     uint32_t it = 0;
     if (lane == 0) it = atomicAdd(ticket, 1u);
@@ -992,11 +1062,15 @@ __global__ void __launch_bounds__(256, PASS == PASS_ENTROPY ? 3 : 2) batch_decod
     a.recs = od.recs;
     a.match_ptr = od.match_ptr;
     uint32_t b = __ldg(od.order + (it - __ldg(ba.item_start + lo)));
-    if (PASS == PASS_ENTROPY) {
-      entropy_block<false>(a, m, g, b, lane);
+    if (PASS == PASS_TOKENS) {
+      TokRec g = tok_records(ba.warp_scratch + (size_t)(blockIdx.x * (blockDim.x >> 5) + wid) * ba.warp_scratch_bytes,
+                             ba.max_ntok);
+      token_block<false>(a, carve_tok(wsm), g, b, lane);
+    } else if (PASS == PASS_LITERALS) {
+      literal_block<false>(a, carve_lit(wsm, ba.window), b, lane);
     } else {
       const uint32_t ntok = __ldg(reinterpret_cast<const uint32_t*>(a.dir + b) + 12);
-      match_block<false, true>(a, gm, b, lane, epoch, ntok ? ntok - 1 : 0);
+      match_block<false, true>(a, reinterpret_cast<MatchRec*>(wsm), b, lane, epoch, ntok ? ntok - 1 : 0);
       publish(od.ready, b, epoch, lane);
     }
   }
@@ -1030,6 +1104,7 @@ __global__ void closure_kernel(ClosureArgs a) {
     a.sh->epoch += 1;
     a.sh->ticket = 0;
     a.sh->ticket2 = 0;
+    a.sh->ticket3 = 0;
     s_min = (uint32_t)a.first;
   }
   uint32_t ntar = (uint32_t)(a.last - a.first + 1);
@@ -1129,11 +1204,13 @@ struct CacheHdr {
   uint32_t next_slot;  // slots handed out in this epoch
   uint32_t n_front;
   uint32_t pad0[4];
-  uint32_t ticket2;    // next work item of the match pass
-  uint32_t pad[51];
+  uint32_t ticket2;    // next work item of the literal pass
+  uint32_t ticket3;    // next work item of the match pass
+  uint32_t pad[50];
 };
 static_assert(sizeof(CacheHdr) == 256, "cache header");
 static_assert(offsetof(CacheHdr, ticket2) == offsetof(ScratchHdr, ticket2), "shared header fields");
+static_assert(offsetof(CacheHdr, ticket3) == offsetof(ScratchHdr, ticket3), "shared header fields");
 static_assert(offsetof(CacheHdr, epoch) == offsetof(ScratchHdr, epoch), "shared header fields");
 static_assert(offsetof(CacheHdr, ticket) == offsetof(ScratchHdr, ticket), "shared header fields");
 static_assert(offsetof(CacheHdr, n_work) == offsetof(ScratchHdr, n_work), "shared header fields");
@@ -1278,6 +1355,7 @@ __global__ void cache_closure_kernel(CacheArgs c) {
     c.h->n_work = n;
     c.h->ticket = 0;
     c.h->ticket2 = 0;
+    c.h->ticket3 = 0;
   }
 }
 
@@ -1292,17 +1370,15 @@ struct CacheDecodeArgs {
 // Decodes a batch's work list into cache slots: the same two passes as a
 // seek, archive by archive.
 template <int PASS>
-__global__ void __launch_bounds__(256, PASS == PASS_ENTROPY ? 3 : 2) cache_decode_kernel(CacheDecodeArgs ca) {
+__global__ void __launch_bounds__(256, ACE_PASS_MIN_CTAS(PASS)) cache_decode_kernel(CacheDecodeArgs ca) {
   extern __shared__ __align__(16) uint8_t smem[];
   const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  WarpMem m = carve(smem + (size_t)wid * ca.warp_smem, ca.window);
-  TokRec g = tok_records(ca.warp_scratch + (size_t)(blockIdx.x * (blockDim.x >> 5) + wid) * ca.warp_scratch_bytes,
-                         ca.max_ntok);
-  MatchRec* gm = reinterpret_cast<MatchRec*>(smem + (size_t)wid * kMatchSmem);
+  uint8_t* wsm = smem + (size_t)wid * ca.warp_smem;
   const CacheArgs& c = ca.c;
+  if (PASS != PASS_TOKENS && *(volatile uint32_t*)&c.h->status) return;
   const uint32_t epoch = *(volatile uint32_t*)&c.h->epoch;
   const uint32_t n_items = *(volatile uint32_t*)&c.h->n_work;
-  uint32_t* ticket = PASS == PASS_ENTROPY ? &c.h->ticket : &c.h->ticket2;
+  uint32_t* ticket = PASS == PASS_TOKENS ? &c.h->ticket : PASS == PASS_LITERALS ? &c.h->ticket2 : &c.h->ticket3;
   while (true) {
     uint32_t it = 0;
     if (lane == 0) it = atomicAdd(ticket, 1u);
@@ -1329,11 +1405,15 @@ __global__ void __launch_bounds__(256, PASS == PASS_ENTROPY ? 3 : 2) cache_decod
     a.timeout_ns = ca.timeout_ns;
     a.recs = c.recs;
     a.match_ptr = nullptr;
-    if (PASS == PASS_ENTROPY) {
-      entropy_block<true>(a, m, g, b, lane);
+    if (PASS == PASS_TOKENS) {
+      TokRec g = tok_records(ca.warp_scratch + (size_t)(blockIdx.x * (blockDim.x >> 5) + wid) * ca.warp_scratch_bytes,
+                             ca.max_ntok);
+      token_block<true>(a, carve_tok(wsm), g, b, lane);
+    } else if (PASS == PASS_LITERALS) {
+      literal_block<true>(a, carve_lit(wsm, ca.window), b, lane);
     } else {
       const uint32_t ntok = __ldg(reinterpret_cast<const uint32_t*>(a.dir + b) + 12);
-      match_block<true, true>(a, gm, b, lane, epoch, ntok ? ntok - 1 : 0);
+      match_block<true, true>(a, reinterpret_cast<MatchRec*>(wsm), b, lane, epoch, ntok ? ntok - 1 : 0);
       publish(arc.ready, b, epoch, lane);
     }
   }
@@ -1361,6 +1441,7 @@ __global__ void cache_reset_kernel(CacheHdr* h) {
   h->next_slot = 0;
   h->ticket = 0;
   h->ticket2 = 0;
+  h->ticket3 = 0;
   h->n_work = 0;
 }
 
@@ -1390,6 +1471,7 @@ __global__ void begin_call_kernel(ScratchHdr* sh) {
   sh->epoch += 1;
   sh->ticket = 0;
   sh->ticket2 = 0;
+  sh->ticket3 = 0;
 }
 
 // FNV-1a 64 (Fowler/Noll/Vo): sequential by definition, one thread.
@@ -1426,7 +1508,7 @@ struct ace_index {
   int num_sms;
   ace_tune tune;
   // occupancy of the decode kernels, per (seek?, pass, warps per CTA, window)
-  mutable int occ_cache[2][2][9][9];
+  mutable int occ_cache[2][3][9][9];
   mutable int occ_level[9][9];  // the per-level match kernel
   // whole decodes resolve matches with one launch per level when there are
   // at most kMaxLevelLaunches levels: level L's blocks are
@@ -1529,12 +1611,13 @@ inline bool aligned(const void* p, uintptr_t a) { return (reinterpret_cast<uintp
     if ((x) != cudaSuccess) return ACE_E_CUDA; \
   } while (0)
 
-// Launch shape of one two-pass decode: the entropy pass (tables, rings and
-// token window in shared memory) and the match pass (match records only).
+// Launch shape of one three-pass decode: per pass the shared memory of a warp
+// (tokens: tables, two rings and escape values; literals: tables, a ring and
+// the token window; matches: the match records) and the grid.
 struct Launch {
   uint32_t warps, chunk;
-  uint32_t smem_e, smem_m;  // shared memory per warp
-  uint32_t grid_e, grid_m;
+  uint32_t smem[3];
+  uint32_t grid[3];
   uint64_t timeout;
 };
 
@@ -1555,50 +1638,73 @@ ace_status occupancy(K kernel, int device, uint32_t warps, size_t smem, int* occ
   return ACE_OK;
 }
 
-// occ_cache: 2 x 9 x 9 ints (pass, warps per CTA, window / 32), 0 = unknown
-template <class KE, class KM>
+// occ_cache: 3 x 9 x 9 ints (pass, warps per CTA, window / 32), 0 = unknown
+template <class K0, class K1, class K2>
 ace_status plan_launch(const ace_index* idx, const ace_tune* tune, uint32_t log2B, uint64_t max_items,
-                       uint64_t max_warps, KE ke, KM km, int* occ_cache, Launch* L) {
+                       uint64_t max_warps, K0 k0, K1 k1, K2 k2, int* occ_cache, Launch* L) {
   ace_tune t = tune ? *tune : idx->tune;
   L->warps = t.warps_per_cta ? t.warps_per_cta : 4;
   L->chunk = t.chunk_tokens ? t.chunk_tokens : 128;
   if (L->warps > kMaxWarpsPerCta || (L->chunk & 31) || L->chunk > kMaxWindow) return ACE_E_INVAL;
   L->timeout = t.wait_timeout_ns ? t.wait_timeout_ns : kDefaultTimeoutNs;
-  L->smem_e = warp_smem_bytes(L->chunk, esc_cap(log2B));
-  L->smem_m = kMatchSmem;
-  int& ce = occ_cache[(0 * 9 + L->warps) * 9 + L->chunk / 32];
-  int& cm = occ_cache[(1 * 9 + L->warps) * 9 + L->chunk / 32];
-  if (ce == 0) {
-    ace_status rc = occupancy(ke, idx->device, L->warps, (size_t)L->warps * L->smem_e, &ce);
-    if (rc) return rc;
+  L->smem[PASS_TOKENS] = tok_smem_bytes(esc_cap(log2B));
+  L->smem[PASS_LITERALS] = lit_smem_bytes(L->chunk);
+  L->smem[PASS_MATCH] = kMatchSmem;
+  int per[3];
+  for (int p = 0; p < 3; p++) {
+    int& c = occ_cache[(p * 9 + L->warps) * 9 + L->chunk / 32];
+    if (c == 0) {
+      const size_t smem = (size_t)L->warps * L->smem[p];
+      ace_status rc = p == 0 ? occupancy(k0, idx->device, L->warps, smem, &c)
+                      : p == 1 ? occupancy(k1, idx->device, L->warps, smem, &c)
+                               : occupancy(k2, idx->device, L->warps, smem, &c);
+      if (rc) return rc;
+    }
+    if (c < 0) return ACE_E_INVAL;
+    per[p] = c;
+    if (t.ctas_per_sm && (int)t.ctas_per_sm < per[p]) per[p] = (int)t.ctas_per_sm;
   }
-  if (cm == 0) {
-    ace_status rc = occupancy(km, idx->device, L->warps, (size_t)L->warps * L->smem_m, &cm);
-    if (rc) return rc;
-  }
-  if (ce < 0 || cm < 0) return ACE_E_INVAL;
-  int per_e = ce, per_m = cm;
-  if (t.ctas_per_sm && (int)t.ctas_per_sm < per_e) per_e = (int)t.ctas_per_sm;
-  if (t.ctas_per_sm && (int)t.ctas_per_sm < per_m) per_m = (int)t.ctas_per_sm;
   uint64_t need = std::max<uint64_t>(1, (max_items + L->warps - 1) / L->warps);
-  uint64_t ge = std::min<uint64_t>((uint64_t)idx->num_sms * per_e, max_warps / L->warps);
-  if (ge < 1) return ACE_E_NOMEM;
-  L->grid_e = (uint32_t)std::min(ge, need);
-  L->grid_m = (uint32_t)std::min<uint64_t>((uint64_t)idx->num_sms * per_m, need);
+  // the token pass keeps per-warp token records in scratch: at most max_warps warps
+  uint64_t g0 = std::min<uint64_t>((uint64_t)idx->num_sms * per[0], max_warps / L->warps);
+  if (g0 < 1) return ACE_E_NOMEM;
+  L->grid[PASS_TOKENS] = (uint32_t)std::min(g0, need);
+  L->grid[PASS_LITERALS] = (uint32_t)std::min<uint64_t>((uint64_t)idx->num_sms * per[1], need);
+  L->grid[PASS_MATCH] = (uint32_t)std::min<uint64_t>((uint64_t)idx->num_sms * per[2], need);
   return ACE_OK;
 }
 
 template <bool SEEK>
 ace_status plan_index_launch(const ace_index* idx, const ace_tune* tune, uint64_t max_items, uint64_t max_warps,
                              Launch* L) {
-  return plan_launch(idx, tune, idx->h.log2_block, max_items, max_warps, decode_kernel<SEEK, PASS_ENTROPY>,
-                     decode_kernel<SEEK, PASS_MATCH>, &idx->occ_cache[SEEK][0][0][0], L);
+  return plan_launch(idx, tune, idx->h.log2_block, max_items, max_warps, decode_kernel<SEEK, PASS_TOKENS>,
+                     decode_kernel<SEEK, PASS_LITERALS>, decode_kernel<SEEK, PASS_MATCH>,
+                     &idx->occ_cache[SEEK][0][0][0], L);
+}
+
+// Launches the passes in the mask (bit p: pass p) in order on s, each with
+// its own shared memory per warp.
+template <class K0, class K1, class K2, class Args>
+void launch_passes(const Launch& L, uint32_t passes, K0 k0, K1 k1, K2 k2, Args a, cudaStream_t s) {
+  const uint32_t th = 32 * L.warps;
+  if (passes & 1) {
+    a.warp_smem = L.smem[0];
+    k0<<<L.grid[0], th, (size_t)L.warps * L.smem[0], s>>>(a);
+  }
+  if (passes & 2) {
+    a.warp_smem = L.smem[1];
+    k1<<<L.grid[1], th, (size_t)L.warps * L.smem[1], s>>>(a);
+  }
+  if (passes & 4) {
+    a.warp_smem = L.smem[2];
+    k2<<<L.grid[2], th, (size_t)L.warps * L.smem[2], s>>>(a);
+  }
 }
 
 template <bool SEEK>
-void launch_two_pass(const Launch& L, const DecodeArgs& a, cudaStream_t s) {
-  decode_kernel<SEEK, PASS_ENTROPY><<<L.grid_e, 32 * L.warps, (size_t)L.warps * L.smem_e, s>>>(a);
-  decode_kernel<SEEK, PASS_MATCH><<<L.grid_m, 32 * L.warps, (size_t)L.warps * L.smem_m, s>>>(a);
+void launch_three_pass(const Launch& L, const DecodeArgs& a, cudaStream_t s) {
+  launch_passes(L, 7, decode_kernel<SEEK, PASS_TOKENS>, decode_kernel<SEEK, PASS_LITERALS>,
+                decode_kernel<SEEK, PASS_MATCH>, a, s);
 }
 
 }  // namespace
@@ -1765,8 +1871,8 @@ ace_status ace_scratch_init(const ace_index* idx, void* d_scratch, uint64_t scra
 
 namespace {
 
-// passes: bit 0 the entropy pass (with the call's header reset before it),
-// bit 1 the match pass.
+// passes: bit 0 the token pass (with the call's header reset before it),
+// bit 1 the literal pass, bit 2 the match pass.
 ace_status decode_all_passes(const ace_index* idx, uint32_t passes, void* d_out, uint64_t out_bytes, void* d_scratch,
                              uint64_t scratch_bytes, const ace_tune* tune, cudaStream_t s) {
   if (!idx || !d_scratch || (!d_out && idx->h.total_size)) return ACE_E_INVAL;
@@ -1790,7 +1896,7 @@ ace_status decode_all_passes(const ace_index* idx, uint32_t passes, void* d_out,
   a.window = L.chunk;
   a.max_ntok = idx->max_ntok;
   a.esc_cap = esc_cap(a.log2B);
-  a.warp_smem = L.smem_e;
+  a.warp_smem = L.smem[PASS_TOKENS];
   a.n_items = (uint32_t)idx->h.n_blocks;
   a.items = idx->d_order;
   a.out = static_cast<uint8_t*>(d_out);
@@ -1801,16 +1907,14 @@ ace_status decode_all_passes(const ace_index* idx, uint32_t passes, void* d_out,
   a.warp_scratch_bytes = warp_scratch_bytes(idx->max_ntok);
   a.recs = reinterpret_cast<MatchRec*>(static_cast<uint8_t*>(d_scratch) + SL.tail);
   a.match_ptr = idx->d_match_ptr;
-  if (passes & 1) {
-    begin_call_kernel<<<1, 1, 0, s>>>(sh);
-    decode_kernel<false, PASS_ENTROPY><<<L.grid_e, 32 * L.warps, (size_t)L.warps * L.smem_e, s>>>(a);
-  }
-  if ((passes & 2) && !idx->by_levels)
-    decode_kernel<false, PASS_MATCH><<<L.grid_m, 32 * L.warps, (size_t)L.warps * L.smem_m, s>>>(a);
-  if ((passes & 2) && idx->by_levels) {
+  if (passes & 1) begin_call_kernel<<<1, 1, 0, s>>>(sh);
+  launch_passes(L, passes & (idx->by_levels ? 3u : 7u), decode_kernel<false, PASS_TOKENS>,
+                decode_kernel<false, PASS_LITERALS>, decode_kernel<false, PASS_MATCH>, a, s);
+  if ((passes & 4) && idx->by_levels) {
+    a.warp_smem = L.smem[PASS_MATCH];
     int& occ = idx->occ_level[L.warps][L.chunk / 32];
     if (occ == 0) {
-      rc = occupancy(match_level_kernel, idx->device, L.warps, (size_t)L.warps * L.smem_m, &occ);
+      rc = occupancy(match_level_kernel, idx->device, L.warps, (size_t)L.warps * L.smem[PASS_MATCH], &occ);
       if (rc) return rc;
     }
     if (occ < 0) return ACE_E_INVAL;
@@ -1825,7 +1929,7 @@ ace_status decode_all_passes(const ace_index* idx, uint32_t passes, void* d_out,
       a.n_items = n;
       a.cur_level = l;
       const uint32_t grid = (uint32_t)std::min<uint64_t>((uint64_t)idx->num_sms * per_sm, (n + L.warps - 1) / L.warps);
-      match_level_kernel<<<grid, 32 * L.warps, (size_t)L.warps * L.smem_m, s>>>(a);
+      match_level_kernel<<<grid, 32 * L.warps, (size_t)L.warps * L.smem[PASS_MATCH], s>>>(a);
     }
   }
   CUDA_TRY(cudaGetLastError());
@@ -1838,14 +1942,13 @@ extern "C" {
 
 ace_status ace_decode_all(const ace_index* idx, void* d_out, uint64_t out_bytes, void* d_scratch,
                           uint64_t scratch_bytes, const ace_tune* tune, cudaStream_t s) {
-  return decode_all_passes(idx, 3, d_out, out_bytes, d_scratch, scratch_bytes, tune, s);
+  return decode_all_passes(idx, 7, d_out, out_bytes, d_scratch, scratch_bytes, tune, s);
 }
 
 ace_status ace_decode_pass(const ace_index* idx, int pass, void* d_out, uint64_t out_bytes, void* d_scratch,
                            uint64_t scratch_bytes, const ace_tune* tune, cudaStream_t s) {
-  if (pass != ACE_PASS_ENTROPY && pass != ACE_PASS_MATCH) return ACE_E_INVAL;
-  return decode_all_passes(idx, pass == ACE_PASS_ENTROPY ? 1u : 2u, d_out, out_bytes, d_scratch, scratch_bytes, tune,
-                           s);
+  if (pass != ACE_PASS_TOKENS && pass != ACE_PASS_LITERALS && pass != ACE_PASS_MATCH) return ACE_E_INVAL;
+  return decode_all_passes(idx, 1u << pass, d_out, out_bytes, d_scratch, scratch_bytes, tune, s);
 }
 
 ace_status ace_seek(const ace_index* idx, uint64_t coord, uint64_t len, void* d_out, uint64_t out_bytes,
@@ -1892,7 +1995,7 @@ ace_status ace_seek(const ace_index* idx, uint64_t coord, uint64_t len, void* d_
   a.window = L.chunk;
   a.max_ntok = idx->max_ntok;
   a.esc_cap = esc_cap(log2B);
-  a.warp_smem = L.smem_e;
+  a.warp_smem = L.smem[PASS_TOKENS];
   a.items = c.work;
   a.out = base + S1.tail;
   a.sh = sh;
@@ -1906,7 +2009,7 @@ ace_status ace_seek(const ace_index* idx, uint64_t coord, uint64_t len, void* d_
   a.warp_scratch_bytes = warp_scratch_bytes(idx->max_ntok);
   a.recs = reinterpret_cast<MatchRec*>(base + S1.tail + (cap << log2B));
   a.match_ptr = nullptr;
-  launch_two_pass<true>(L, a, s);
+  launch_three_pass<true>(L, a, s);
   CUDA_TRY(cudaGetLastError());
   return ACE_OK;
 }
@@ -1988,7 +2091,7 @@ struct ace_batch {
   uint64_t scratch_bytes;
   BatchArgs args;
   Launch L;
-  int occ[2][9][9];
+  int occ[3][9][9];
 };
 
 namespace {
@@ -2084,8 +2187,8 @@ ace_status ace_batch_create(const ace_index* const* idx, uint32_t n, void* const
   b->d_scratch = base;
   b->scratch_bytes = scratch_bytes;
   // the launch shape uses the largest block size's escape table
-  rc = plan_launch(idx[0], tune, B.max_log2B, B.items, B.n_warps, batch_decode_kernel<PASS_ENTROPY>,
-                   batch_decode_kernel<PASS_MATCH>, &b->occ[0][0][0], &b->L);
+  rc = plan_launch(idx[0], tune, B.max_log2B, B.items, B.n_warps, batch_decode_kernel<PASS_TOKENS>,
+                   batch_decode_kernel<PASS_LITERALS>, batch_decode_kernel<PASS_MATCH>, &b->occ[0][0][0], &b->L);
   if (rc == ACE_OK &&
       (cudaMemsetAsync(base, 0, B.warps, s) != cudaSuccess ||
        cudaMemcpyAsync(base + B.objs, od.data(), n * sizeof(ObjDesc), cudaMemcpyHostToDevice, s) != cudaSuccess ||
@@ -2102,7 +2205,7 @@ ace_status ace_batch_create(const ace_index* const* idx, uint32_t n, void* const
   a.n_objs = n;
   a.n_items = (uint32_t)B.items;
   a.window = b->L.chunk;
-  a.warp_smem = b->L.smem_e;
+  a.warp_smem = b->L.smem[PASS_TOKENS];
   a.esc_cap = esc_cap(B.max_log2B);
   a.max_ntok = (uint32_t)B.max_ntok;
   a.sh = reinterpret_cast<ScratchHdr*>(base);
@@ -2118,8 +2221,8 @@ ace_status ace_decode_batch(const ace_batch* b, cudaStream_t s) {
   if (!b->args.n_items) return ACE_OK;
   const Launch& L = b->L;
   begin_call_kernel<<<1, 1, 0, s>>>(b->args.sh);
-  batch_decode_kernel<PASS_ENTROPY><<<L.grid_e, 32 * L.warps, (size_t)L.warps * L.smem_e, s>>>(b->args);
-  batch_decode_kernel<PASS_MATCH><<<L.grid_m, 32 * L.warps, (size_t)L.warps * L.smem_m, s>>>(b->args);
+  launch_passes(L, 7, batch_decode_kernel<PASS_TOKENS>, batch_decode_kernel<PASS_LITERALS>,
+                batch_decode_kernel<PASS_MATCH>, b->args, s);
   CUDA_TRY(cudaGetLastError());
   return ACE_OK;
 }
@@ -2139,7 +2242,7 @@ ace_status ace_batch_sync(const ace_batch* b, cudaStream_t s) {
 
 ace_status ace_batch_launch_shape(const ace_batch* b, uint32_t* grid, uint32_t* warps_per_cta, uint32_t* window) {
   if (!b) return ACE_E_INVAL;
-  if (grid) *grid = b->L.grid_e;
+  if (grid) *grid = b->L.grid[PASS_TOKENS];
   if (warps_per_cta) *warps_per_cta = b->L.warps;
   if (window) *window = b->L.chunk;
   return ACE_OK;
@@ -2161,7 +2264,7 @@ struct ace_cache {
   CacheDecodeArgs dargs;
   Launch L;
   uint64_t req_off;  // requests are staged here by ace_seek_batch_host
-  int occ[2][9][9];
+  int occ[3][9][9];
 };
 
 namespace {
@@ -2270,8 +2373,8 @@ ace_status ace_cache_create(const ace_index* const* idx, uint32_t n, void* const
   c->mem = base;
   c->bytes = bytes;
   c->req_off = C.reqs;
-  rc = plan_launch(idx[0], tune, log2B, n_slots, C.n_warps, cache_decode_kernel<PASS_ENTROPY>,
-                   cache_decode_kernel<PASS_MATCH>, &c->occ[0][0][0], &c->L);
+  rc = plan_launch(idx[0], tune, log2B, n_slots, C.n_warps, cache_decode_kernel<PASS_TOKENS>,
+                   cache_decode_kernel<PASS_LITERALS>, cache_decode_kernel<PASS_MATCH>, &c->occ[0][0][0], &c->L);
   // header (epoch 1: no block is cached, since every ready flag starts at 0)
   CacheHdr h{};
   h.epoch = 1;
@@ -2301,7 +2404,7 @@ ace_status ace_cache_create(const ace_index* const* idx, uint32_t n, void* const
   a.n_reqs = 0;
   CacheDecodeArgs& d = c->dargs;
   d.window = c->L.chunk;
-  d.warp_smem = c->L.smem_e;
+  d.warp_smem = c->L.smem[PASS_TOKENS];
   d.esc_cap = esc_cap(log2B);
   d.max_ntok = (uint32_t)C.max_ntok;
   d.timeout_ns = c->L.timeout;
@@ -2323,8 +2426,8 @@ ace_status ace_seek_batch(const ace_cache* c, const ace_seek_req* d_reqs, uint32
   CacheDecodeArgs d = c->dargs;
   d.c = a;
   const Launch& L = c->L;
-  cache_decode_kernel<PASS_ENTROPY><<<L.grid_e, 32 * L.warps, (size_t)L.warps * L.smem_e, s>>>(d);
-  cache_decode_kernel<PASS_MATCH><<<L.grid_m, 32 * L.warps, (size_t)L.warps * L.smem_m, s>>>(d);
+  launch_passes(L, 7, cache_decode_kernel<PASS_TOKENS>, cache_decode_kernel<PASS_LITERALS>,
+                cache_decode_kernel<PASS_MATCH>, d, s);
   cache_copy_kernel<<<std::min<uint32_t>(n, 1024), 256, 0, s>>>(a, static_cast<uint8_t*>(d_pool));
   CUDA_TRY(cudaGetLastError());
   return ACE_OK;
@@ -2472,7 +2575,7 @@ ace_status ace_seek_noalloc(const ace_index* idx, uint64_t coord, uint64_t len, 
   a.window = L.chunk;
   a.max_ntok = idx->max_ntok;
   a.esc_cap = esc_cap(log2B);
-  a.warp_smem = L.smem_e;
+  a.warp_smem = L.smem[PASS_TOKENS];
   a.items = c.work;
   a.out = base + S.tail;
   a.sh = sh;
@@ -2486,7 +2589,7 @@ ace_status ace_seek_noalloc(const ace_index* idx, uint64_t coord, uint64_t len, 
   a.warp_scratch_bytes = warp_scratch_bytes(idx->max_ntok);
   a.recs = reinterpret_cast<MatchRec*>(base + S.tail + (cap << log2B));
   a.match_ptr = nullptr;
-  launch_two_pass<true>(L, a, s);
+  launch_three_pass<true>(L, a, s);
   CUDA_TRY(cudaGetLastError());
   // the status lives in the shared array, so the call waits for it
   uint32_t status = 0;

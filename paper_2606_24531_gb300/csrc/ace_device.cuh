@@ -23,8 +23,9 @@ struct ScratchHdr {
   uint32_t min_block;  // seek: smallest block reached by the closure
   uint64_t fnv;        // verify: last FNV-1a 64 computed
   uint64_t guard_bad;  // verify: guard bytes that differ from the canary
-  uint32_t ticket2;    // next work item of the match pass
-  uint32_t pad[51];
+  uint32_t ticket2;    // next work item of the literal pass
+  uint32_t ticket3;    // next work item of the match pass
+  uint32_t pad[50];
 };
 static_assert(sizeof(ScratchHdr) == 256, "scratch header");
 

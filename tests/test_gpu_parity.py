@@ -98,18 +98,18 @@ def test_edge_sizes_and_empty():
 
 
 def test_separate_passes_equal_decode_all():
-    """ace_decode_pass(ENTROPY) then ace_decode_pass(MATCH) on one stream is
-    ace_decode_all; a pass number outside the two is rejected."""
+    """ace_decode_pass(TOKENS), (LITERALS), then (MATCH) on one stream is
+    ace_decode_all; a pass number outside the three is rejected."""
     data = synth.generate("text", 1_500_000, 21)
     arc = ace.ace_encode(data, 14, 4)
     da = DeviceArchive(arc)
     out = torch.zeros(da.total, dtype=torch.uint8, device="cuda")
-    for p in (ace.ACE_PASS_ENTROPY, ace.ACE_PASS_MATCH):
+    for p in (ace.ACE_PASS_TOKENS, ace.ACE_PASS_LITERALS, ace.ACE_PASS_MATCH):
         ace.ace_decode_pass(da.idx, p, out, da.total, da.d_scratch, da.scratch_bytes, None, da.stream)
     assert da.sync() == ace.ACE_OK
     assert np.array_equal(out.cpu().numpy(), data)
     with pytest.raises(ace.AceError) as e:
-        ace.ace_decode_pass(da.idx, 2, out, da.total, da.d_scratch, da.scratch_bytes, None, da.stream)
+        ace.ace_decode_pass(da.idx, 3, out, da.total, da.d_scratch, da.scratch_bytes, None, da.stream)
     assert e.value.status == ace.ACE_E_INVAL
     da.close()
 
