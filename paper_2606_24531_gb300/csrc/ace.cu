@@ -496,7 +496,7 @@ __device__ bool literal_block(const DecodeArgs& a, const LitMem& m, uint32_t b, 
         break;
       }
       uint32_t tp = 0, cur_lit = m.tlit[0], cur_dst = m.tdst[0], nxt_lit = m.tlit[1];
-      rans_run(sl, m.ring, *m.lut, lend, lane, lt, [&](bool act, uint32_t i, uint32_t s) {
+      auto place = [&](bool act, uint32_t i, uint32_t s) {
         if (act) {
           while (nxt_lit <= i) {
             tp++;
@@ -506,7 +506,37 @@ __device__ bool literal_block(const DecodeArgs& a, const LitMem& m, uint32_t b, 
           }
           obase[cur_dst + (i - cur_lit)] = (uint8_t)s;
         }
-      });
+      };
+      if (sl.k == 0 && lend - sl.next >= 64) {
+        // slot-table streams: a partial round up to a round boundary, then
+        // full rounds, each lane's literal pointer moving 32 bytes a round
+        // until its literal index passes into the next token's run
+        if (sl.next & 31) {
+          bool act;
+          uint32_t i;
+          const uint32_t s = rans_round(sl, m.ring, *m.lut, lend, lane, lt, act, i);
+          place(act, i, s);
+        }
+        const uint32_t nfull = (lend - sl.next) >> 5;
+        uint32_t i = sl.next + lane;
+        auto seek_token = [&]() {
+          while (nxt_lit <= i) {
+            tp++;
+            cur_lit = nxt_lit;
+            cur_dst = m.tdst[tp];
+            nxt_lit = m.tlit[tp + 1];
+          }
+          return obase + cur_dst + (i - cur_lit);
+        };
+        uint8_t* op = seek_token();
+        table_full_rounds(sl, m.ring, *m.lut, nfull, lane, lt, [&](uint32_t s) {
+          if (i >= nxt_lit) op = seek_token();
+          *op = (uint8_t)s;
+          op += 32;
+          i += 32;
+        });
+      }
+      rans_run(sl, m.ring, *m.lut, lend, lane, lt, place);
       __syncwarp();
     }
   }

@@ -427,6 +427,58 @@ __device__ __forceinline__ void rans_run(Stream& st, uint8_t* ring, const Lut& l
   }
 }
 
+// One full round in slot-table mode (st.k == 0): every lane decodes one
+// symbol of state x, with renormalisation bytes read from the ring at the
+// running position pos as in rans_round.  The caller checks the ring.
+__device__ __forceinline__ uint32_t table_round(uint32_t& x, uint32_t& pos, const uint8_t* ring, const Lut& lut,
+                                                uint32_t lt) {
+  const uint32_t slot = x & (ACE_SCALE - 1);
+  const uint32_t s = lut.sym[slot];
+  const uint32_t fc = lut.fc[s];
+  const uint32_t xn = (fc >> 16) * (x >> ACE_SCALE_BITS) + slot - (fc & 0xffffu);
+  const bool p1 = xn < ACE_RANS_L, p2 = xn < (1u << 15);
+  const uint32_t b1 = __ballot_sync(kFull, p1), b2 = __ballot_sync(kFull, p2);
+  const uint32_t p = pos + __popc(b1 & lt) + __popc(b2 & lt);
+  const uint32_t c0 = ring[p & (kRing - 1)], c1 = ring[(p + 1) & (kRing - 1)];
+  const uint32_t x1 = (xn << 8) | c0, x2 = (x1 << 8) | c1;
+  x = p2 ? x2 : (p1 ? x1 : xn);
+  pos += __popc(b1) + __popc(b2);
+  return s;
+}
+
+// nfull full rounds in slot-table mode from a round boundary (st.next a
+// multiple of 32), handing each round's symbol to emit(s) in order.  The ring
+// is checked once per two rounds: a round reads at most 64 bytes, and after a
+// check the position is less than one segment into the ring, whose two oldest
+// segments have landed.
+template <class Emit>
+__device__ __forceinline__ void table_full_rounds(Stream& st, uint8_t* ring, const Lut& lut, uint32_t nfull,
+                                                  uint32_t lane, uint32_t lt, Emit&& emit) {
+  uint32_t x = st.x, pos = st.pos, base = st.base;
+  auto check = [&]() {
+    if (pos >= base + kSeg) {
+      ring_issue(st, ring, base + kRing, lane);
+      base += kSeg;
+      cp_async_wait<2>();
+      __syncwarp();
+    }
+  };
+  uint32_t r = 0;
+  for (; r + 2 <= nfull; r += 2) {
+    check();
+    emit(table_round(x, pos, ring, lut, lt));
+    emit(table_round(x, pos, ring, lut, lt));
+  }
+  if (r < nfull) {
+    check();
+    emit(table_round(x, pos, ring, lut, lt));
+  }
+  st.x = x;
+  st.pos = pos;
+  st.base = base;
+  st.next += 32 * nfull;
+}
+
 // All symbols consumed, all bytes consumed and every state back at L.
 __device__ __forceinline__ bool stream_finished(const Stream& st) {
   bool ok = st.next == st.nsym && st.pos == st.nbytes && (st.nsym == 0 || st.x == ACE_RANS_L);
