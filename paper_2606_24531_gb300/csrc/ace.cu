@@ -251,8 +251,12 @@ __host__ __device__ inline uint32_t tok_smem_bytes(uint32_t escn) {
   return (sizeof(Lut) + 2 * kRing + 2 * escn + 15) & ~15u;
 }
 
-__host__ __device__ inline uint32_t lit_smem_bytes(uint32_t window) {
-  return (sizeof(Lut) + kRing + 8 * (window + 1) + 15) & ~15u;
+// A plain seek's literal pass runs a handful of warps, each on its own
+// critical path: a deeper ring keeps its renormalisation bytes ahead of it.
+constexpr uint32_t kSeekRing = 2048;
+
+__host__ __device__ inline uint32_t lit_smem_bytes(uint32_t window, uint32_t ring) {
+  return (sizeof(Lut) + ring + 8 * (window + 1) + 15) & ~15u;
 }
 
 __host__ __device__ inline uint64_t warp_scratch_bytes(uint64_t max_ntok) {
@@ -267,11 +271,11 @@ __device__ inline TokMem carve_tok(uint8_t* base) {
   return m;
 }
 
-__device__ inline LitMem carve_lit(uint8_t* base, uint32_t window) {
+__device__ inline LitMem carve_lit(uint8_t* base, uint32_t window, uint32_t ring) {
   LitMem m;
   m.lut = reinterpret_cast<Lut*>(base);
   m.ring = base + sizeof(Lut);
-  m.tdst = reinterpret_cast<uint32_t*>(m.ring + kRing);
+  m.tdst = reinterpret_cast<uint32_t*>(m.ring + ring);
   m.tlit = m.tdst + (window + 1);
   return m;
 }
@@ -291,6 +295,16 @@ struct Addr {
     if (SEEK) {
       uint64_t k = p >> a.log2B;
       return a.out + ((uint64_t)__ldg(a.slot_of + k) << a.log2B) + (p & ((1ull << a.log2B) - 1));
+    }
+    return a.out + p;
+  }
+  // the same, with block b's own bytes at obase without a slot lookup
+  __device__ __forceinline__ static const uint8_t* at(const DecodeArgs& a, uint64_t p, uint64_t b, const uint8_t* obase) {
+    if (SEEK) {
+      uint64_t k = p >> a.log2B;
+      const uint64_t off = p & ((1ull << a.log2B) - 1);
+      if (k == b) return obase + off;
+      return a.out + ((uint64_t)__ldg(a.slot_of + k) << a.log2B) + off;
     }
     return a.out + p;
   }
@@ -321,6 +335,46 @@ template <bool SEEK>
 __device__ __forceinline__ MatchRec* recs_of(const DecodeArgs& a, uint32_t b) {
   if (!SEEK) return a.recs + __ldg(a.match_ptr + b);
   return a.recs + (uint64_t)__ldg(a.slot_of + b) * a.max_ntok;
+}
+
+// n bytes from src to dst by one warp: 16-byte vectors, four per lane in
+// flight, when both are 16-byte aligned, else sixteen independent byte loads
+// per lane before their stores (a store may not be passed by a later load
+// the compiler cannot prove disjoint, so each batch is written out whole).
+__device__ __forceinline__ void warp_copy(uint8_t* dst, const uint8_t* src, uint64_t n, uint32_t lane) {
+  if (((reinterpret_cast<uintptr_t>(dst) | reinterpret_cast<uintptr_t>(src)) & 15) == 0) {
+    const uint64_t nv = n >> 4;
+    const uint4* s4 = reinterpret_cast<const uint4*>(src);
+    uint4* d4 = reinterpret_cast<uint4*>(dst);
+    for (uint64_t v0 = 0; v0 < nv; v0 += 128) {
+      uint4 t[4];
+#pragma unroll
+      for (uint32_t u = 0; u < 4; u++) {
+        const uint64_t v = v0 + 32 * u + lane;
+        if (v < nv) t[u] = __ldcg(s4 + v);
+      }
+#pragma unroll
+      for (uint32_t u = 0; u < 4; u++) {
+        const uint64_t v = v0 + 32 * u + lane;
+        if (v < nv) d4[v] = t[u];
+      }
+    }
+    for (uint64_t p = (nv << 4) + lane; p < n; p += 32) dst[p] = __ldcg(src + p);
+    return;
+  }
+  for (uint64_t p0 = 0; p0 < n; p0 += 512) {
+    uint8_t t[16];
+#pragma unroll
+    for (uint32_t u = 0; u < 16; u++) {
+      const uint64_t p = p0 + 32 * u + lane;
+      if (p < n) t[u] = __ldcg(src + p);
+    }
+#pragma unroll
+    for (uint32_t u = 0; u < 16; u++) {
+      const uint64_t p = p0 + 32 * u + lane;
+      if (p < n) dst[p] = t[u];
+    }
+  }
 }
 
 // Token pass of one block (Section 3: the block boundary is the entry point
@@ -438,7 +492,7 @@ __device__ bool token_block(const DecodeArgs& a, const TokMem& m, const TokRec& 
 // t's run starts where the previous match ended and ends at its own match's
 // destination (the last token's at the block end).  Returns false if the
 // literal stream is corrupt.
-template <bool SEEK>
+template <bool SEEK, uint32_t RING>
 __device__ bool literal_block(const DecodeArgs& a, const LitMem& m, uint32_t b, uint32_t lane) {
   bool ok = true;
   const uint32_t* dw = reinterpret_cast<const uint32_t*>(a.dir + b);
@@ -454,9 +508,9 @@ __device__ bool literal_block(const DecodeArgs& a, const LitMem& m, uint32_t b, 
     const int k = ACE_S_LIT;
     uint64_t soff = (uint64_t)__shfl_sync(kFull, dv, 2 * k) | ((uint64_t)__shfl_sync(kFull, dv, 2 * k + 1) << 32);
     uint32_t sbytes = __shfl_sync(kFull, dv, 6 + k), nsym = __shfl_sync(kFull, dv, 9 + k);
-    if (!stream_open(a.arc + a.payload_off + soff, sbytes, nsym, m.ring, sl, lane)) fail(a, ok, ACE_E_CORRUPT, b, 20, lane);
+    if (!stream_open<RING>(a.arc + a.payload_off + soff, sbytes, nsym, m.ring, sl, lane)) fail(a, ok, ACE_E_CORRUPT, b, 20, lane);
   }
-  cp_async_wait<2>();
+  cp_async_wait<RING / kSeg - 2>();
   __syncwarp();
   if (ok && sl.nsym) {
     if (!lut_build(sl, *m.lut, lane)) fail(a, ok, ACE_E_CORRUPT, b, 35, lane);
@@ -514,7 +568,7 @@ __device__ bool literal_block(const DecodeArgs& a, const LitMem& m, uint32_t b, 
         if (sl.next & 31) {
           bool act;
           uint32_t i;
-          const uint32_t s = rans_round(sl, m.ring, *m.lut, lend, lane, lt, act, i);
+          const uint32_t s = rans_round<RING>(sl, m.ring, *m.lut, lend, lane, lt, act, i);
           place(act, i, s);
         }
         const uint32_t nfull = (lend - sl.next) >> 5;
@@ -529,14 +583,14 @@ __device__ bool literal_block(const DecodeArgs& a, const LitMem& m, uint32_t b, 
           return obase + cur_dst + (i - cur_lit);
         };
         uint8_t* op = seek_token();
-        table_full_rounds(sl, m.ring, *m.lut, nfull, lane, lt, [&](uint32_t s) {
+        table_full_rounds<RING>(sl, m.ring, *m.lut, nfull, lane, lt, [&](uint32_t s) {
           if (i >= nxt_lit) op = seek_token();
           *op = (uint8_t)s;
           op += 32;
           i += 32;
         });
       }
-      rans_run(sl, m.ring, *m.lut, lend, lane, lt, place);
+      rans_run<RING>(sl, m.ring, *m.lut, lend, lane, lt, place);
       __syncwarp();
     }
   }
@@ -561,7 +615,8 @@ constexpr uint32_t kLongMin = 512;
 
 // Source of a short match: the aligned 8-byte words covering [S, S + len).
 template <bool SEEK>
-__device__ __forceinline__ void short_load(const DecodeArgs& a, uint64_t S, uint32_t len, uint64_t (&w)[5]) {
+__device__ __forceinline__ void short_load(const DecodeArgs& a, uint64_t S, uint32_t len, uint64_t (&w)[5], uint64_t b,
+                                           const uint8_t* obase) {
   const uint64_t a0 = S & ~7ull;
   const uint32_t off = (uint32_t)(S & 7);
 #pragma unroll
@@ -570,10 +625,10 @@ __device__ __forceinline__ void short_load(const DecodeArgs& a, uint64_t S, uint
     w[k] = 0;
     if (8 * k < off + len) {
       if (q + 8 <= a.total) {
-        w[k] = __ldcg(reinterpret_cast<const unsigned long long*>(Addr<SEEK>::at(a, q)));
+        w[k] = __ldcg(reinterpret_cast<const unsigned long long*>(Addr<SEEK>::at(a, q, b, obase)));
       } else {
         for (uint32_t t = 0; t < 8 && q + t < a.total; t++)
-          w[k] |= (uint64_t)__ldcg(Addr<SEEK>::at(a, q + t)) << (8 * t);
+          w[k] |= (uint64_t)__ldcg(Addr<SEEK>::at(a, q + t, b, obase)) << (8 * t);
       }
     }
   }
@@ -793,6 +848,11 @@ __device__ bool match_block(const DecodeArgs& a, MatchRec* gm, uint32_t b, uint3
         const uint32_t* flags = WAIT ? a.ready : a.level;
         f0[q] = ld_relaxed(flags + k0);
         f1[q] = k1 != k0 ? ld_relaxed(flags + k1) : f0[q];
+        if (SEEK && !WAIT) {  // a seek's source blocks must be in its closure
+          const uint32_t r0 = ld_relaxed(a.ready + k0), r1 = ld_relaxed(a.ready + k1);
+          if (r0 != epoch) f0[q] |= 0x80000000u;
+          if (r1 != epoch) f1[q] |= 0x80000000u;
+        }
       }
       if (rend > bstart) {  // bytes of this block: the group's matches writing them
         const uint32_t s_rel = S > bstart ? (uint32_t)(S - bstart) : 0u, e_rel = (uint32_t)(rend - bstart);
@@ -843,10 +903,10 @@ __device__ bool match_block(const DecodeArgs& a, MatchRec* gm, uint32_t b, uint3
       if (sgo) {  // short: the next match's loads go out before the previous one's stores
         uint64_t cur[5], nxt[5];
         uint32_t jc = lane + 32 * (__ffs(sgo) - 1), rest = sgo & (sgo - 1);
-        short_load<SEEK>(a, gS[jc], gL[jc], cur);
+        short_load<SEEK>(a, gS[jc], gL[jc], cur, b, obase);
         while (true) {
           const uint32_t jn = rest ? lane + 32 * (__ffs(rest) - 1) : 0u;
-          if (rest) short_load<SEEK>(a, gS[jn], gL[jn], nxt);
+          if (rest) short_load<SEEK>(a, gS[jn], gL[jn], nxt, b, obase);
           short_store(obase + gD[jc], (uint32_t)(gS[jc] & 7), gL[jc], cur);
           if (!rest) break;
           rest &= rest - 1;
@@ -895,7 +955,7 @@ __device__ bool match_block(const DecodeArgs& a, MatchRec* gm, uint32_t b, uint3
             while (gX[jc + 1] <= p) jc++;
             const uint32_t i = p - gX[jc], ml = gL[jc];
             const uint64_t S = gS[jc], d = bstart + gD[jc] - S;
-            v[u] = __ldcg(Addr<SEEK>::at(a, src_index(S, d, ml, i)));
+            v[u] = __ldcg(Addr<SEEK>::at(a, src_index(S, d, ml, i), b, obase));
             dp[u] = obase + gD[jc] + i;
           }
         }
@@ -915,8 +975,10 @@ __device__ bool match_block(const DecodeArgs& a, MatchRec* gm, uint32_t b, uint3
         const uint64_t S = gS[j], D = bstart + gD[j];
         const uint64_t rend = S + min((uint64_t)gL[j], D - S);
         const uint64_t k0 = S >> a.log2B, k1 = min((rend - 1) >> a.log2B, (uint64_t)b - 1);
-        for (uint64_t k = k0 + 1; k < k1; k++)  // a source spanning more than two earlier blocks
+        for (uint64_t k = k0 + 1; k < k1; k++) {  // a source spanning more than two earlier blocks
           if (__ldg(a.level + k) >= a.cur_level) bad = true;
+          if (SEEK && ld_relaxed(a.ready + k) != epoch) bad = true;
+        }
       }
       if (__any_sync(kFull, bad)) fail(a, ok, ACE_E_CORRUPT, b, 39, lane);
       __syncwarp();
@@ -973,7 +1035,8 @@ __global__ void __launch_bounds__(256, ACE_PASS_MIN_CTAS(PASS)) decode_kernel(De
       continue;
     }
     if (PASS == PASS_LITERALS) {
-      literal_block<SEEK>(a, carve_lit(wsm, a.window), b, lane);
+      constexpr uint32_t ring = SEEK ? kSeekRing : kRing;
+      literal_block<SEEK, ring>(a, carve_lit(wsm, a.window, ring), b, lane);
       continue;
     }
     const uint32_t ntok = __ldg(reinterpret_cast<const uint32_t*>(a.dir + b) + 12);
@@ -983,7 +1046,7 @@ __global__ void __launch_bounds__(256, ACE_PASS_MIN_CTAS(PASS)) decode_kernel(De
       uint64_t bs = (uint64_t)b << a.log2B, be = min(bs + ((uint64_t)1 << a.log2B), a.total);
       uint64_t lo = max(bs, a.coord), hi = min(be, a.coord + a.len);
       const uint8_t* src = a.out + ((uint64_t)a.slot_of[b] << a.log2B) - bs;
-      for (uint64_t p = lo + lane; p < hi; p += 32) a.slice[p - a.coord] = __ldcg(src + p);
+      if (hi > lo) warp_copy(a.slice + (lo - a.coord), src + lo, hi - lo, lane);
     }
     publish(a.ready, b, epoch, lane);
   }
@@ -994,31 +1057,52 @@ __global__ void __launch_bounds__(256, ACE_PASS_MIN_CTAS(PASS)) decode_kernel(De
 // waits.  Blocks are dealt out statically (block k of the level to warp
 // k mod the warps in the grid), and each warp fetches its next block's
 // number and record range while it resolves the current one.
+template <bool SEEK>
 __global__ void __launch_bounds__(256, 2) match_level_kernel(DecodeArgs a) {
   extern __shared__ __align__(16) uint8_t smem[];
   const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const uint32_t nw = gridDim.x * (blockDim.x >> 5);
   if (*(volatile uint32_t*)&a.sh->status) return;
+  const uint32_t epoch = *(volatile uint32_t*)&a.sh->epoch;
+  // a seek's level ranges come from its closure, on the device
+  const uint32_t* items = a.items;
+  uint32_t n_items = a.n_items;
+  if (SEEK) {
+    const uint32_t l0 = *(volatile uint32_t*)&a.sh->lv_start[a.cur_level];
+    items = a.items + l0;
+    n_items = *(volatile uint32_t*)&a.sh->lv_start[a.cur_level + 1] - l0;
+  }
   MatchRec* gm = reinterpret_cast<MatchRec*>(smem + (size_t)wid * kMatchSmem);
   uint32_t it = blockIdx.x * (blockDim.x >> 5) + wid;
-  if (it >= a.n_items) return;
-  uint32_t b = __ldg(a.items + it);
-  uint64_t p0 = __ldg(a.match_ptr + b), p1 = __ldg(a.match_ptr + b + 1);
+  if (it >= n_items) return;
+  auto n_matches = [&](uint32_t b) -> uint32_t {
+    if (SEEK) {
+      const uint32_t ntok = __ldg(reinterpret_cast<const uint32_t*>(a.dir + b) + 12);
+      return ntok ? ntok - 1 : 0;
+    }
+    return (uint32_t)(__ldg(a.match_ptr + b + 1) - __ldg(a.match_ptr + b));
+  };
+  uint32_t b = __ldg(items + it);
+  uint32_t nm = n_matches(b);
   while (true) {
     const uint32_t nx = it + nw;
-    uint32_t bn = 0;
-    uint64_t q0 = 0, q1 = 0;
-    if (nx < a.n_items) {
-      bn = __ldg(a.items + nx);
-      q0 = __ldg(a.match_ptr + bn);
-      q1 = __ldg(a.match_ptr + bn + 1);
+    uint32_t bn = 0, nmn = 0;
+    if (nx < n_items) {
+      bn = __ldg(items + nx);
+      nmn = n_matches(bn);
     }
-    match_block<false, false>(a, gm, b, lane, 0, (uint32_t)(p1 - p0));
-    if (nx >= a.n_items) break;
+    const bool ok = match_block<SEEK, false>(a, gm, b, lane, epoch, nm);
+    if (SEEK && ok && a.slice) {
+      // the part of this block inside [coord, coord + len) to the caller
+      uint64_t bs = (uint64_t)b << a.log2B, be = min(bs + ((uint64_t)1 << a.log2B), a.total);
+      uint64_t lo = max(bs, a.coord), hi = min(be, a.coord + a.len);
+      const uint8_t* src = a.out + ((uint64_t)a.slot_of[b] << a.log2B) - bs;
+      if (hi > lo) warp_copy(a.slice + (lo - a.coord), src + lo, hi - lo, lane);
+    }
+    if (nx >= n_items) break;
     it = nx;
     b = bn;
-    p0 = q0;
-    p1 = q1;
+    nm = nmn;
   }
 }
 
@@ -1097,7 +1181,7 @@ __global__ void __launch_bounds__(256, ACE_PASS_MIN_CTAS(PASS)) batch_decode_ker
                              ba.max_ntok);
       token_block<false>(a, carve_tok(wsm), g, b, lane);
     } else if (PASS == PASS_LITERALS) {
-      literal_block<false>(a, carve_lit(wsm, ba.window), b, lane);
+      literal_block<false, kRing>(a, carve_lit(wsm, ba.window, kRing), b, lane);
     } else {
       const uint32_t ntok = __ldg(reinterpret_cast<const uint32_t*>(a.dir + b) + 12);
       match_block<false, true>(a, reinterpret_cast<MatchRec*>(wsm), b, lane, epoch, ntok ? ntok - 1 : 0);
@@ -1120,15 +1204,23 @@ struct ClosureArgs {
   uint64_t nb;
   uint64_t first, last;  // target blocks
   uint64_t cap;          // slots available
+  const uint32_t* level; // by levels: each block's dependency level (else null)
+  uint32_t n_levels;
+  uint32_t* ready;       // by levels: closure blocks get the call's epoch
 };
 
 // The blocks a seek must decode: its target blocks and, transitively, every
-// block their matches read (Section 2), listed in ascending block order (a
-// valid decode order: sources always precede).  One CTA.
+// block their matches read (Section 2).  Breadth first from the targets, a
+// warp per frontier block with its lanes over the block's dependency
+// intervals; then an ordered compaction of the marked blocks gives each its
+// slot, and the work list is ordered by dependency level (blocks of a level
+// in ascending order) with the level ranges in the scratch header -- a valid
+// decode order either way, since sources always precede.  One CTA.
 __global__ void closure_kernel(ClosureArgs a) {
   __shared__ uint32_t n_next, s_min;
   __shared__ uint32_t wsum[32];
   __shared__ uint32_t carry;
+  __shared__ uint32_t lcnt[kMaxLevelLaunches + 1];
   const uint32_t tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
   if (tid == 0) {
     a.sh->epoch += 1;
@@ -1137,6 +1229,7 @@ __global__ void closure_kernel(ClosureArgs a) {
     a.sh->ticket3 = 0;
     s_min = (uint32_t)a.first;
   }
+  if (tid <= kMaxLevelLaunches) lcnt[tid] = 0;
   uint32_t ntar = (uint32_t)(a.last - a.first + 1);
   for (uint32_t i = tid; i < ntar; i += blockDim.x) {
     uint32_t b = (uint32_t)a.first + i;
@@ -1150,16 +1243,19 @@ __global__ void closure_kernel(ClosureArgs a) {
   while (n_front) {
     if (tid == 0) n_next = 0;
     __syncthreads();
-    for (uint32_t i = tid; i < n_front; i += blockDim.x) {
-      uint32_t b = cur[i];
-      for (uint32_t e = a.dep_ptr[b]; e < a.dep_ptr[b + 1]; e++)
-        for (uint32_t k = a.dep_iv[2 * e]; k <= a.dep_iv[2 * e + 1]; k++) {
+    for (uint32_t f = wid; f < n_front; f += nw) {
+      const uint32_t b = cur[f];
+      const uint32_t e1 = a.dep_ptr[b + 1];
+      for (uint32_t e = a.dep_ptr[b] + lane; e < e1; e += 32) {
+        const uint32_t k0 = a.dep_iv[2 * e], k1 = a.dep_iv[2 * e + 1];
+        for (uint32_t k = k0; k <= k1; k++) {
           uint32_t old = atomicOr(&a.marks[k >> 5], 1u << (k & 31));
           if (!(old & (1u << (k & 31)))) {
             nxt[atomicAdd(&n_next, 1u)] = k;
             atomicMin(&s_min, k);
           }
         }
+      }
     }
     __syncthreads();
     n_front = n_next;
@@ -1168,7 +1264,8 @@ __global__ void closure_kernel(ClosureArgs a) {
     nxt = t;
     __syncthreads();
   }
-  // ordered compaction of the marked blocks, clearing the marks behind it
+  // ordered compaction of the marked blocks into front0, clearing the marks
+  // behind it; a block's slot is its place in ascending order
   if (tid == 0) carry = 0;
   __syncthreads();
   uint32_t w0 = s_min >> 5, w1 = (uint32_t)(a.last >> 5);
@@ -1190,8 +1287,10 @@ __global__ void closure_kernel(ClosureArgs a) {
       uint32_t bit = __ffs(bits) - 1;
       bits &= bits - 1;
       uint32_t b = wi * 32 + bit;
-      a.work[pos] = b;
-      if (pos < a.cap) a.slot_of[b] = pos;
+      if (pos < a.cap) {
+        a.front0[pos] = b;
+        a.slot_of[b] = pos;
+      }
       pos++;
     }
     if (wi <= w1) a.marks[wi] = 0;
@@ -1199,13 +1298,38 @@ __global__ void closure_kernel(ClosureArgs a) {
     if (tid == blockDim.x - 1) carry = pos;
     __syncthreads();
   }
-  if (tid == 0) {
-    uint32_t n = carry;
-    if (n > a.cap) {
+  const uint32_t n = carry;
+  if (n > a.cap) {
+    if (tid == 0) {
       record_error(&a.sh->status, &a.sh->err_block, &a.sh->err_where, ACE_E_NOMEM, n, 50);
-      n = 0;
+      a.sh->n_work = 0;
     }
+    return;
+  }
+  // the work list by level (one level when levels are not used)
+  const uint32_t epoch = a.sh->epoch;
+  for (uint32_t i = tid; i < n; i += blockDim.x) {
+    const uint32_t b = a.front0[i];
+    atomicAdd(&lcnt[a.level ? a.level[b] : 0], 1u);
+    if (a.ready) a.ready[b] = epoch;  // members of this seek's closure
+  }
+  __syncthreads();
+  if (tid == 0) {
+    const uint32_t nl = a.level ? a.n_levels : 1;
+    uint32_t c = 0;
+    for (uint32_t l = 0; l < nl; l++) {
+      const uint32_t k = lcnt[l];
+      lcnt[l] = c;
+      a.sh->lv_start[l] = c;
+      c += k;
+    }
+    a.sh->lv_start[nl] = c;
     a.sh->n_work = n;
+  }
+  __syncthreads();
+  for (uint32_t i = tid; i < n; i += blockDim.x) {
+    const uint32_t b = a.front0[i];
+    a.work[atomicAdd(&lcnt[a.level ? a.level[b] : 0], 1u)] = b;
   }
 }
 
@@ -1440,7 +1564,7 @@ __global__ void __launch_bounds__(256, ACE_PASS_MIN_CTAS(PASS)) cache_decode_ker
                              ca.max_ntok);
       token_block<true>(a, carve_tok(wsm), g, b, lane);
     } else if (PASS == PASS_LITERALS) {
-      literal_block<true>(a, carve_lit(wsm, ca.window), b, lane);
+      literal_block<true, kRing>(a, carve_lit(wsm, ca.window, kRing), b, lane);
     } else {
       const uint32_t ntok = __ldg(reinterpret_cast<const uint32_t*>(a.dir + b) + 12);
       match_block<true, true>(a, reinterpret_cast<MatchRec*>(wsm), b, lane, epoch, ntok ? ntok - 1 : 0);
@@ -1452,15 +1576,19 @@ __global__ void __launch_bounds__(256, ACE_PASS_MIN_CTAS(PASS)) cache_decode_ker
 // Each request's bytes from the cache slots to its place in the output pool.
 __global__ void cache_copy_kernel(CacheArgs c, uint8_t* pool) {
   if (*(volatile uint32_t*)&c.h->status) return;  // a failed batch copies nothing
+  const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const uint64_t B = (uint64_t)1 << c.log2B;
   for (uint32_t r = blockIdx.x; r < c.n_reqs; r += gridDim.x) {
     const ace_seek_req q = c.reqs[r];
     const CacheArc& ca = c.arcs[q.archive];
-    uint8_t* dst = pool + q.out_off;
-    for (uint64_t i = threadIdx.x; i < q.len; i += blockDim.x) {
-      uint64_t p = q.coord + i;
-      uint32_t slot = __ldg(ca.slot_of + (p >> c.log2B));
-      dst[i] = __ldcg(c.slots + ((uint64_t)slot << c.log2B) + (p & (B - 1)));
+    if (q.len == 0) continue;
+    // a warp per block the request covers: one slot lookup, then a batched copy
+    const uint64_t k0 = q.coord >> c.log2B, k1 = (q.coord + q.len - 1) >> c.log2B;
+    for (uint64_t k = k0 + wid; k <= k1; k += nw) {
+      const uint64_t lo = max(k << c.log2B, q.coord), hi = min((k + 1) << c.log2B, q.coord + q.len);
+      const uint32_t slot = __ldg(ca.slot_of + k);
+      warp_copy(pool + q.out_off + (lo - q.coord), c.slots + ((uint64_t)slot << c.log2B) + (lo & (B - 1)), hi - lo,
+                lane);
     }
   }
 }
@@ -1539,7 +1667,8 @@ struct ace_index {
   ace_tune tune;
   // occupancy of the decode kernels, per (seek?, pass, warps per CTA, window)
   mutable int occ_cache[2][3][9][9];
-  mutable int occ_level[9][9];  // the per-level match kernel
+  mutable int occ_level[9][9];       // the per-level match kernel, whole decodes
+  mutable int occ_level_seek[9][9];  // and seeks
   // whole decodes resolve matches with one launch per level when there are
   // at most kMaxLevelLaunches levels: level L's blocks are
   // order[level_start[L] .. level_start[L + 1])
@@ -1671,14 +1800,14 @@ ace_status occupancy(K kernel, int device, uint32_t warps, size_t smem, int* occ
 // occ_cache: 3 x 9 x 9 ints (pass, warps per CTA, window / 32), 0 = unknown
 template <class K0, class K1, class K2>
 ace_status plan_launch(const ace_index* idx, const ace_tune* tune, uint32_t log2B, uint64_t max_items,
-                       uint64_t max_warps, K0 k0, K1 k1, K2 k2, int* occ_cache, Launch* L) {
+                       uint64_t max_warps, K0 k0, K1 k1, K2 k2, int* occ_cache, Launch* L, uint32_t lit_ring = kRing) {
   ace_tune t = tune ? *tune : idx->tune;
   L->warps = t.warps_per_cta ? t.warps_per_cta : 4;
   L->chunk = t.chunk_tokens ? t.chunk_tokens : 128;
   if (L->warps > kMaxWarpsPerCta || (L->chunk & 31) || L->chunk > kMaxWindow) return ACE_E_INVAL;
   L->timeout = t.wait_timeout_ns ? t.wait_timeout_ns : kDefaultTimeoutNs;
   L->smem[PASS_TOKENS] = tok_smem_bytes(esc_cap(log2B));
-  L->smem[PASS_LITERALS] = lit_smem_bytes(L->chunk);
+  L->smem[PASS_LITERALS] = lit_smem_bytes(L->chunk, lit_ring);
   L->smem[PASS_MATCH] = kMatchSmem;
   int per[3];
   for (int p = 0; p < 3; p++) {
@@ -1709,7 +1838,7 @@ ace_status plan_index_launch(const ace_index* idx, const ace_tune* tune, uint64_
                              Launch* L) {
   return plan_launch(idx, tune, idx->h.log2_block, max_items, max_warps, decode_kernel<SEEK, PASS_TOKENS>,
                      decode_kernel<SEEK, PASS_LITERALS>, decode_kernel<SEEK, PASS_MATCH>,
-                     &idx->occ_cache[SEEK][0][0][0], L);
+                     &idx->occ_cache[SEEK][0][0][0], L, SEEK ? kSeekRing : kRing);
 }
 
 // Launches the passes in the mask (bit p: pass p) in order on s, each with
@@ -1735,6 +1864,33 @@ template <bool SEEK>
 void launch_three_pass(const Launch& L, const DecodeArgs& a, cudaStream_t s) {
   launch_passes(L, 7, decode_kernel<SEEK, PASS_TOKENS>, decode_kernel<SEEK, PASS_LITERALS>,
                 decode_kernel<SEEK, PASS_MATCH>, a, s);
+}
+
+// A seek after its closure kernel: tokens and literals over the work list,
+// then, for an archive with few levels, one match launch per level (the
+// level ranges are read on the device), else one match launch that waits on
+// the source blocks' flags.  max_items bounds the work list.
+ace_status launch_seek(const ace_index* idx, const Launch& L, DecodeArgs a, uint64_t max_items, cudaStream_t s) {
+  if (!idx->by_levels) {
+    launch_three_pass<true>(L, a, s);
+    return ACE_OK;
+  }
+  launch_passes(L, 3, decode_kernel<true, PASS_TOKENS>, decode_kernel<true, PASS_LITERALS>,
+                decode_kernel<true, PASS_MATCH>, a, s);
+  a.warp_smem = L.smem[PASS_MATCH];
+  int& occ = idx->occ_level_seek[L.warps][L.chunk / 32];
+  if (occ == 0) {
+    ace_status rc = occupancy(match_level_kernel<true>, idx->device, L.warps, (size_t)L.warps * L.smem[PASS_MATCH], &occ);
+    if (rc) return rc;
+  }
+  if (occ < 0) return ACE_E_INVAL;
+  const uint32_t grid =
+      (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>((uint64_t)idx->num_sms * occ, (max_items + L.warps - 1) / L.warps));
+  for (uint32_t l = 0; l < idx->n_levels; l++) {
+    a.cur_level = l;
+    match_level_kernel<true><<<grid, 32 * L.warps, (size_t)L.warps * L.smem[PASS_MATCH], s>>>(a);
+  }
+  return ACE_OK;
 }
 
 }  // namespace
@@ -1944,7 +2100,7 @@ ace_status decode_all_passes(const ace_index* idx, uint32_t passes, void* d_out,
     a.warp_smem = L.smem[PASS_MATCH];
     int& occ = idx->occ_level[L.warps][L.chunk / 32];
     if (occ == 0) {
-      rc = occupancy(match_level_kernel, idx->device, L.warps, (size_t)L.warps * L.smem[PASS_MATCH], &occ);
+      rc = occupancy(match_level_kernel<false>, idx->device, L.warps, (size_t)L.warps * L.smem[PASS_MATCH], &occ);
       if (rc) return rc;
     }
     if (occ < 0) return ACE_E_INVAL;
@@ -1959,7 +2115,7 @@ ace_status decode_all_passes(const ace_index* idx, uint32_t passes, void* d_out,
       a.n_items = n;
       a.cur_level = l;
       const uint32_t grid = (uint32_t)std::min<uint64_t>((uint64_t)idx->num_sms * per_sm, (n + L.warps - 1) / L.warps);
-      match_level_kernel<<<grid, 32 * L.warps, (size_t)L.warps * L.smem[PASS_MATCH], s>>>(a);
+      match_level_kernel<false><<<grid, 32 * L.warps, (size_t)L.warps * L.smem[PASS_MATCH], s>>>(a);
     }
   }
   CUDA_TRY(cudaGetLastError());
@@ -2010,6 +2166,9 @@ ace_status ace_seek(const ace_index* idx, uint64_t coord, uint64_t len, void* d_
   c.first = first;
   c.last = last;
   c.cap = cap;
+  c.level = idx->by_levels ? idx->d_level : nullptr;
+  c.n_levels = idx->n_levels;
+  c.ready = idx->by_levels ? reinterpret_cast<uint32_t*>(base + S1.ready) : nullptr;
   Launch L;
   ace_status rc = plan_index_launch<true>(idx, nullptr, cap, S1.n_warps, &L);
   if (rc) return rc;
@@ -2039,7 +2198,9 @@ ace_status ace_seek(const ace_index* idx, uint64_t coord, uint64_t len, void* d_
   a.warp_scratch_bytes = warp_scratch_bytes(idx->max_ntok);
   a.recs = reinterpret_cast<MatchRec*>(base + S1.tail + (cap << log2B));
   a.match_ptr = nullptr;
-  launch_three_pass<true>(L, a, s);
+  a.level = idx->d_level;
+  rc = launch_seek(idx, L, a, cap, s);
+  if (rc) return rc;
   CUDA_TRY(cudaGetLastError());
   return ACE_OK;
 }
@@ -2590,6 +2751,9 @@ ace_status ace_seek_noalloc(const ace_index* idx, uint64_t coord, uint64_t len, 
   c.first = first;
   c.last = last;
   c.cap = cap;
+  c.level = idx->by_levels ? idx->d_level : nullptr;
+  c.n_levels = idx->n_levels;
+  c.ready = idx->by_levels ? reinterpret_cast<uint32_t*>(base + S.ready) : nullptr;
   Launch L;
   rc = plan_index_launch<true>(idx, nullptr, cap, S.n_warps, &L);
   if (rc) return rc;
@@ -2619,7 +2783,9 @@ ace_status ace_seek_noalloc(const ace_index* idx, uint64_t coord, uint64_t len, 
   a.warp_scratch_bytes = warp_scratch_bytes(idx->max_ntok);
   a.recs = reinterpret_cast<MatchRec*>(base + S.tail + (cap << log2B));
   a.match_ptr = nullptr;
-  launch_three_pass<true>(L, a, s);
+  a.level = idx->d_level;
+  rc = launch_seek(idx, L, a, cap, s);
+  if (rc) return rc;
   CUDA_TRY(cudaGetLastError());
   // the status lives in the shared array, so the call waits for it
   uint32_t status = 0;

@@ -25,7 +25,8 @@ struct ScratchHdr {
   uint64_t guard_bad;  // verify: guard bytes that differ from the canary
   uint32_t ticket2;    // next work item of the literal pass
   uint32_t ticket3;    // next work item of the match pass
-  uint32_t pad[50];
+  uint32_t lv_start[33];  // seek by levels: the work list's level l is [lv_start[l], lv_start[l + 1])
+  uint32_t pad[17];
 };
 static_assert(sizeof(ScratchHdr) == 256, "scratch header");
 
@@ -185,11 +186,15 @@ struct Stream {
   uint32_t x;          // this lane's state
 };
 
-// Copies renormalisation bytes [off, off + 128) into their ring segment; the
-// copyable extent is nbytes rounded up to 16, which stays inside the archive.
+// Copies renormalisation bytes [off, off + 128) into their segment of a
+// RING-byte ring; the copyable extent is nbytes rounded up to 16, which stays
+// inside the archive.  A ring of RING / 128 segments keeps all but the two
+// newest landed (the refill waits for the rest).
+template <uint32_t RING = kRing>
 __device__ __forceinline__ void ring_issue(const Stream& st, uint8_t* ring, uint32_t off, uint32_t lane) {
+  static_assert(RING % kSeg == 0 && (RING & (RING - 1)) == 0 && RING / kSeg >= 4, "ring of segments");
   uint32_t o = off + 16 * lane;
-  if (lane < kSeg / 16 && o < ((st.nbytes + 15) & ~15u)) cp_async16(ring + (o & (kRing - 1)), st.g + o);
+  if (lane < kSeg / 16 && o < ((st.nbytes + 15) & ~15u)) cp_async16(ring + (o & (RING - 1)), st.g + o);
   cp_async_commit();
 }
 
@@ -197,6 +202,7 @@ __device__ __forceinline__ void ring_issue(const Stream& st, uint8_t* ring, uint
 // point) and locates the renormalisation bytes; issues the first ring fill.
 // The stream bounds were validated when the index was built.  Returns false
 // (all lanes) for a state outside [L, 2^31) or a table overrunning the stream.
+template <uint32_t RING = kRing>
 __device__ __forceinline__ bool stream_open(const uint8_t* pay, uint32_t sbytes, uint32_t nsym, uint8_t* ring,
                                             Stream& st, uint32_t lane) {
   st.nsym = nsym;
@@ -218,7 +224,7 @@ __device__ __forceinline__ bool stream_open(const uint8_t* pay, uint32_t sbytes,
   st.g = pay + head;
   st.head = head;
   st.nbytes = sbytes - head;
-  for (uint32_t s = 0; s < kRing / kSeg; s++) ring_issue(st, ring, s * kSeg, lane);
+  for (uint32_t s = 0; s < RING / kSeg; s++) ring_issue<RING>(st, ring, s * kSeg, lane);
   // the frequency table (bytes 160 .. head) is read when the stream's tables
   // are built: bring its lines into L1 now
   if (lane < 5 && 128 + 128 * lane < head) {
@@ -349,12 +355,13 @@ __device__ __forceinline__ void lookup(const Stream& st, const Lut& lut, uint32_
 // harmless; the end-of-stream check (all bytes consumed, every state at L)
 // rejects a stream that needed them.  Sets act and i for this lane and
 // returns the symbol.
+template <uint32_t RING = kRing>
 __device__ __forceinline__ uint32_t rans_round(Stream& st, uint8_t* ring, const Lut& lut, uint32_t end,
                                                uint32_t lane, uint32_t lt, bool& act, uint32_t& i) {
   if (st.pos >= st.base + kSeg) {  // oldest segment consumed: refill it further on
-    ring_issue(st, ring, st.base + kRing, lane);
+    ring_issue<RING>(st, ring, st.base + RING, lane);
     st.base += kSeg;
-    cp_async_wait<2>();
+    cp_async_wait<RING / kSeg - 2>();
     __syncwarp();
   }
   uint32_t base = st.next & ~31u;
@@ -368,7 +375,7 @@ __device__ __forceinline__ uint32_t rans_round(Stream& st, uint8_t* ring, const 
   bool p1 = act && xn < ACE_RANS_L, p2 = act && xn < (1u << 15);
   uint32_t b1 = __ballot_sync(kFull, p1), b2 = __ballot_sync(kFull, p2);
   uint32_t p = st.pos + __popc(b1 & lt) + __popc(b2 & lt);
-  uint32_t c0 = ring[p & (kRing - 1)], c1 = ring[(p + 1) & (kRing - 1)];
+  uint32_t c0 = ring[p & (RING - 1)], c1 = ring[(p + 1) & (RING - 1)];
   uint32_t x1 = (xn << 8) | c0, x2 = (x1 << 8) | c1;
   xn = p2 ? x2 : (p1 ? x1 : xn);
   st.x = act ? xn : x;
@@ -379,11 +386,12 @@ __device__ __forceinline__ uint32_t rans_round(Stream& st, uint8_t* ring, const 
 
 // A full round: st.next is a multiple of 32 and at least 32 symbols remain,
 // so every lane is active.
+template <uint32_t RING = kRing>
 __device__ __forceinline__ uint32_t rans_round_full(Stream& st, uint8_t* ring, const Lut& lut, uint32_t lt) {
   if (st.pos >= st.base + kSeg) {
-    ring_issue(st, ring, st.base + kRing, threadIdx.x & 31);
+    ring_issue<RING>(st, ring, st.base + RING, threadIdx.x & 31);
     st.base += kSeg;
-    cp_async_wait<2>();
+    cp_async_wait<RING / kSeg - 2>();
     __syncwarp();
   }
   uint32_t x = st.x;
@@ -394,7 +402,7 @@ __device__ __forceinline__ uint32_t rans_round_full(Stream& st, uint8_t* ring, c
   bool p1 = xn < ACE_RANS_L, p2 = xn < (1u << 15);
   uint32_t b1 = __ballot_sync(kFull, p1), b2 = __ballot_sync(kFull, p2);
   uint32_t p = st.pos + __popc(b1 & lt) + __popc(b2 & lt);
-  uint32_t c0 = ring[p & (kRing - 1)], c1 = ring[(p + 1) & (kRing - 1)];
+  uint32_t c0 = ring[p & (RING - 1)], c1 = ring[(p + 1) & (RING - 1)];
   uint32_t x1 = (xn << 8) | c0, x2 = (x1 << 8) | c1;
   st.x = p2 ? x2 : (p1 ? x1 : xn);
   st.pos += __popc(b1) + __popc(b2);
@@ -405,24 +413,24 @@ __device__ __forceinline__ uint32_t rans_round_full(Stream& st, uint8_t* ring, c
 // Decodes symbols [st.next, end), handing each to sink(act, i, s) per
 // round (act false on lanes without a symbol this round): a partial first
 // round up to the next multiple of 32, full rounds, then a partial last one.
-template <class Sink>
+template <uint32_t RING = kRing, class Sink>
 __device__ __forceinline__ void rans_run(Stream& st, uint8_t* ring, const Lut& lut, uint32_t end, uint32_t lane,
                                          uint32_t lt, Sink&& sink) {
   if (st.next < end && ((st.next & 31) || end - st.next < 32)) {
     bool act;
     uint32_t i;
-    uint32_t s = rans_round(st, ring, lut, end, lane, lt, act, i);
+    uint32_t s = rans_round<RING>(st, ring, lut, end, lane, lt, act, i);
     sink(act, i, s);
   }
   while (end - st.next >= 32 && st.next < end) {
     uint32_t i = st.next + lane;
-    uint32_t s = rans_round_full(st, ring, lut, lt);
+    uint32_t s = rans_round_full<RING>(st, ring, lut, lt);
     sink(true, i, s);
   }
   if (st.next < end) {
     bool act;
     uint32_t i;
-    uint32_t s = rans_round(st, ring, lut, end, lane, lt, act, i);
+    uint32_t s = rans_round<RING>(st, ring, lut, end, lane, lt, act, i);
     sink(act, i, s);
   }
 }
@@ -430,6 +438,7 @@ __device__ __forceinline__ void rans_run(Stream& st, uint8_t* ring, const Lut& l
 // One full round in slot-table mode (st.k == 0): every lane decodes one
 // symbol of state x, with renormalisation bytes read from the ring at the
 // running position pos as in rans_round.  The caller checks the ring.
+template <uint32_t RING = kRing>
 __device__ __forceinline__ uint32_t table_round(uint32_t& x, uint32_t& pos, const uint8_t* ring, const Lut& lut,
                                                 uint32_t lt) {
   const uint32_t slot = x & (ACE_SCALE - 1);
@@ -439,7 +448,7 @@ __device__ __forceinline__ uint32_t table_round(uint32_t& x, uint32_t& pos, cons
   const bool p1 = xn < ACE_RANS_L, p2 = xn < (1u << 15);
   const uint32_t b1 = __ballot_sync(kFull, p1), b2 = __ballot_sync(kFull, p2);
   const uint32_t p = pos + __popc(b1 & lt) + __popc(b2 & lt);
-  const uint32_t c0 = ring[p & (kRing - 1)], c1 = ring[(p + 1) & (kRing - 1)];
+  const uint32_t c0 = ring[p & (RING - 1)], c1 = ring[(p + 1) & (RING - 1)];
   const uint32_t x1 = (xn << 8) | c0, x2 = (x1 << 8) | c1;
   x = p2 ? x2 : (p1 ? x1 : xn);
   pos += __popc(b1) + __popc(b2);
@@ -451,27 +460,27 @@ __device__ __forceinline__ uint32_t table_round(uint32_t& x, uint32_t& pos, cons
 // is checked once per two rounds: a round reads at most 64 bytes, and after a
 // check the position is less than one segment into the ring, whose two oldest
 // segments have landed.
-template <class Emit>
+template <uint32_t RING = kRing, class Emit>
 __device__ __forceinline__ void table_full_rounds(Stream& st, uint8_t* ring, const Lut& lut, uint32_t nfull,
                                                   uint32_t lane, uint32_t lt, Emit&& emit) {
   uint32_t x = st.x, pos = st.pos, base = st.base;
   auto check = [&]() {
     if (pos >= base + kSeg) {
-      ring_issue(st, ring, base + kRing, lane);
+      ring_issue<RING>(st, ring, base + RING, lane);
       base += kSeg;
-      cp_async_wait<2>();
+      cp_async_wait<RING / kSeg - 2>();
       __syncwarp();
     }
   };
   uint32_t r = 0;
   for (; r + 2 <= nfull; r += 2) {
     check();
-    emit(table_round(x, pos, ring, lut, lt));
-    emit(table_round(x, pos, ring, lut, lt));
+    emit(table_round<RING>(x, pos, ring, lut, lt));
+    emit(table_round<RING>(x, pos, ring, lut, lt));
   }
   if (r < nfull) {
     check();
-    emit(table_round(x, pos, ring, lut, lt));
+    emit(table_round<RING>(x, pos, ring, lut, lt));
   }
   st.x = x;
   st.pos = pos;
