@@ -40,6 +40,7 @@ struct IndexArgs {
   uint32_t* lv_count;  // n_blocks + 1 entries
   uint32_t* lv_cursor; // n_blocks + 1 entries
   uint64_t nb, total, payload_off, arc_bytes, deps_off;
+  uint64_t max_iv;  // intervals that fit between the pointer table and the payload
   uint32_t log2B, w;
 };
 
@@ -47,6 +48,12 @@ struct IndexArgs {
 // stream bounds and token counts (Section 2 block layout, Section 3 streams).
 __global__ void validate_kernel(IndexArgs a) {
   uint64_t b = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  if (b == 0) {  // the interval table must end before the payload
+    const uint32_t niv = a.dep_ptr[a.nb];
+    a.ih->n_iv = niv;
+    if (a.deps_off + 4 * (a.nb + 1) + 8ull * niv > a.payload_off)
+      record_error(&a.ih->status, &a.ih->err_block, &a.ih->err_where, ACE_E_CORRUPT, 0, 12);
+  }
   if (b >= a.nb) return;
   const ace_block_dir d = a.dir[b];
   uint64_t B = (uint64_t)1 << a.log2B, bstart = b << a.log2B;
@@ -71,7 +78,7 @@ __global__ void validate_kernel(IndexArgs a) {
   }
   if (!where) {
     uint32_t lo = a.dep_ptr[b], hi = a.dep_ptr[b + 1], niv = a.dep_ptr[a.nb];
-    if (lo > hi || hi > niv) where = 10;
+    if (lo > hi || hi > niv || hi > a.max_iv) where = 10;  // intervals read below stay before the payload
     else
       for (uint32_t i = lo; i < hi && !where; i++) {
         uint32_t f = a.dep_iv[2 * i], l = a.dep_iv[2 * i + 1];
@@ -123,9 +130,38 @@ __global__ void match_scan_kernel(IndexArgs a) {
 // Dependency levels: level[b] = 0 without sources in other blocks, else
 // 1 + the deepest block it reads (Section 2).  Sources always precede, so
 // one CTA walks the blocks in chunks and relaxes each chunk to its fixed point.
+// One sweep of the dependency levels (Section 2: a block decodes once the
+// blocks it reads are present), a warp per block with its lanes over the
+// block's dependency intervals: level[b] <- max(level[b], 1 + the largest
+// level of a block it reads).  Levels only grow toward each block's depth in
+// the dependency graph, and reach it after as many sweeps as there are
+// levels; a sweep that changes a level sets its flag.
+constexpr uint32_t kLevelSweeps = 8;
+
+__global__ void levels_sweep_kernel(IndexArgs a, uint32_t sweep) {
+  if (*(volatile uint32_t*)&a.ih->status) return;
+  if (sweep > 0 && !*(volatile uint32_t*)&a.ih->relax[sweep - 1]) return;  // settled already
+  const uint32_t lane = threadIdx.x & 31;
+  const uint64_t nw = (uint64_t)gridDim.x * (blockDim.x >> 5);
+  for (uint64_t b = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5; b < a.nb; b += nw) {
+    uint32_t lv = 0;
+    const uint32_t e1 = a.dep_ptr[b + 1];
+    for (uint32_t e = a.dep_ptr[b] + lane; e < e1; e += 32)
+      for (uint32_t k = a.dep_iv[2 * e]; k <= a.dep_iv[2 * e + 1]; k++) lv = max(lv, a.level[k] + 1);
+#pragma unroll
+    for (int d = 16; d; d >>= 1) lv = max(lv, __shfl_xor_sync(kFull, lv, d));
+    if (lane == 0 && lv > a.level[b]) {
+      a.level[b] = lv;
+      a.ih->relax[sweep] = 1;
+    }
+  }
+}
+
+// The levels in one CTA, block chunk by block chunk, for archives whose
+// levels did not settle within the sweeps (deep dependency chains).
 __global__ void levels_kernel(IndexArgs a) {
   __shared__ int changed;
-  uint32_t maxlv = 0;
+  if (*(volatile uint32_t*)&a.ih->status || !*(volatile uint32_t*)&a.ih->relax[kLevelSweeps - 1]) return;
   for (uint64_t c0 = 0; c0 < a.nb; c0 += blockDim.x) {
     uint64_t b = c0 + threadIdx.x;
     if (b < a.nb) a.level[b] = 0;
@@ -146,14 +182,17 @@ __global__ void levels_kernel(IndexArgs a) {
       if (!changed) break;
       __syncthreads();
     }
-    if (b < a.nb) maxlv = max(maxlv, a.level[b]);
   }
-  atomicMax(&a.ih->n_levels, maxlv + 1);
 }
 
 __global__ void level_hist_kernel(IndexArgs a) {
+  if (*(volatile uint32_t*)&a.ih->status) return;
   uint64_t b = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
-  if (b < a.nb) atomicAdd(&a.lv_count[a.level[b]], 1u);
+  if (b < a.nb) {
+    const uint32_t lv = a.level[b];
+    atomicAdd(&a.lv_count[lv], 1u);
+    atomicMax(&a.ih->n_levels, lv + 1);
+  }
 }
 
 // Exclusive scan of the level histogram into level start offsets (one CTA).
@@ -177,6 +216,7 @@ __global__ void level_scan_kernel(IndexArgs a) {
     __syncthreads();
     uint32_t ex = carry + wsum[wid] + incl - v;
     if (i < a.nb + 1) a.lv_cursor[i] = ex;
+    if (i < 33) a.ih->lvc[i] = v;  // the host reads the first levels' sizes with the header
     __syncthreads();
     if (threadIdx.x == blockDim.x - 1) carry = ex + v;
     __syncthreads();
@@ -184,6 +224,7 @@ __global__ void level_scan_kernel(IndexArgs a) {
 }
 
 __global__ void level_scatter_kernel(IndexArgs a) {
+  if (*(volatile uint32_t*)&a.ih->status) return;
   uint64_t b = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
   if (b < a.nb) a.order[atomicAdd(&a.lv_cursor[a.level[b]], 1u)] = (uint32_t)b;
 }
@@ -1949,12 +1990,7 @@ ace_status ace_index_build(const void* d_archive, uint64_t archive_bytes, const 
   if (cudaGetDevice(&idx->device) != cudaSuccess) return bail(ACE_E_CUDA);
   if (cudaDeviceGetAttribute(&idx->num_sms, cudaDevAttrMultiProcessorCount, idx->device) != cudaSuccess)
     return bail(ACE_E_CUDA);
-  uint32_t niv = 0;
-  if (cudaMemcpyAsync(&niv, idx->d_arc + h.deps_off + 4 * h.n_blocks, 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-      cudaStreamSynchronize(s) != cudaSuccess)
-    return bail(ACE_E_CUDA);
-  idx->n_iv = niv;
-  if (h.deps_off + 4 * (h.n_blocks + 1) + 8ull * niv > h.payload_off) return bail(ACE_E_CORRUPT);
+  // the interval table's bounds are checked on the device with the rest
   idx->d_dep_iv = reinterpret_cast<const uint32_t*>(idx->d_arc + h.deps_off + 4 * (h.n_blocks + 1));
   if (cudaMemsetAsync(idx->d_mem, 0, L.total, s) != cudaSuccess) return bail(ACE_E_CUDA);
   IndexArgs a;
@@ -1974,36 +2010,34 @@ ace_status ace_index_build(const void* d_archive, uint64_t archive_bytes, const 
   a.payload_off = h.payload_off;
   a.arc_bytes = h.archive_bytes;
   a.deps_off = h.deps_off;
+  a.max_iv = (h.payload_off - h.deps_off - 4 * (h.n_blocks + 1)) / 8;
   a.log2B = h.log2_block;
   a.w = h.off_width;
   if (h.n_blocks) {
+    // every step on the device, each skipping once the header holds an
+    // error; the host reads the header once at the end
     uint32_t g = (uint32_t)((h.n_blocks + 255) / 256);
     validate_kernel<<<g, 256, 0, s>>>(a);
+    match_scan_kernel<<<1, 1024, 0, s>>>(a);
+    const uint32_t gs = (uint32_t)std::min<uint64_t>((h.n_blocks + 7) / 8, (uint64_t)idx->num_sms * 8);
+    for (uint32_t k = 0; k < kLevelSweeps; k++) levels_sweep_kernel<<<gs, 256, 0, s>>>(a, k);
+    levels_kernel<<<1, 1024, 0, s>>>(a);
+    level_hist_kernel<<<g, 256, 0, s>>>(a);
+    level_scan_kernel<<<1, 1024, 0, s>>>(a);
+    level_scatter_kernel<<<g, 256, 0, s>>>(a);
     IndexHdr ih;
     if (cudaMemcpyAsync(&ih, idx->d_ih, sizeof ih, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess)
       return bail(ACE_E_CUDA);
     if (ih.status) return bail((ace_status)ih.status);
+    idx->n_iv = ih.n_iv;
     idx->max_ntok = ih.max_ntok;
-    match_scan_kernel<<<1, 1024, 0, s>>>(a);
-    levels_kernel<<<1, 1024, 0, s>>>(a);
-    level_hist_kernel<<<g, 256, 0, s>>>(a);
-    level_scan_kernel<<<1, 1024, 0, s>>>(a);
-    level_scatter_kernel<<<g, 256, 0, s>>>(a);
-    if (cudaMemcpyAsync(&ih, idx->d_ih, sizeof ih, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-        cudaStreamSynchronize(s) != cudaSuccess)
-      return bail(ACE_E_CUDA);
-    if (ih.status) return bail((ace_status)ih.status);
     idx->n_levels = ih.n_levels;
     idx->n_matches = ih.n_matches;
     idx->by_levels = ih.n_levels <= kMaxLevelLaunches;
     if (idx->by_levels) {
-      uint32_t cnt[kMaxLevelLaunches];
-      if (cudaMemcpyAsync(cnt, a.lv_count, 4ull * ih.n_levels, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-          cudaStreamSynchronize(s) != cudaSuccess)
-        return bail(ACE_E_CUDA);
       idx->level_start[0] = 0;
-      for (uint32_t l = 0; l < ih.n_levels; l++) idx->level_start[l + 1] = idx->level_start[l] + cnt[l];
+      for (uint32_t l = 0; l < ih.n_levels; l++) idx->level_start[l + 1] = idx->level_start[l] + ih.lvc[l];
       if (idx->level_start[ih.n_levels] != h.n_blocks) return bail(ACE_E_CORRUPT);
     }
   }

@@ -39,7 +39,10 @@ struct IndexHdr {
   uint32_t max_ntok;   // most tokens in any block: sizes the per-warp token records
   uint32_t pad0;
   uint64_t n_matches;  // matches in the archive: sizes a whole decode's match records
-  uint32_t pad[56];
+  uint32_t relax[8];   // level sweep k changed a level
+  uint32_t n_iv;       // dependency intervals in the archive
+  uint32_t lvc[33];    // blocks per level, for the first 33 levels
+  uint32_t pad[14];
 };
 static_assert(sizeof(IndexHdr) == 256, "index header");
 
