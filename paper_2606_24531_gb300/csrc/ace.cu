@@ -286,7 +286,7 @@ struct TokRec {
   uint8_t* offb;   // [5 max_ntok]
 };
 
-constexpr uint32_t kMatchGroup = 128;  // matches whose records sit in shared memory at a time
+constexpr uint32_t kMatchGroup = 64;  // matches whose records sit in shared memory at a time
 
 __host__ __device__ inline uint32_t tok_smem_bytes(uint32_t escn) {
   return (sizeof(Lut) + 2 * kRing + 2 * escn + 15) & ~15u;
@@ -820,7 +820,7 @@ __device__ __forceinline__ uint32_t upper_bound(uint32_t n, uint32_t x, Key key)
 }
 
 // Match pass of one block (Section 2: a block decodes once the blocks holding
-// its sources are present).  Groups of up to 128 matches: their records are
+// its sources are present).  Groups of up to 64 matches: their records are
 // loaded together; with WAIT the source blocks before this one are checked
 // with overlapping relaxed loads (a bounded wait only for one not yet
 // published); without it (one launch per dependency level) each source
@@ -1037,7 +1037,7 @@ __device__ bool match_block(const DecodeArgs& a, MatchRec* gm, uint32_t b, uint3
 enum { PASS_TOKENS = 0, PASS_LITERALS = 1, PASS_MATCH = 2 };
 
 // Registers per thread allowed by each pass's launch bounds (256 threads).
-#define ACE_PASS_MIN_CTAS(P) ((P) == PASS_TOKENS ? 3 : (P) == PASS_LITERALS ? 4 : 2)
+#define ACE_PASS_MIN_CTAS(P) ((P) == PASS_TOKENS ? 4 : (P) == PASS_LITERALS ? 4 : 2)
 
 // The match pass keeps only its match-record area in shared memory.
 constexpr uint32_t kMatchSmem = 20 * kMatchGroup + 16;
