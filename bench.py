@@ -315,14 +315,15 @@ def main():
         sc.reset()
         blat, bt0 = [], time.perf_counter()
         for s0 in range(0, len(blocks), 256):
-            chunk = [(0, int(b) * B, B) for b in blocks[s0:s0 + 256]]
+            bb = np.asarray(blocks[s0:s0 + 256], np.uint64)
             t0 = time.perf_counter()
-            outs = sc.seek_many(chunk)
+            r = sc.plan_arrays(np.zeros(len(bb), np.uint32), bb * np.uint64(B), np.full(len(bb), B, np.uint64))
+            sc.run_batch(r)
             t1 = time.perf_counter()
-            blat += [t1 - t0] * len(chunk)
+            blat += [t1 - t0] * len(bb)
             if s0 % 2560 == 0:
-                b = int(blocks[s0])
-                assert torch.equal(outs[0], d_data[b * B:(b + 1) * B])
+                b, o = int(bb[0]), int(r[0]["out_off"])
+                assert torch.equal(sc.pool[o:o + B], d_data[b * B:(b + 1) * B])
         bwall = time.perf_counter() - bt0
         blat_us = np.array(blat) * 1e6
         sc.close()

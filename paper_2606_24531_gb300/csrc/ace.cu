@@ -1429,7 +1429,8 @@ struct CacheArgs {
 
 __device__ __forceinline__ bool cache_mark(const CacheArgs& c, uint32_t a, uint32_t b, uint32_t epoch) {
   const CacheArc& ca = c.arcs[a];
-  if (ld_acquire(ca.ready + b) == epoch) return false;  // already cached
+  // flags are set by earlier launches on this stream, ordered before this one
+  if (ld_relaxed(ca.ready + b) == epoch) return false;  // already cached
   uint32_t bit = 1u << (b & 31);
   return !(atomicOr(ca.marks + (b >> 5), bit) & bit);
 }
@@ -1477,10 +1478,11 @@ __global__ void cache_closure_kernel(CacheArgs c) {
   while (n_front && !overflow) {
     if (tid == 0) n_next = 0;
     __syncthreads();
-    for (uint32_t i = tid; i < n_front; i += blockDim.x) {
+    for (uint32_t i = wid; i < n_front; i += nw) {  // a warp per frontier block, lanes over its intervals
       uint32_t a = cur[2 * i], b = cur[2 * i + 1];
       const CacheArc& ca = c.arcs[a];
-      for (uint32_t e = ca.dep_ptr[b]; e < ca.dep_ptr[b + 1]; e++)
+      const uint32_t e1 = ca.dep_ptr[b + 1];
+      for (uint32_t e = ca.dep_ptr[b] + lane; e < e1; e += 32)
         for (uint32_t k = ca.dep_iv[2 * e]; k <= ca.dep_iv[2 * e + 1]; k++)
           if (cache_mark(c, a, k, epoch)) {
             uint32_t j = atomicAdd(&n_next, 1u);
@@ -1605,7 +1607,7 @@ __global__ void __launch_bounds__(256, ACE_PASS_MIN_CTAS(PASS)) cache_decode_ker
                              ca.max_ntok);
       token_block<true>(a, carve_tok(wsm), g, b, lane);
     } else if (PASS == PASS_LITERALS) {
-      literal_block<true, kRing>(a, carve_lit(wsm, ca.window, kRing), b, lane);
+      literal_block<true, kSeekRing>(a, carve_lit(wsm, ca.window, kSeekRing), b, lane);
     } else {
       const uint32_t ntok = __ldg(reinterpret_cast<const uint32_t*>(a.dir + b) + 12);
       match_block<true, true>(a, reinterpret_cast<MatchRec*>(wsm), b, lane, epoch, ntok ? ntok - 1 : 0);
@@ -2599,7 +2601,8 @@ ace_status ace_cache_create(const ace_index* const* idx, uint32_t n, void* const
   c->bytes = bytes;
   c->req_off = C.reqs;
   rc = plan_launch(idx[0], tune, log2B, n_slots, C.n_warps, cache_decode_kernel<PASS_TOKENS>,
-                   cache_decode_kernel<PASS_LITERALS>, cache_decode_kernel<PASS_MATCH>, &c->occ[0][0][0], &c->L);
+                   cache_decode_kernel<PASS_LITERALS>, cache_decode_kernel<PASS_MATCH>, &c->occ[0][0][0], &c->L,
+                   kSeekRing);
   // header (epoch 1: no block is cached, since every ready flag starts at 0)
   CacheHdr h{};
   h.epoch = 1;

@@ -43,12 +43,22 @@ class SeekCache:
     def plan(self, reqs):
         """Request array for [(archive, coord, len)], results packed 16-byte
         aligned in the pool; None if they do not fit one batch."""
-        r = np.zeros(len(reqs), ace.SEEK_REQ)
-        off = 0
-        for k, (a, c, n) in enumerate(reqs):
-            r[k] = (a, 0, c, n, off)
-            off += (n + 15) & ~15
-        if off > self.pool_bytes or len(reqs) > self.max_reqs:
+        if not len(reqs):
+            return np.zeros(0, ace.SEEK_REQ)
+        a, c, n = (np.asarray(x, np.uint64) for x in zip(*reqs))
+        return self.plan_arrays(a, c, n)
+
+    def plan_arrays(self, archive, coord, length):
+        """plan() for parallel arrays of archive ids, coordinates and lengths."""
+        n = len(coord)
+        r = np.zeros(n, ace.SEEK_REQ)
+        r["archive"] = archive
+        r["coord"] = coord
+        r["len"] = length
+        aligned = (np.asarray(length, np.uint64) + np.uint64(15)) & ~np.uint64(15)
+        ends = np.cumsum(aligned, dtype=np.uint64)
+        r["out_off"][1:] = ends[:-1]
+        if (n and int(ends[-1]) > self.pool_bytes) or n > self.max_reqs:
             return None
         return r
 
@@ -69,19 +79,25 @@ class SeekCache:
     def reset(self):
         ace.ace_cache_reset(self.cache, self.stream)
 
-    def seek_many(self, reqs):
-        """Blocking convenience: results of [(archive, coord, len)] as pool views."""
-        r = self.plan(reqs)
-        assert r is not None, "batch larger than the pool"
+    def run_batch(self, r):
+        """Blocking: runs the planned batch r (resetting the cache once if it
+        ran out of slots); the results are in the pool at r["out_off"]."""
         for attempt in range(2):
             self.submit(r)
             st = self.sync()
             if st == ace.ACE_OK:
-                return [self.pool[int(q["out_off"]): int(q["out_off"]) + int(q["len"])] for q in r]
+                return r
             if st != ace.ACE_E_NOMEM or attempt:
                 raise ace.AceError(st, "seek batch")
             self.reset()
         raise AssertionError("unreachable")
+
+    def seek_many(self, reqs):
+        """Blocking convenience: results of [(archive, coord, len)] as pool views."""
+        r = self.plan(reqs)
+        assert r is not None, "batch larger than the pool"
+        self.run_batch(r)
+        return [self.pool[int(q["out_off"]): int(q["out_off"]) + int(q["len"])] for q in r]
 
     def close(self):
         if self.cache is not None:
