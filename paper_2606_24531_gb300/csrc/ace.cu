@@ -21,6 +21,11 @@ namespace {
 
 constexpr uint64_t kDefaultTimeoutNs = 2000000000ull;
 constexpr uint32_t kMaxLevelLaunches = 32;  // whole decodes with more levels wait on flags instead
+// A seek's closure marks its blocks' ready flags with the call's epoch and
+// this bit; publishing a decoded block clears it.  A source block whose flag
+// shows neither is outside the closure: the archive is corrupt.  (Epochs
+// count calls on one scratch buffer and stay below 2^31.)
+constexpr uint32_t kPendingFlag = 0x80000000u;
 
 inline uint64_t align256(uint64_t v) { return (v + 255) & ~255ull; }
 
@@ -257,6 +262,7 @@ struct DecodeArgs {
   const uint64_t* match_ptr;  // whole decode: block -> first record; null: max_ntok records per slot
   const uint32_t* level;   // whole decode by levels: each block's dependency level
   uint32_t cur_level;      // whole decode by levels: the level this launch resolves
+  bool closure_flags;      // seek: the closure marked its blocks' ready flags (kPendingFlag)
 };
 
 // Shared memory of one warp in the token pass: one stream's tables at a
@@ -890,7 +896,7 @@ __device__ bool match_block(const DecodeArgs& a, MatchRec* gm, uint32_t b, uint3
         f0[q] = ld_relaxed(flags + k0);
         f1[q] = k1 != k0 ? ld_relaxed(flags + k1) : f0[q];
         if (SEEK && !WAIT) {  // a seek's source blocks must be in its closure
-          const uint32_t r0 = ld_relaxed(a.ready + k0), r1 = ld_relaxed(a.ready + k1);
+          const uint32_t r0 = ld_relaxed(a.ready + k0) & ~kPendingFlag, r1 = ld_relaxed(a.ready + k1) & ~kPendingFlag;
           if (r0 != epoch) f0[q] |= 0x80000000u;
           if (r1 != epoch) f1[q] |= 0x80000000u;
         }
@@ -912,9 +918,14 @@ __device__ bool match_block(const DecodeArgs& a, MatchRec* gm, uint32_t b, uint3
         const uint64_t rend = S + min((uint64_t)gL[j], D - S);
         const uint64_t k0 = S >> a.log2B, k1 = min((rend - 1) >> a.log2B, (uint64_t)b - 1);
         if (f0[q] == epoch && f1[q] == epoch && k1 <= k0 + 1) continue;  // blocks between them: the bounded wait
+      if (SEEK && a.closure_flags && ((f0[q] & ~kPendingFlag) != epoch || (f1[q] & ~kPendingFlag) != epoch)) {
+        bad = true;  // a source block outside the seek's closure
+        continue;
+      }
         for (uint64_t k = k0; k <= k1 && !timeout; k++)
           if (!wait_flag(a.ready + k, epoch, a.timeout_ns, &a.sh->status)) timeout = true;
       }
+      if (__any_sync(kFull, bad)) fail(a, ok, ACE_E_CORRUPT, b, 39, lane);
       if (__any_sync(kFull, timeout)) fail(a, ok, ACE_E_TIMEOUT, b, 38, lane);
       if (!ok) break;
       if (__any_sync(kFull, ext != 0)) fence_acquire();
@@ -1018,7 +1029,7 @@ __device__ bool match_block(const DecodeArgs& a, MatchRec* gm, uint32_t b, uint3
         const uint64_t k0 = S >> a.log2B, k1 = min((rend - 1) >> a.log2B, (uint64_t)b - 1);
         for (uint64_t k = k0 + 1; k < k1; k++) {  // a source spanning more than two earlier blocks
           if (__ldg(a.level + k) >= a.cur_level) bad = true;
-          if (SEEK && ld_relaxed(a.ready + k) != epoch) bad = true;
+          if (SEEK && (ld_relaxed(a.ready + k) & ~kPendingFlag) != epoch) bad = true;
         }
       }
       if (__any_sync(kFull, bad)) fail(a, ok, ACE_E_CORRUPT, b, 39, lane);
@@ -1247,7 +1258,7 @@ struct ClosureArgs {
   uint64_t cap;          // slots available
   const uint32_t* level; // by levels: each block's dependency level (else null)
   uint32_t n_levels;
-  uint32_t* ready;       // by levels: closure blocks get the call's epoch
+  uint32_t* ready;       // closure blocks get the call's epoch with kPendingFlag set
 };
 
 // The blocks a seek must decode: its target blocks and, transitively, every
@@ -1352,7 +1363,7 @@ __global__ void closure_kernel(ClosureArgs a) {
   for (uint32_t i = tid; i < n; i += blockDim.x) {
     const uint32_t b = a.front0[i];
     atomicAdd(&lcnt[a.level ? a.level[b] : 0], 1u);
-    if (a.ready) a.ready[b] = epoch;  // members of this seek's closure
+    if (a.ready) a.ready[b] = epoch | kPendingFlag;  // a member of this seek's closure, not yet decoded
   }
   __syncthreads();
   if (tid == 0) {
@@ -1909,12 +1920,16 @@ void launch_three_pass(const Launch& L, const DecodeArgs& a, cudaStream_t s) {
                 decode_kernel<SEEK, PASS_MATCH>, a, s);
 }
 
+// A plain seek decodes about a hundred blocks at most levels deep: one match
+// launch waiting on flags beats a launch per level there.
+constexpr bool kSeekByLevels = false;
+
 // A seek after its closure kernel: tokens and literals over the work list,
 // then, for an archive with few levels, one match launch per level (the
 // level ranges are read on the device), else one match launch that waits on
 // the source blocks' flags.  max_items bounds the work list.
 ace_status launch_seek(const ace_index* idx, const Launch& L, DecodeArgs a, uint64_t max_items, cudaStream_t s) {
-  if (!idx->by_levels) {
+  if (!idx->by_levels || !kSeekByLevels) {
     launch_three_pass<true>(L, a, s);
     return ACE_OK;
   }
@@ -2204,7 +2219,7 @@ ace_status ace_seek(const ace_index* idx, uint64_t coord, uint64_t len, void* d_
   c.cap = cap;
   c.level = idx->by_levels ? idx->d_level : nullptr;
   c.n_levels = idx->n_levels;
-  c.ready = idx->by_levels ? reinterpret_cast<uint32_t*>(base + S1.ready) : nullptr;
+  c.ready = reinterpret_cast<uint32_t*>(base + S1.ready);
   Launch L;
   ace_status rc = plan_index_launch<true>(idx, nullptr, cap, S1.n_warps, &L);
   if (rc) return rc;
@@ -2235,6 +2250,7 @@ ace_status ace_seek(const ace_index* idx, uint64_t coord, uint64_t len, void* d_
   a.recs = reinterpret_cast<MatchRec*>(base + S1.tail + (cap << log2B));
   a.match_ptr = nullptr;
   a.level = idx->d_level;
+  a.closure_flags = true;
   rc = launch_seek(idx, L, a, cap, s);
   if (rc) return rc;
   CUDA_TRY(cudaGetLastError());
@@ -2790,7 +2806,7 @@ ace_status ace_seek_noalloc(const ace_index* idx, uint64_t coord, uint64_t len, 
   c.cap = cap;
   c.level = idx->by_levels ? idx->d_level : nullptr;
   c.n_levels = idx->n_levels;
-  c.ready = idx->by_levels ? reinterpret_cast<uint32_t*>(base + S.ready) : nullptr;
+  c.ready = reinterpret_cast<uint32_t*>(base + S.ready);
   Launch L;
   rc = plan_index_launch<true>(idx, nullptr, cap, S.n_warps, &L);
   if (rc) return rc;
@@ -2821,6 +2837,7 @@ ace_status ace_seek_noalloc(const ace_index* idx, uint64_t coord, uint64_t len, 
   a.recs = reinterpret_cast<MatchRec*>(base + S.tail + (cap << log2B));
   a.match_ptr = nullptr;
   a.level = idx->d_level;
+  a.closure_flags = true;
   rc = launch_seek(idx, L, a, cap, s);
   if (rc) return rc;
   CUDA_TRY(cudaGetLastError());

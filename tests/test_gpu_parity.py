@@ -1,6 +1,8 @@
 """GPU parity: the sm_103a decoder, called through the C ABI, against the
 oracle and the original bytes.  Decoded output has exactly one correct
 value, so every comparison is bit-exact (tolerance 0 bytes)."""
+import time
+
 import numpy as np
 import pytest
 
@@ -217,10 +219,10 @@ def _with_dep_removed(arc, block):
     return bad
 
 
-def test_wait_gives_up_with_timeout_status():
-    """A seek whose closure misses a source block waits on a flag nothing
-    sets; the bounded wait ends with ACE_E_TIMEOUT and the context stays
-    usable."""
+def test_seek_outside_its_closure_is_reported_at_once():
+    """A seek whose closure misses a source block (its dependency list was
+    emptied on the host) finds the block's flag unmarked by the closure and
+    reports the archive corrupt without waiting; the context stays usable."""
     data = synth.generate("text", 200_000, 12)
     arc = oracle.encode(data, 12, 4, 16)
     b = 30
@@ -228,13 +230,61 @@ def test_wait_gives_up_with_timeout_status():
     assert deps and deps != [(0, 0)]
     bad = _with_dep_removed(arc, b)
     da = DeviceArchive(bad, max_seek_blocks=64)
-    ace.ace_index_set_tune(da.idx, ace.make_tune(wait_timeout_ns=2_000_000))
+    ace.ace_index_set_tune(da.idx, ace.make_tune(wait_timeout_ns=2_000_000_000))
+    t0 = time.perf_counter()
     da.seek(b * 4096, 100)
-    assert da.sync() == ace.ACE_E_TIMEOUT
+    assert da.sync() == ace.ACE_E_CORRUPT
+    assert time.perf_counter() - t0 < 1.0  # no wait ran out
     # a clean seek on the same scratch still works
     out = da.seek(0, 4096)
     assert da.sync() == ace.ACE_OK
     assert np.array_equal(out.cpu().numpy(), data[:4096])
+    da.close()
+
+
+def test_wait_gives_up_with_timeout_status():
+    """A seek batch through the block cache whose closure misses a source
+    block waits on a flag nothing sets; the bounded wait ends with
+    ACE_E_TIMEOUT and the cache stays usable after a reset."""
+    from paper_2606_24531_gb300.serve import SeekCache
+
+    data = synth.generate("text", 200_000, 12)
+    arc = oracle.encode(data, 12, 4, 16)
+    b = 30
+    bad = _with_dep_removed(arc, b)
+    da = DeviceArchive(bad, max_seek_blocks=64)
+    c = SeekCache([da], n_slots=64, max_reqs=4, pool_bytes=1 << 16,
+                  tune=ace.make_tune(wait_timeout_ns=2_000_000))
+    c.submit(c.plan([(0, b * 4096, 100)]))
+    assert c.sync() == ace.ACE_E_TIMEOUT
+    c.reset()
+    out = c.seek_many([(0, 0, 4096)])
+    assert np.array_equal(out[0].cpu().numpy(), data[:4096])
+    c.close()
+    da.close()
+
+
+def test_library_archive_seek_with_a_dependency_removed():
+    """A library archive (few dependency levels) whose block lost its
+    dependency list: the seek's closure misses the blocks its matches read,
+    which is reported as corrupt rather than read from other blocks' slots;
+    a clean seek still works."""
+    data = synth.generate("fastq", 3_000_000, 31)
+    arc = ace.ace_encode(data, 14, 16)
+    deps = oracle.deps(arc)
+    b = next(k for k in range(len(deps)) if deps[k] and deps[k] != [(0, 0)] and k > 70)
+    bad = _with_dep_removed(arc, b)
+    da = DeviceArchive(bad, max_seek_blocks=256)
+    assert da.info["n_levels"] <= 32
+    s = da.seek(b * 16384, 16384)
+    st = da.sync()
+    if st == ace.ACE_OK:  # only if block 0 happens to hold every source
+        assert np.array_equal(s.cpu().numpy(), data[b * 16384:(b + 1) * 16384])
+    else:
+        assert st == ace.ACE_E_CORRUPT, ace.ace_status_str(st)
+    out = da.seek(0, 16384)
+    assert da.sync() == ace.ACE_OK
+    assert np.array_equal(out.cpu().numpy(), data[:16384])
     da.close()
 
 
