@@ -37,6 +37,7 @@ WORKLOADS = {
 WORKLOAD = "fastq-256MiB-16KiB-blocks"
 SEEK_SEED = 2
 REF_SAMPLE = 8 << 20  # the reference arm decodes this many bytes of the workload per step
+E2E_INFLIGHT = 3      # end-to-end steps in flight, each with its own stream and device buffers
 METRIC = "decompressed GB/s (% HBM roofline); 16KB seek p50/p99 us, batched vs plain"
 KERNEL_SOURCES = ["paper_2606_24531_gb300/csrc/ace.cu", "paper_2606_24531_gb300/csrc/ace_device.cuh"]
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "literal_pass_fastq256.txt")
@@ -340,11 +341,11 @@ def main():
 
         # end to end through the C ABI from pinned host memory: every step
         # uploads the archive, builds its index, decodes and downloads the
-        # output; two steps are in flight on two streams with their own
-        # device buffers, so one step's copies overlap the other's decode
+        # output; E2E_INFLIGHT steps are in flight on their own streams and
+        # device buffers, so one step's copies overlap another's decode
         h_arc = torch.from_numpy(arc).pin_memory()
         slots = []
-        for _ in range(2):
+        for _ in range(E2E_INFLIGHT):
             st2 = torch.cuda.Stream(dev)
             slots.append({
                 "stream": st2,
@@ -375,17 +376,19 @@ def main():
             assert st_ == ace.ACE_OK
 
         n_e2e = max(4, min(args.steps, 20))
-        for k in range(2):  # warm-up
-            e2e_step(slots[k % 2])
+        depth = len(slots)
+        for k in range(depth):  # warm-up
+            e2e_step(slots[k])
         for sl in slots:
             e2e_finish(sl)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for k in range(n_e2e):
-            e2e_step(slots[k % 2])
-            if k > 0:
-                e2e_finish(slots[(k - 1) % 2])
-        e2e_finish(slots[(n_e2e - 1) % 2])
+            if k >= depth:
+                e2e_finish(slots[k % depth])  # the step that last used this slot
+            e2e_step(slots[k % depth])
+        for k in range(max(0, n_e2e - depth), n_e2e):
+            e2e_finish(slots[k % depth])
         e2e_s = (time.perf_counter() - t0) / n_e2e
         for sl in slots:
             assert np.array_equal(sl["h_out"].numpy()[:4096], data[:4096])
@@ -393,7 +396,8 @@ def main():
         result["e2e"] = {"value": world * total / e2e_s / 1e9, "unit": "GB/s",
                          "h2d_bytes_per_step": int(arc.size), "d2h_bytes_per_step": int(total),
                          "includes": "per step: H2D of the archive from pinned memory, index build, decode, "
-                                     "D2H of the output to pinned memory; two steps in flight on two streams"}
+                                     "D2H of the output to pinned memory; %d steps in flight on as many streams"
+                                     % E2E_INFLIGHT}
         del slots
 
         # batched: 4,096 uneven objects (log-uniform 4 KiB .. 2 MiB, four

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cstdint>
 #include <cstdio>
 #include <cstring>
@@ -144,8 +145,11 @@ __global__ void match_scan_kernel(IndexArgs a) {
 constexpr uint32_t kLevelSweeps = 8;
 
 __global__ void levels_sweep_kernel(IndexArgs a, uint32_t sweep) {
+  __shared__ uint32_t changed;
   if (*(volatile uint32_t*)&a.ih->status) return;
   if (sweep > 0 && !*(volatile uint32_t*)&a.ih->relax[sweep - 1]) return;  // settled already
+  if (threadIdx.x == 0) changed = 0;
+  __syncthreads();
   const uint32_t lane = threadIdx.x & 31;
   const uint64_t nw = (uint64_t)gridDim.x * (blockDim.x >> 5);
   for (uint64_t b = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5; b < a.nb; b += nw) {
@@ -157,9 +161,11 @@ __global__ void levels_sweep_kernel(IndexArgs a, uint32_t sweep) {
     for (int d = 16; d; d >>= 1) lv = max(lv, __shfl_xor_sync(kFull, lv, d));
     if (lane == 0 && lv > a.level[b]) {
       a.level[b] = lv;
-      a.ih->relax[sweep] = 1;
+      changed = 1;
     }
   }
+  __syncthreads();
+  if (threadIdx.x == 0 && changed) a.ih->relax[sweep] = 1;  // one store per CTA, not per block
 }
 
 // The levels in one CTA, block chunk by block chunk, for archives whose
@@ -1824,6 +1830,49 @@ inline bool aligned(const void* p, uintptr_t a) { return (reinterpret_cast<uintp
     if ((x) != cudaSuccess) return ACE_E_CUDA; \
   } while (0)
 
+// Small device headers (status words, counts) come back to the host through
+// pinned, mapped host memory written by a one-warp kernel, not through a
+// copy: a copy would queue on the copy engines behind large transfers that
+// other streams have in flight.  The library's only allocation, 256 KiB of
+// host memory, is made once per process; calls take 256-byte slots in turn
+// and hold one only while they wait for their stream.
+constexpr uint32_t kMirrorSlots = 1024, kMirrorBytes = 256;
+
+__global__ void mirror_kernel(const uint32_t* src, uint32_t* dst, uint32_t words) {
+  for (uint32_t i = threadIdx.x; i < words; i += blockDim.x) dst[i] = *(volatile const uint32_t*)(src + i);
+}
+
+std::once_flag g_mirror_once;
+uint8_t* g_mirror_host = nullptr;
+uint8_t* g_mirror_dev = nullptr;
+std::atomic<uint32_t> g_mirror_next{0};
+
+// Reads bytes (a multiple of 4, at most 256) at d_src into h_dst after the
+// work already on s; synchronises s.
+ace_status read_header(const void* d_src, void* h_dst, uint32_t bytes, cudaStream_t s) {
+  std::call_once(g_mirror_once, [] {
+    void* h = nullptr;
+    void* d = nullptr;
+    if (cudaHostAlloc(&h, (size_t)kMirrorSlots * kMirrorBytes, cudaHostAllocMapped | cudaHostAllocPortable) !=
+        cudaSuccess)
+      return;
+    if (cudaHostGetDevicePointer(&d, h, 0) != cudaSuccess) {
+      cudaFreeHost(h);
+      return;
+    }
+    g_mirror_host = static_cast<uint8_t*>(h);
+    g_mirror_dev = static_cast<uint8_t*>(d);
+  });
+  if (!g_mirror_host || bytes > kMirrorBytes || (bytes & 3)) return ACE_E_CUDA;
+  const uint32_t k = g_mirror_next.fetch_add(1) % kMirrorSlots;
+  mirror_kernel<<<1, 64, 0, s>>>(static_cast<const uint32_t*>(d_src),
+                                 reinterpret_cast<uint32_t*>(g_mirror_dev + (size_t)k * kMirrorBytes), bytes / 4);
+  CUDA_TRY(cudaGetLastError());
+  CUDA_TRY(cudaStreamSynchronize(s));
+  std::memcpy(h_dst, (const void*)(g_mirror_host + (size_t)k * kMirrorBytes), bytes);
+  return ACE_OK;
+}
+
 // Launch shape of one three-pass decode: per pass the shared memory of a warp
 // (tokens: tables, two rings and escape values; literals: tables, a ring and
 // the token window; matches: the match records) and the grid.
@@ -2043,9 +2092,7 @@ ace_status ace_index_build(const void* d_archive, uint64_t archive_bytes, const 
     level_scan_kernel<<<1, 1024, 0, s>>>(a);
     level_scatter_kernel<<<g, 256, 0, s>>>(a);
     IndexHdr ih;
-    if (cudaMemcpyAsync(&ih, idx->d_ih, sizeof ih, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-        cudaStreamSynchronize(s) != cudaSuccess)
-      return bail(ACE_E_CUDA);
+    if (read_header(idx->d_ih, &ih, sizeof ih, s) != ACE_OK) return bail(ACE_E_CUDA);
     if (ih.status) return bail((ace_status)ih.status);
     idx->n_iv = ih.n_iv;
     idx->max_ntok = ih.max_ntok;
@@ -2259,10 +2306,9 @@ ace_status ace_seek(const ace_index* idx, uint64_t coord, uint64_t len, void* d_
 
 ace_status ace_sync(const ace_index* idx, void* d_scratch, cudaStream_t s) {
   if (!idx || !d_scratch) return ACE_E_INVAL;
-  CUDA_TRY(cudaStreamSynchronize(s));
   ScratchHdr h;
-  CUDA_TRY(cudaMemcpyAsync(&h, d_scratch, sizeof h, cudaMemcpyDeviceToHost, s));
-  CUDA_TRY(cudaStreamSynchronize(s));
+  ace_status rc = read_header(d_scratch, &h, sizeof h, s);
+  if (rc) return rc;
   if (h.status) {
     CUDA_TRY(cudaMemsetAsync(d_scratch, 0, 3 * sizeof(uint32_t), s));
     CUDA_TRY(cudaStreamSynchronize(s));
@@ -2472,10 +2518,9 @@ ace_status ace_decode_batch(const ace_batch* b, cudaStream_t s) {
 
 ace_status ace_batch_sync(const ace_batch* b, cudaStream_t s) {
   if (!b) return ACE_E_INVAL;
-  CUDA_TRY(cudaStreamSynchronize(s));
   ScratchHdr h;
-  CUDA_TRY(cudaMemcpyAsync(&h, b->d_scratch, sizeof h, cudaMemcpyDeviceToHost, s));
-  CUDA_TRY(cudaStreamSynchronize(s));
+  ace_status rc = read_header(b->d_scratch, &h, sizeof h, s);
+  if (rc) return rc;
   if (h.status) {
     CUDA_TRY(cudaMemsetAsync(b->d_scratch, 0, 3 * sizeof(uint32_t), s));
     CUDA_TRY(cudaStreamSynchronize(s));
@@ -2695,10 +2740,9 @@ ace_status ace_seek_batch_host(const ace_cache* c, const ace_seek_req* h_reqs, c
 
 ace_status ace_cache_sync(const ace_cache* c, cudaStream_t s) {
   if (!c) return ACE_E_INVAL;
-  CUDA_TRY(cudaStreamSynchronize(s));
   CacheHdr h;
-  CUDA_TRY(cudaMemcpyAsync(&h, c->mem, sizeof h, cudaMemcpyDeviceToHost, s));
-  CUDA_TRY(cudaStreamSynchronize(s));
+  ace_status rc = read_header(c->mem, &h, sizeof h, s);
+  if (rc) return rc;
   if (h.status) {
     CUDA_TRY(cudaMemsetAsync(c->mem, 0, 3 * sizeof(uint32_t), s));
     CUDA_TRY(cudaStreamSynchronize(s));
@@ -2709,8 +2753,8 @@ ace_status ace_cache_sync(const ace_cache* c, cudaStream_t s) {
 ace_status ace_cache_usage(const ace_cache* c, uint32_t* used_slots, uint32_t* n_slots, cudaStream_t s) {
   if (!c) return ACE_E_INVAL;
   CacheHdr h;
-  CUDA_TRY(cudaMemcpyAsync(&h, c->mem, sizeof h, cudaMemcpyDeviceToHost, s));
-  CUDA_TRY(cudaStreamSynchronize(s));
+  ace_status rc = read_header(c->mem, &h, sizeof h, s);
+  if (rc) return rc;
   if (used_slots) *used_slots = h.next_slot;
   if (n_slots) *n_slots = c->n_slots;
   return ACE_OK;
@@ -2843,8 +2887,8 @@ ace_status ace_seek_noalloc(const ace_index* idx, uint64_t coord, uint64_t len, 
   CUDA_TRY(cudaGetLastError());
   // the status lives in the shared array, so the call waits for it
   uint32_t status = 0;
-  CUDA_TRY(cudaMemcpyAsync(&status, base, sizeof status, cudaMemcpyDeviceToHost, s));
-  CUDA_TRY(cudaStreamSynchronize(s));
+  rc = read_header(base, &status, sizeof status, s);
+  if (rc) return rc;
   return (ace_status)status;
 }
 
