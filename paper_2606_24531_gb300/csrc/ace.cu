@@ -512,10 +512,17 @@ __device__ bool token_block(const DecodeArgs& a, const TokMem& m, const TokRec& 
   if (ok && nm) {
     if (!lut_build(so, *m.lut, lane)) fail(a, ok, ACE_E_CORRUPT, b, 33, lane);
     const uint32_t oend = w * nm;
-    if (ok)
-      rans_run(so, ro, *m.lut, oend, lane, lt, [&](bool act, uint32_t i, uint32_t s) {
-        if (act) g.offb[i] = (uint8_t)s;
+    auto put = [&](bool act, uint32_t i, uint32_t s) {
+      if (act) g.offb[i] = (uint8_t)s;
+    };
+    if (ok && so.k == 0 && oend >= 64) {  // slot-table streams: full rounds in the fast loop
+      uint32_t i = lane;
+      table_full_rounds(so, ro, *m.lut, oend >> 5, lane, lt, [&](uint32_t s) {
+        g.offb[i] = (uint8_t)s;
+        i += 32;
       });
+    }
+    if (ok) rans_run(so, ro, *m.lut, oend, lane, lt, put);
   }
   __syncwarp();
   // the match records: absolute source, destination in the block, length
@@ -901,11 +908,6 @@ __device__ bool match_block(const DecodeArgs& a, MatchRec* gm, uint32_t b, uint3
         const uint32_t* flags = WAIT ? a.ready : a.level;
         f0[q] = ld_relaxed(flags + k0);
         f1[q] = k1 != k0 ? ld_relaxed(flags + k1) : f0[q];
-        if (SEEK && !WAIT) {  // a seek's source blocks must be in its closure
-          const uint32_t r0 = ld_relaxed(a.ready + k0) & ~kPendingFlag, r1 = ld_relaxed(a.ready + k1) & ~kPendingFlag;
-          if (r0 != epoch) f0[q] |= 0x80000000u;
-          if (r1 != epoch) f1[q] |= 0x80000000u;
-        }
       }
       if (rend > bstart) {  // bytes of this block: the group's matches writing them
         const uint32_t s_rel = S > bstart ? (uint32_t)(S - bstart) : 0u, e_rel = (uint32_t)(rend - bstart);
@@ -1033,10 +1035,8 @@ __device__ bool match_block(const DecodeArgs& a, MatchRec* gm, uint32_t b, uint3
         const uint64_t S = gS[j], D = bstart + gD[j];
         const uint64_t rend = S + min((uint64_t)gL[j], D - S);
         const uint64_t k0 = S >> a.log2B, k1 = min((rend - 1) >> a.log2B, (uint64_t)b - 1);
-        for (uint64_t k = k0 + 1; k < k1; k++) {  // a source spanning more than two earlier blocks
+        for (uint64_t k = k0 + 1; k < k1; k++)  // a source spanning more than two earlier blocks
           if (__ldg(a.level + k) >= a.cur_level) bad = true;
-          if (SEEK && (ld_relaxed(a.ready + k) & ~kPendingFlag) != epoch) bad = true;
-        }
       }
       if (__any_sync(kFull, bad)) fail(a, ok, ACE_E_CORRUPT, b, 39, lane);
       __syncwarp();
@@ -1115,49 +1115,28 @@ __global__ void __launch_bounds__(256, ACE_PASS_MIN_CTAS(PASS)) decode_kernel(De
 // waits.  Blocks are dealt out statically (block k of the level to warp
 // k mod the warps in the grid), and each warp fetches its next block's
 // number and record range while it resolves the current one.
-template <bool SEEK>
 __global__ void __launch_bounds__(256, 2) match_level_kernel(DecodeArgs a) {
   extern __shared__ __align__(16) uint8_t smem[];
   const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const uint32_t nw = gridDim.x * (blockDim.x >> 5);
   if (*(volatile uint32_t*)&a.sh->status) return;
-  const uint32_t epoch = *(volatile uint32_t*)&a.sh->epoch;
-  // a seek's level ranges come from its closure, on the device
-  const uint32_t* items = a.items;
-  uint32_t n_items = a.n_items;
-  if (SEEK) {
-    const uint32_t l0 = *(volatile uint32_t*)&a.sh->lv_start[a.cur_level];
-    items = a.items + l0;
-    n_items = *(volatile uint32_t*)&a.sh->lv_start[a.cur_level + 1] - l0;
-  }
   MatchRec* gm = reinterpret_cast<MatchRec*>(smem + (size_t)wid * kMatchSmem);
   uint32_t it = blockIdx.x * (blockDim.x >> 5) + wid;
-  if (it >= n_items) return;
+  if (it >= a.n_items) return;
   auto n_matches = [&](uint32_t b) -> uint32_t {
-    if (SEEK) {
-      const uint32_t ntok = __ldg(reinterpret_cast<const uint32_t*>(a.dir + b) + 12);
-      return ntok ? ntok - 1 : 0;
-    }
     return (uint32_t)(__ldg(a.match_ptr + b + 1) - __ldg(a.match_ptr + b));
   };
-  uint32_t b = __ldg(items + it);
+  uint32_t b = __ldg(a.items + it);
   uint32_t nm = n_matches(b);
   while (true) {
     const uint32_t nx = it + nw;
     uint32_t bn = 0, nmn = 0;
-    if (nx < n_items) {
-      bn = __ldg(items + nx);
+    if (nx < a.n_items) {
+      bn = __ldg(a.items + nx);
       nmn = n_matches(bn);
     }
-    const bool ok = match_block<SEEK, false>(a, gm, b, lane, epoch, nm);
-    if (SEEK && ok && a.slice) {
-      // the part of this block inside [coord, coord + len) to the caller
-      uint64_t bs = (uint64_t)b << a.log2B, be = min(bs + ((uint64_t)1 << a.log2B), a.total);
-      uint64_t lo = max(bs, a.coord), hi = min(be, a.coord + a.len);
-      const uint8_t* src = a.out + ((uint64_t)a.slot_of[b] << a.log2B) - bs;
-      if (hi > lo) warp_copy(a.slice + (lo - a.coord), src + lo, hi - lo, lane);
-    }
-    if (nx >= n_items) break;
+    match_block<false, false>(a, gm, b, lane, 0, nm);
+    if (nx >= a.n_items) break;
     it = nx;
     b = bn;
     nm = nmn;
@@ -1727,8 +1706,7 @@ struct ace_index {
   ace_tune tune;
   // occupancy of the decode kernels, per (seek?, pass, warps per CTA, window)
   mutable int occ_cache[2][3][9][9];
-  mutable int occ_level[9][9];       // the per-level match kernel, whole decodes
-  mutable int occ_level_seek[9][9];  // and seeks
+  mutable int occ_level[9][9];  // the per-level match kernel
   // whole decodes resolve matches with one launch per level when there are
   // at most kMaxLevelLaunches levels: level L's blocks are
   // order[level_start[L] .. level_start[L + 1])
@@ -1969,34 +1947,13 @@ void launch_three_pass(const Launch& L, const DecodeArgs& a, cudaStream_t s) {
                 decode_kernel<SEEK, PASS_MATCH>, a, s);
 }
 
-// A plain seek decodes about a hundred blocks at most levels deep: one match
-// launch waiting on flags beats a launch per level there.
-constexpr bool kSeekByLevels = false;
-
 // A seek after its closure kernel: tokens and literals over the work list,
-// then, for an archive with few levels, one match launch per level (the
-// level ranges are read on the device), else one match launch that waits on
-// the source blocks' flags.  max_items bounds the work list.
-ace_status launch_seek(const ace_index* idx, const Launch& L, DecodeArgs a, uint64_t max_items, cudaStream_t s) {
-  if (!idx->by_levels || !kSeekByLevels) {
-    launch_three_pass<true>(L, a, s);
-    return ACE_OK;
-  }
-  launch_passes(L, 3, decode_kernel<true, PASS_TOKENS>, decode_kernel<true, PASS_LITERALS>,
-                decode_kernel<true, PASS_MATCH>, a, s);
-  a.warp_smem = L.smem[PASS_MATCH];
-  int& occ = idx->occ_level_seek[L.warps][L.chunk / 32];
-  if (occ == 0) {
-    ace_status rc = occupancy(match_level_kernel<true>, idx->device, L.warps, (size_t)L.warps * L.smem[PASS_MATCH], &occ);
-    if (rc) return rc;
-  }
-  if (occ < 0) return ACE_E_INVAL;
-  const uint32_t grid =
-      (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>((uint64_t)idx->num_sms * occ, (max_items + L.warps - 1) / L.warps));
-  for (uint32_t l = 0; l < idx->n_levels; l++) {
-    a.cur_level = l;
-    match_level_kernel<true><<<grid, 32 * L.warps, (size_t)L.warps * L.smem[PASS_MATCH], s>>>(a);
-  }
+// then one match launch over the level-ordered list that waits, bounded, on
+// the pending members of the closure.  (One launch per level, as whole
+// decodes do, is slower for a seek's hundred-odd blocks.)
+ace_status launch_seek(const ace_index* idx, const Launch& L, const DecodeArgs& a, cudaStream_t s) {
+  (void)idx;
+  launch_three_pass<true>(L, a, s);
   return ACE_OK;
 }
 
@@ -2198,7 +2155,7 @@ ace_status decode_all_passes(const ace_index* idx, uint32_t passes, void* d_out,
     a.warp_smem = L.smem[PASS_MATCH];
     int& occ = idx->occ_level[L.warps][L.chunk / 32];
     if (occ == 0) {
-      rc = occupancy(match_level_kernel<false>, idx->device, L.warps, (size_t)L.warps * L.smem[PASS_MATCH], &occ);
+      rc = occupancy(match_level_kernel, idx->device, L.warps, (size_t)L.warps * L.smem[PASS_MATCH], &occ);
       if (rc) return rc;
     }
     if (occ < 0) return ACE_E_INVAL;
@@ -2213,7 +2170,7 @@ ace_status decode_all_passes(const ace_index* idx, uint32_t passes, void* d_out,
       a.n_items = n;
       a.cur_level = l;
       const uint32_t grid = (uint32_t)std::min<uint64_t>((uint64_t)idx->num_sms * per_sm, (n + L.warps - 1) / L.warps);
-      match_level_kernel<false><<<grid, 32 * L.warps, (size_t)L.warps * L.smem[PASS_MATCH], s>>>(a);
+      match_level_kernel<<<grid, 32 * L.warps, (size_t)L.warps * L.smem[PASS_MATCH], s>>>(a);
     }
   }
   CUDA_TRY(cudaGetLastError());
@@ -2298,7 +2255,7 @@ ace_status ace_seek(const ace_index* idx, uint64_t coord, uint64_t len, void* d_
   a.match_ptr = nullptr;
   a.level = idx->d_level;
   a.closure_flags = true;
-  rc = launch_seek(idx, L, a, cap, s);
+  rc = launch_seek(idx, L, a, s);
   if (rc) return rc;
   CUDA_TRY(cudaGetLastError());
   return ACE_OK;
@@ -2882,7 +2839,7 @@ ace_status ace_seek_noalloc(const ace_index* idx, uint64_t coord, uint64_t len, 
   a.match_ptr = nullptr;
   a.level = idx->d_level;
   a.closure_flags = true;
-  rc = launch_seek(idx, L, a, cap, s);
+  rc = launch_seek(idx, L, a, s);
   if (rc) return rc;
   CUDA_TRY(cudaGetLastError());
   // the status lives in the shared array, so the call waits for it
