@@ -862,13 +862,23 @@ __device__ bool match_block(const DecodeArgs& a, MatchRec* gm, uint32_t b, uint3
   uint32_t* gD = reinterpret_cast<uint32_t*>(gS + kMatchGroup);   // [kMatchGroup] destinations in the block
   uint32_t* gL = gD + kMatchGroup;                                // [kMatchGroup] lengths
   uint32_t* gX = gL + kMatchGroup;                                // [kMatchGroup + 1] starts in a round's copy
+  // each group's records are loaded while the group before it resolves
+  uint4 rn[kLaneMatches];
+#pragma unroll
+  for (uint32_t q = 0; q < kLaneMatches; q++) {
+    const uint32_t j = lane + 32 * q;
+    rn[q] = j < min(kMatchGroup, nm) ? __ldcg(rec + j) : make_uint4(0, 0, 0, 0);
+  }
   for (uint32_t t0 = 0; ok && t0 < nm; t0 += kMatchGroup) {
     const uint32_t gn = min(kMatchGroup, nm - t0);
     uint4 r[kLaneMatches];
 #pragma unroll
+    for (uint32_t q = 0; q < kLaneMatches; q++) r[q] = rn[q];
+    const uint32_t t1 = t0 + kMatchGroup;
+#pragma unroll
     for (uint32_t q = 0; q < kLaneMatches; q++) {
       const uint32_t j = lane + 32 * q;
-      r[q] = j < gn ? __ldcg(rec + t0 + j) : make_uint4(0, 0, 0, 0);
+      rn[q] = t1 < nm && j < min(kMatchGroup, nm - t1) ? __ldcg(rec + t1 + j) : make_uint4(0, 0, 0, 0);
     }
     uint32_t pend = 0;
 #pragma unroll
