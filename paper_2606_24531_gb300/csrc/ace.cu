@@ -298,7 +298,7 @@ struct TokRec {
   uint8_t* offb;   // [5 max_ntok]
 };
 
-constexpr uint32_t kMatchGroup = 64;  // matches whose records sit in shared memory at a time
+constexpr uint32_t kMatchGroup = 32;  // matches whose records sit in shared memory at a time
 
 __host__ __device__ inline uint32_t tok_smem_bytes(uint32_t escn) {
   return (sizeof(Lut) + 2 * kRing + 2 * escn + 15) & ~15u;
@@ -839,7 +839,7 @@ __device__ __forceinline__ uint32_t upper_bound(uint32_t n, uint32_t x, Key key)
 }
 
 // Match pass of one block (Section 2: a block decodes once the blocks holding
-// its sources are present).  Groups of up to 64 matches: their records are
+// its sources are present).  Groups of up to 32 matches: their records are
 // loaded together; with WAIT the source blocks before this one are checked
 // with overlapping relaxed loads (a bounded wait only for one not yet
 // published); without it (one launch per dependency level) each source
