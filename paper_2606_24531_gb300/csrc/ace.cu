@@ -667,6 +667,8 @@ __device__ bool literal_block(const DecodeArgs& a, const LitMem& m, uint32_t b, 
 constexpr uint32_t kLaneMatches = kMatchGroup / 32;
 // Bytes in flight per lane in the bytewise copy of a round's matches.
 constexpr uint32_t kCopyUnroll = 8;
+// 16-byte pieces in flight per lane in the copy of a round's long matches.
+constexpr uint32_t kLongUnroll = 4;
 // Copy classes: a non-overlapping match of at most kShortMax bytes is copied
 // by one lane, one of at least kLongMin bytes by the whole warp in 16-byte
 // pieces, every other one bytewise with the round's other such matches.
@@ -761,49 +763,6 @@ __device__ __forceinline__ uint4 shfl_down16(uint4 v, uint32_t d) {
                     __shfl_down_sync(kFull, v.w, d));
 }
 
-// The whole warp copies one long non-overlapping match from sp to dp within
-// [lo, hi) (whole-decode addressing): lane l of a step writes the aligned
-// 16-byte destination piece c = 32 u + l, two pieces per lane in flight,
-// each built from the aligned source piece it starts in and the next one
-// (the next lane's, or one more load on lane 31).  Pieces the match covers
-// go out as 16-byte stores, the two end pieces bytewise.
-__device__ __forceinline__ void copy_long(uint8_t* dp, const uint8_t* sp, uint32_t len, const uint8_t* lo,
-                                          const uint8_t* hi, uint32_t lane) {
-  const uint32_t hd = (uint32_t)(reinterpret_cast<uintptr_t>(dp) & 15);
-  uint8_t* dal = dp - hd;
-  const uint8_t* s0 = sp - hd;  // source of dal[0]
-  const uint32_t r = (uint32_t)(reinterpret_cast<uintptr_t>(s0) & 15);
-  const uint8_t* sal = s0 - r;
-  const uint32_t nch = (hd + len + 15) >> 4;
-  for (uint32_t c0 = 0; c0 < nch; c0 += 64) {
-    uint4 A[2], Bn[2];
-#pragma unroll
-    for (uint32_t u = 0; u < 2; u++) {
-      const uint32_t c = c0 + 32 * u + lane;
-      A[u] = c <= nch ? ld16_in(sal + 16ull * c, lo, hi) : make_uint4(0, 0, 0, 0);
-      Bn[u] = (lane == 31 && c + 1 <= nch) ? ld16_in(sal + 16ull * (c + 1), lo, hi) : make_uint4(0, 0, 0, 0);
-    }
-#pragma unroll
-    for (uint32_t u = 0; u < 2; u++) {
-      const uint32_t c = c0 + 32 * u + lane;
-      const uint4 nb = shfl_down16(A[u], 1);
-      const uint4 B = lane == 31 ? Bn[u] : nb;
-      if (c >= nch) continue;
-      const uint4 v = funnel128(A[u], B, r);
-      const int first = 16 * (int)c - (int)hd;  // match byte held by the piece's first byte
-      if (first >= 0 && first + 16 <= (int)len) {
-        *reinterpret_cast<uint4*>(dal + 16ull * c) = v;
-      } else {
-#pragma unroll 1
-        for (uint32_t k = 0; k < 16; k++) {
-          const int di = first + (int)k;
-          const uint32_t x = k < 4 ? v.x : k < 8 ? v.y : k < 12 ? v.z : v.w;
-          if (di >= 0 && di < (int)len) dal[16ull * c + k] = (uint8_t)(x >> (8 * (k & 3)));
-        }
-      }
-    }
-  }
-}
 
 // Whether a bit of the 128-bit mask (P0, P1, P2, P3) is set in [lo, hi].
 __device__ __forceinline__ bool any_in(uint32_t P0, uint32_t P1, uint32_t P2, uint32_t P3, uint32_t lo,
@@ -985,15 +944,76 @@ __device__ bool match_block(const DecodeArgs& a, MatchRec* gm, uint32_t b, uint3
           for (uint32_t k = 0; k < 5; k++) cur[k] = nxt[k];
         }
       }
-      {  // long: one match at a time
-        uint32_t rest = lgo, any;
-        while ((any = __ballot_sync(kFull, rest != 0)) != 0) {
-          const uint32_t src_lane = __ffs(any) - 1;
-          const uint32_t q = __ffs(__shfl_sync(kFull, rest, src_lane)) - 1;
-          const uint32_t j = src_lane + 32 * q;
-          copy_long(obase + gD[j], a.out + gS[j], gL[j], a.out, a.out + a.total, lane);
-          if (lane == src_lane) rest &= ~(1u << q);
+      if (__any_sync(kFull, lgo != 0)) {
+        // long: the round's long matches at once, laid end to end as the
+        // aligned 16-byte source pieces each one needs (its destination
+        // pieces plus one), kLongUnroll pieces per lane in flight; piece c
+        // and piece c + 1 build destination piece c, and piece c + 1 is the
+        // next lane's (lane 0's next one for lane 31)
+        static_assert(kLaneMatches == 1, "one match per lane");
+        const bool mine = lgo & 1;
+        const uint32_t hd0 = (uint32_t)(reinterpret_cast<uintptr_t>(obase + gD[lane]) & 15);
+        const uint32_t np = mine ? ((hd0 + gL[lane] + 15) >> 4) + 1 : 0u;
+        const uint32_t incl = warp_incl_sum(np, lane);
+        gX[lane] = incl - np;
+        if (lane == 31) gX[32] = incl;
+        const uint32_t T = __shfl_sync(kFull, incl, 31);
+        __syncwarp();
+        auto piece = [&](uint32_t c, uint32_t& jp) -> uint4 {
+          const uint32_t j = upper_bound(33, c, [&](uint32_t i) { return gX[i]; }) - 1;
+          const uint32_t pc = c - gX[j];
+          jp = j | (pc << 5);
+          uint8_t* dpj = obase + gD[j];
+          const uint8_t* s0 = a.out + gS[j] - (reinterpret_cast<uintptr_t>(dpj) & 15);
+          const uint8_t* sal = s0 - (reinterpret_cast<uintptr_t>(s0) & 15);
+          return ld16_in(sal + 16ull * pc, a.out, a.out + a.total);
+        };
+        for (uint32_t c0 = 0; c0 < T; c0 += 32 * kLongUnroll) {
+          uint4 A[kLongUnroll];
+          uint32_t jp[kLongUnroll];
+          uint4 An = make_uint4(0, 0, 0, 0);
+#pragma unroll
+          for (uint32_t u = 0; u < kLongUnroll; u++) {
+            const uint32_t c = c0 + 32 * u + lane;
+            jp[u] = 0xffffffffu;
+            A[u] = c < T ? piece(c, jp[u]) : make_uint4(0, 0, 0, 0);
+          }
+          if (lane == 31 && c0 + 32 * kLongUnroll < T) {
+            uint32_t unused;
+            An = piece(c0 + 32 * kLongUnroll, unused);
+          }
+#pragma unroll
+          for (uint32_t u = 0; u < kLongUnroll; u++) {
+            const uint4 nb = shfl_down16(A[u], 1);
+            uint4 n0 = An;
+            if (u + 1 < kLongUnroll)
+              n0 = make_uint4(__shfl_sync(kFull, A[u + 1 < kLongUnroll ? u + 1 : u].x, 0),
+                              __shfl_sync(kFull, A[u + 1 < kLongUnroll ? u + 1 : u].y, 0),
+                              __shfl_sync(kFull, A[u + 1 < kLongUnroll ? u + 1 : u].z, 0),
+                              __shfl_sync(kFull, A[u + 1 < kLongUnroll ? u + 1 : u].w, 0));
+            const uint4 B = lane == 31 ? n0 : nb;
+            if (jp[u] == 0xffffffffu) continue;
+            const uint32_t j = jp[u] & 31, pc = jp[u] >> 5, ml = gL[j];
+            uint8_t* dpj = obase + gD[j];
+            const uint32_t hd = (uint32_t)(reinterpret_cast<uintptr_t>(dpj) & 15);
+            if (pc >= ((hd + ml + 15) >> 4)) continue;  // the trailing source piece stores nothing
+            const uint8_t* s0 = a.out + gS[j] - hd;
+            const uint4 v = funnel128(A[u], B, (uint32_t)(reinterpret_cast<uintptr_t>(s0) & 15));
+            uint8_t* dal = dpj - hd;
+            const int first = 16 * (int)pc - (int)hd;  // match byte held by the piece's first byte
+            if (first >= 0 && first + 16 <= (int)ml) {
+              *reinterpret_cast<uint4*>(dal + 16ull * pc) = v;
+            } else {
+#pragma unroll 1
+              for (uint32_t k = 0; k < 16; k++) {
+                const int di = first + (int)k;
+                const uint32_t x = k < 4 ? v.x : k < 8 ? v.y : k < 12 ? v.z : v.w;
+                if (di >= 0 && di < (int)ml) dal[16ull * pc + k] = (uint8_t)(x >> (8 * (k & 3)));
+              }
+            }
+          }
         }
+        __syncwarp();
       }
       // the rest laid end to end in group order: gX[j] is where match j
       // starts, gX[kMatchGroup] the total
