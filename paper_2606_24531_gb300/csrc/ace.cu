@@ -668,7 +668,7 @@ constexpr uint32_t kLaneMatches = kMatchGroup / 32;
 // Bytes in flight per lane in the bytewise copy of a round's matches.
 constexpr uint32_t kCopyUnroll = 8;
 // 16-byte pieces in flight per lane in the copy of a round's long matches.
-constexpr uint32_t kLongUnroll = 4;
+constexpr uint32_t kLongUnroll = 2;
 // Copy classes: a non-overlapping match of at most kShortMax bytes is copied
 // by one lane, one of at least kLongMin bytes by the whole warp in 16-byte
 // pieces, every other one bytewise with the round's other such matches.
