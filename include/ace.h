@@ -25,7 +25,10 @@
  *  - Calls that share one scratch buffer must be ordered on one stream;
  *    calls with separate scratch buffers may overlap on the device.
  *  - The library keeps no global state except the CUDA device it runs on,
- *    taken as the current device when the index is built.
+ *    taken as the current device when the index is built, and 256 KiB of
+ *    pinned, mapped host memory allocated once per process on first use,
+ *    through which the calls that report a device status read it back
+ *    (a copy would queue behind other streams' large transfers).
  */
 #ifndef ACE_H
 #define ACE_H
@@ -203,8 +206,9 @@ ace_status ace_decode_pass(const ace_index *idx, int pass, void *d_out, uint64_t
  * the len requested bytes are written to d_out[0, len).  Nothing else in
  * d_out is touched.  coord and len need no alignment.  ACE_E_RANGE when
  * len == 0 or coord + len > total_size.  If the blocks to decode exceed the
- * max_seek_blocks the scratch was sized for, ace_sync reports ACE_E_NOMEM.
- * Asynchronous.
+ * max_seek_blocks the scratch was sized for, ace_sync reports ACE_E_NOMEM;
+ * if a match reads a block outside that set (the archive's dependency lists
+ * disagree with its matches), ace_sync reports ACE_E_CORRUPT.  Asynchronous.
  */
 ace_status ace_seek(const ace_index *idx, uint64_t coord, uint64_t len, void *d_out,
                     uint64_t out_bytes, void *d_scratch, uint64_t scratch_bytes, cudaStream_t s);
@@ -231,9 +235,10 @@ ace_status ace_sync(const ace_index *idx, void *d_scratch, cudaStream_t s);
  * ace_batch_create records the archives (all on the current device) and
  * their outputs (out_bytes[i] >= the archive's total size) in the scratch,
  * plans the launch from tune (NULL = defaults), and synchronises s.  It
- * allocates no device memory.  ace_decode_batch then enqueues exactly two
- * kernels on s and no host synchronisation, so it can be captured into a
- * CUDA graph and replayed; each replay decodes every archive again.
+ * allocates no device memory.  ace_decode_batch then enqueues exactly four
+ * kernels on s (a header reset and the token, literal and match passes) and
+ * no host synchronisation, so it can be captured into a CUDA graph and
+ * replayed; each replay decodes every archive again.
  * ace_batch_sync synchronises s and returns (then clears) the first device
  * error.  ace_batch_launch_shape reports the planned grid, warps per CTA and
  * token window.
@@ -347,7 +352,8 @@ ace_status ace_fnv1a64(const void *d_p, uint64_t n, uint64_t *d_result, cudaStre
  * up the array's device address; make that first call before any stream
  * capture.  The index's device must be current.  Archives whose per-block
  * tables and token records do not fit, or requests covering more blocks
- * than the remaining slots, return ACE_E_NOMEM.  Calls no allocator.
+ * than the remaining slots, return ACE_E_NOMEM.  Calls no allocator (the
+ * status buffer above already exists once an index was built).
  * Synchronises s and returns the seek's device-side status (ACE_OK,
  * ACE_E_CORRUPT, ACE_E_TIMEOUT, ACE_E_NOMEM when the closure exceeds the
  * slots); otherwise as ace_seek.

@@ -264,7 +264,7 @@ struct DecodeArgs {
   uint64_t timeout_ns;
   uint8_t* warp_scratch;   // per-warp token records
   uint64_t warp_scratch_bytes;
-  MatchRec* recs;          // match records between the two passes
+  MatchRec* recs;          // match records, from the token pass to the literal and match passes
   const uint64_t* match_ptr;  // whole decode: block -> first record; null: max_ntok records per slot
   const uint32_t* level;   // whole decode by levels: each block's dependency level
   uint32_t cur_level;      // whole decode by levels: the level this launch resolves
@@ -806,7 +806,7 @@ __device__ __forceinline__ uint32_t upper_bound(uint32_t n, uint32_t x, Key key)
 // dependency lists disagree with its matches.  Then the group resolves in
 // rounds.  A match is ready in a round when no
 // pending match of its block writes a byte its source reads; literal bytes
-// are final after the entropy pass.  The first pending match is always ready,
+// are final after the literal pass.  The first pending match is always ready,
 // so every round makes progress, and a round's ready matches read no byte
 // another one writes.  Returns false if a record is corrupt or a wait gave up.
 template <bool SEEK, bool WAIT>
@@ -846,7 +846,7 @@ __device__ bool match_block(const DecodeArgs& a, MatchRec* gm, uint32_t b, uint3
       if (j >= gn) continue;
       const uint64_t S = (uint64_t)r[q].x | ((uint64_t)r[q].y << 32);
       uint32_t ml = r[q].w;
-      if (ml && (S >= bstart + r[q].z || (uint64_t)r[q].z + ml > blen)) {  // checked again: the entropy pass may have failed
+      if (ml && (S >= bstart + r[q].z || (uint64_t)r[q].z + ml > blen)) {  // checked again: the token pass may have failed
         bad = true;
         ml = 0;
       }
@@ -1096,10 +1096,11 @@ __device__ __forceinline__ void publish(uint32_t* ready, uint32_t b, uint32_t ep
   if (lane == 0) st_release(ready + b, epoch);
 }
 
-// One pass over a work list by persistent warps: the entropy pass decodes
-// every block's streams and places its literals; the match pass, launched
-// after it, resolves every block's matches in (level, block) order and
-// publishes the block.
+// One pass over a work list by persistent warps: the token pass decodes every
+// block's length and offset streams into match records; the literal pass
+// decodes every block's literal stream straight to its output positions; the
+// match pass, launched after them, resolves every block's matches in (level,
+// block) order, waiting on source blocks' flags, and publishes the block.
 template <bool SEEK, int PASS>
 __global__ void __launch_bounds__(256, ACE_PASS_MIN_CTAS(PASS)) decode_kernel(DecodeArgs a) {
   extern __shared__ __align__(16) uint8_t smem[];
@@ -1590,7 +1591,7 @@ struct CacheDecodeArgs {
   uint64_t warp_scratch_bytes;
 };
 
-// Decodes a batch's work list into cache slots: the same two passes as a
+// Decodes a batch's work list into cache slots: the same three passes as a
 // seek, archive by archive.
 template <int PASS>
 __global__ void __launch_bounds__(256, ACE_PASS_MIN_CTAS(PASS)) cache_decode_kernel(CacheDecodeArgs ca) {

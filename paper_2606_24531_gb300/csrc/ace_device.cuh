@@ -46,9 +46,9 @@ struct IndexHdr {
 };
 static_assert(sizeof(IndexHdr) == 256, "index header");
 
-// One match of a block, between the entropy pass that finds it and the
-// match pass that resolves it: absolute source, destination within the
-// block, length.
+// One match of a block, between the token pass that finds it and the match
+// pass that resolves it: absolute source, destination within the block,
+// length.
 struct MatchRec {
   uint64_t S;
   uint32_t D;
