@@ -147,6 +147,11 @@ ace_status ace_index_build(const void *d_archive, uint64_t archive_bytes, const 
 /* Fills h_info from the host handle (no device access). */
 ace_status ace_index_info(const ace_index *idx, ace_info *h_info);
 
+/* Blocks per dependency level (Section 2's decode order), for the first
+ * min(n, n_levels) levels, into h_counts.  Synchronises s when the counts
+ * live only on the device (archives with more than 32 levels). */
+ace_status ace_index_levels(const ace_index *idx, uint32_t *h_counts, uint32_t n, cudaStream_t s);
+
 /* Releases the host handle; the caller frees the device buffers. */
 ace_status ace_index_free(ace_index *idx);
 

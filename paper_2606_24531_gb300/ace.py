@@ -70,6 +70,7 @@ _SIGS = {
     "ace_index_size": ([_vp, _u64, _P(_u64)], _i32),
     "ace_index_build": ([_vp, _u64, _vp, _u64, _vp, _u64, _vp, _P(_vp)], _i32),
     "ace_index_info": ([_vp, _P(ace_info)], _i32),
+    "ace_index_levels": ([_vp, _P(_u32), _u32, _vp], _i32),
     "ace_index_free": ([_vp], _i32),
     "ace_scratch_size": ([_vp, _u64, _P(_u64)], _i32),
     "ace_scratch_init": ([_vp, _vp, _u64, _vp], _i32),
@@ -192,6 +193,14 @@ def ace_index_build(d_archive, archive_bytes, h_header, d_index_mem, index_bytes
                                  _ptr(d_index_mem), index_bytes, _stream(stream), ctypes.byref(out)),
            "ace_index_build")
     return out
+
+
+def ace_index_levels(idx, n_levels, stream=None):
+    """Blocks per dependency level, as a numpy array of n_levels entries."""
+    out = np.zeros(max(n_levels, 1), np.uint32)
+    _check(lib().ace_index_levels(idx, out.ctypes.data_as(ctypes.POINTER(_u32)), n_levels, _stream(stream)),
+           "ace_index_levels")
+    return out[:n_levels]
 
 
 def ace_index_info(idx):

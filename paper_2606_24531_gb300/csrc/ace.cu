@@ -2110,6 +2110,20 @@ ace_status ace_index_info(const ace_index* idx, ace_info* info) {
   return ACE_OK;
 }
 
+ace_status ace_index_levels(const ace_index* idx, uint32_t* h_counts, uint32_t n, cudaStream_t s) {
+  if (!idx || (!h_counts && n)) return ACE_E_INVAL;
+  const uint32_t m = std::min(n, idx->n_levels);
+  if (!m) return ACE_OK;
+  if (idx->by_levels) {
+    for (uint32_t l = 0; l < m; l++) h_counts[l] = idx->level_start[l + 1] - idx->level_start[l];
+    return ACE_OK;
+  }
+  const IndexLayout L = index_layout(idx->h.n_blocks);
+  CUDA_TRY(cudaMemcpyAsync(h_counts, idx->d_mem + L.lv_count, 4ull * m, cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  return ACE_OK;
+}
+
 ace_status ace_index_set_tune(ace_index* idx, const ace_tune* tune) {
   if (!idx) return ACE_E_INVAL;
   if (tune && (tune->warps_per_cta > kMaxWarpsPerCta || (tune->chunk_tokens & 31) || tune->chunk_tokens > kMaxWindow))

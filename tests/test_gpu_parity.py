@@ -361,4 +361,7 @@ def test_levels_match_oracle():
         nb = da.info["n_blocks"]
         level = da.d_index[256:256 + 4 * nb].cpu().numpy().view(np.uint32)
         assert np.array_equal(level, lv)
+        n_lv = da.info["n_levels"]
+        counts = ace.ace_index_levels(da.idx, n_lv)
+        assert np.array_equal(counts, np.bincount(lv, minlength=n_lv)[:n_lv])
         da.close()
