@@ -25,7 +25,8 @@ class AceError(RuntimeError):
 
 class ace_encode_params(ctypes.Structure):
     _fields_ = [("log2_block", ctypes.c_uint32), ("min_match", ctypes.c_uint32),
-                ("threads", ctypes.c_uint32), ("max_chain", ctypes.c_uint32)]
+                ("threads", ctypes.c_uint32), ("max_chain", ctypes.c_uint32),
+                ("off_width", ctypes.c_uint32)]
 
 
 class ace_encode_stats(ctypes.Structure):
@@ -157,11 +158,11 @@ def ace_encode_bound(n, log2_block):
     return out.value
 
 
-def ace_encode(h_in, log2_block=14, min_match=4, threads=0, max_chain=16, stats=False):
+def ace_encode(h_in, log2_block=14, min_match=4, threads=0, max_chain=16, stats=False, off_width=0):
     """Encode host bytes (numpy uint8) into an archive (numpy uint8) on the
     CPU; with stats=True also return the parse statistics as a dict."""
     a = np.ascontiguousarray(h_in, dtype=np.uint8)
-    prm = ace_encode_params(log2_block, min_match, threads, max_chain)
+    prm = ace_encode_params(log2_block, min_match, threads, max_chain, off_width)
     enc, n = _vp(), _u64()
     _check(lib().ace_encode_run(a.ctypes.data, a.size, ctypes.byref(prm), ctypes.byref(enc),
                                 ctypes.byref(n)), "ace_encode_run")

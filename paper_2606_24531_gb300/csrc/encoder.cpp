@@ -418,7 +418,9 @@ ace_status ace_encode_run(const void* h_in, uint64_t n, const ace_encode_params*
   uint32_t max_level = kMaxLevel;
   uint64_t B = 1ull << prm->log2_block, nb = (n + B - 1) / B;
   if (nb > 0xFFFFFFFFull) return ACE_E_INVAL;
-  int w = n > (1ull << 32) ? 5 : 4;
+  if (prm->off_width != 0 && prm->off_width != 4 && prm->off_width != 5) return ACE_E_INVAL;
+  if (prm->off_width == 4 && n > (1ull << 32)) return ACE_E_INVAL;
+  int w = (n > (1ull << 32) || prm->off_width == 5) ? 5 : 4;
   ace_encoder* e = new (std::nothrow) ace_encoder();
   if (!e) return ACE_E_NOMEM;
   try {

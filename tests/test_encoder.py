@@ -54,3 +54,16 @@ def test_deterministic_across_thread_counts():
     a1 = ace.ace_encode(data, 14, 16, threads=1)
     a8 = ace.ace_encode(data, 14, 16, threads=8)
     assert np.array_equal(a1, a8)
+
+
+def test_five_byte_offsets_round_trip():
+    """Offsets are stored in 5 bytes above 2^32 bytes of input; the encoder can
+    force that width on small inputs so the path is covered without 4 GiB."""
+    data = synth.generate("mixed", 400_000, 5)
+    a4 = ace.ace_encode(data, 12, 4)
+    a5 = ace.ace_encode(data, 12, 4, off_width=5)
+    assert oracle.info(a4)["off_width"] == 4 and oracle.info(a5)["off_width"] == 5
+    assert np.array_equal(oracle.decode(a5), data)
+    assert np.array_equal(oracle.levels(a5), oracle.levels(a4))
+    with pytest.raises(Exception):
+        ace.ace_encode(data, 12, 4, off_width=3)

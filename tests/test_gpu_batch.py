@@ -76,3 +76,16 @@ def test_uneven_batch_4096_objects():
     assert db.sync() == ace.ACE_OK
     _check_all(db, datas)
     db.close()
+
+
+def test_batch_mixes_offset_widths():
+    """Archives with 4- and 5-byte offsets side by side in one launch."""
+    import synth
+    datas = [synth.generate(p, n, s) for p, n, s in
+             [("mixed", 300_000, 1), ("fastq", 200_000, 2), ("text", 150_001, 3), ("genome", 90_000, 4)]]
+    arcs = [ace.ace_encode(d, 12, 4, off_width=5 if i % 2 else 0) for i, d in enumerate(datas)]
+    db = DeviceBatch(arcs)
+    db.decode()
+    assert db.sync() == ace.ACE_OK
+    _check_all(db, datas)
+    db.close()

@@ -188,6 +188,29 @@ def test_seek_random_ranges():
     da.close()
 
 
+@pytest.mark.parametrize("log2b", [8, 12])
+def test_five_byte_offsets_decode_and_seek(log2b):
+    """5-byte absolute offsets (the width above 2^32 bytes), forced on a small
+    input: whole decode, separate passes, batched and plain seeks."""
+    data = synth.generate("mixed", 2_000_000 + 77, 40 + log2b)
+    arc = ace.ace_encode(data, log2b, 4, off_width=5)
+    assert oracle.info(arc)["off_width"] == 5
+    st, out = gpu_decode(arc)
+    assert st == ace.ACE_OK, ace.ace_status_str(st)
+    assert np.array_equal(out, data)
+    da = DeviceArchive(arc, max_seek_blocks=4096)
+    rng = np.random.default_rng(log2b)
+    n = data.size
+    cases = [(0, 1), (n - 1, 1), (n - 3000, 3000)]
+    cases += [(int(c), int(rng.integers(1, 200_000))) for c in rng.integers(0, n - 200_000, 12)]
+    for coord, length in cases:
+        s = da.seek(coord, length)
+        st = da.sync()
+        assert st == ace.ACE_OK, (coord, length, ace.ace_status_str(st))
+        assert np.array_equal(s.cpu().numpy(), data[coord:coord + length]), (coord, length)
+    da.close()
+
+
 def test_seek_closure_larger_than_scratch_reports_nomem():
     data = synth.generate("genome", 2_000_000, 4)
     arc = oracle.encode(data, 12, 4, 16)  # deep chains: long closures
