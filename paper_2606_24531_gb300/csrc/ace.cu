@@ -643,7 +643,7 @@ __device__ bool literal_block(const DecodeArgs& a, const LitMem& m, uint32_t b, 
           return obase + cur_dst + (i - cur_lit);
         };
         uint8_t* op = seek_token();
-        table_full_rounds<RING>(sl, m.ring, *m.lut, nfull, lane, lt, [&](uint32_t s) {
+        table_full_rounds<RING, 4>(sl, m.ring, *m.lut, nfull, lane, lt, [&](uint32_t s) {
           if (i >= nxt_lit) op = seek_token();
           *op = (uint8_t)s;
           op += 32;
@@ -675,8 +675,17 @@ constexpr uint32_t kLongUnroll = 2;
 constexpr uint32_t kShortMax = 32;
 constexpr uint32_t kLongMin = 512;
 
+// A load of match source bytes.  L1: through the SM's L1 cache, for a pass
+// whose sources were all written by earlier launches or by this warp (one
+// launch per dependency level); else at L2 only, which every SM sees
+// coherently (source blocks published by other warps of the same launch).
+template <bool L1, class T>
+__device__ __forceinline__ T ld_src(const T* p) {
+  return L1 ? __ldca(p) : __ldcg(p);
+}
+
 // Source of a short match: the aligned 8-byte words covering [S, S + len).
-template <bool SEEK>
+template <bool SEEK, bool L1>
 __device__ __forceinline__ void short_load(const DecodeArgs& a, uint64_t S, uint32_t len, uint64_t (&w)[5], uint64_t b,
                                            const uint8_t* obase) {
   const uint64_t a0 = S & ~7ull;
@@ -687,10 +696,10 @@ __device__ __forceinline__ void short_load(const DecodeArgs& a, uint64_t S, uint
     w[k] = 0;
     if (8 * k < off + len) {
       if (q + 8 <= a.total) {
-        w[k] = __ldcg(reinterpret_cast<const unsigned long long*>(Addr<SEEK>::at(a, q, b, obase)));
+        w[k] = ld_src<L1>(reinterpret_cast<const unsigned long long*>(Addr<SEEK>::at(a, q, b, obase)));
       } else {
         for (uint32_t t = 0; t < 8 && q + t < a.total; t++)
-          w[k] |= (uint64_t)__ldcg(Addr<SEEK>::at(a, q + t, b, obase)) << (8 * t);
+          w[k] |= (uint64_t)ld_src<L1>(Addr<SEEK>::at(a, q + t, b, obase)) << (8 * t);
       }
     }
   }
@@ -729,13 +738,14 @@ __device__ __forceinline__ void short_store(uint8_t* dp, uint32_t off, uint32_t 
 }
 
 // 16 bytes at p, bytes outside [lo, hi) read as zero.
+template <bool L1>
 __device__ __forceinline__ uint4 ld16_in(const uint8_t* p, const uint8_t* lo, const uint8_t* hi) {
-  if (p >= lo && p + 16 <= hi) return __ldcg(reinterpret_cast<const uint4*>(p));
+  if (p >= lo && p + 16 <= hi) return ld_src<L1>(reinterpret_cast<const uint4*>(p));
   uint4 v = make_uint4(0, 0, 0, 0);
 #pragma unroll 1
   for (uint32_t k = 0; k < 16; k++) {
     if (p + k < lo || p + k >= hi) continue;
-    const uint32_t x = (uint32_t)__ldcg(p + k) << (8 * (k & 3));
+    const uint32_t x = (uint32_t)ld_src<L1>(p + k) << (8 * (k & 3));
     if (k < 4) v.x |= x;
     else if (k < 8) v.y |= x;
     else if (k < 12) v.z |= x;
@@ -812,6 +822,9 @@ __device__ __forceinline__ uint32_t upper_bound(uint32_t n, uint32_t x, Key key)
 template <bool SEEK, bool WAIT>
 __device__ bool match_block(const DecodeArgs& a, MatchRec* gm, uint32_t b, uint32_t lane, uint32_t epoch,
                             uint32_t nm) {
+  // one launch per level: every source was written before the launch or by
+  // this warp, so source loads may go through L1
+  constexpr bool kL1 = !WAIT;
   bool ok = true, bad = false;
   const uint64_t B = (uint64_t)1 << a.log2B, bstart = (uint64_t)b << a.log2B;
   const uint32_t blen = (uint32_t)min(B, a.total - bstart);
@@ -932,10 +945,10 @@ __device__ bool match_block(const DecodeArgs& a, MatchRec* gm, uint32_t b, uint3
       if (sgo) {  // short: the next match's loads go out before the previous one's stores
         uint64_t cur[5], nxt[5];
         uint32_t jc = lane + 32 * (__ffs(sgo) - 1), rest = sgo & (sgo - 1);
-        short_load<SEEK>(a, gS[jc], gL[jc], cur, b, obase);
+        short_load<SEEK, kL1>(a, gS[jc], gL[jc], cur, b, obase);
         while (true) {
           const uint32_t jn = rest ? lane + 32 * (__ffs(rest) - 1) : 0u;
-          if (rest) short_load<SEEK>(a, gS[jn], gL[jn], nxt, b, obase);
+          if (rest) short_load<SEEK, kL1>(a, gS[jn], gL[jn], nxt, b, obase);
           short_store(obase + gD[jc], (uint32_t)(gS[jc] & 7), gL[jc], cur);
           if (!rest) break;
           rest &= rest - 1;
@@ -966,7 +979,7 @@ __device__ bool match_block(const DecodeArgs& a, MatchRec* gm, uint32_t b, uint3
           uint8_t* dpj = obase + gD[j];
           const uint8_t* s0 = a.out + gS[j] - (reinterpret_cast<uintptr_t>(dpj) & 15);
           const uint8_t* sal = s0 - (reinterpret_cast<uintptr_t>(s0) & 15);
-          return ld16_in(sal + 16ull * pc, a.out, a.out + a.total);
+          return ld16_in<kL1>(sal + 16ull * pc, a.out, a.out + a.total);
         };
         for (uint32_t c0 = 0; c0 < T; c0 += 32 * kLongUnroll) {
           uint4 A[kLongUnroll];
@@ -1045,7 +1058,7 @@ __device__ bool match_block(const DecodeArgs& a, MatchRec* gm, uint32_t b, uint3
             while (gX[jc + 1] <= p) jc++;
             const uint32_t i = p - gX[jc], ml = gL[jc];
             const uint64_t S = gS[jc], d = bstart + gD[jc] - S;
-            v[u] = __ldcg(Addr<SEEK>::at(a, src_index(S, d, ml, i), b, obase));
+            v[u] = ld_src<kL1>(Addr<SEEK>::at(a, src_index(S, d, ml, i), b, obase));
             dp[u] = obase + gD[jc] + i;
           }
         }
@@ -1171,6 +1184,188 @@ __global__ void __launch_bounds__(256, 2) match_level_kernel(DecodeArgs a) {
     it = nx;
     b = bn;
     nm = nmn;
+  }
+}
+
+// The match pass of a dependency level with few blocks, a CTA per block: a
+// warp per block would leave most of the GPU idle while each block's matches
+// resolve one round after another.  Every byte of the block gets a 16-bit
+// entry in shared memory: 0x8000 | its value once final (a literal, or a
+// match byte whose source lies in an earlier block, which the launches
+// before finished), else the in-block position it copies.  A match byte
+// equals the byte at its source, which precedes it (Section 2, the
+// sequential LZ77 copy), so the entries form chains that each end at a final
+// one; pointer jumping (every pending entry takes its target's entry) ends
+// all of them in at most log2(B) + 1 sweeps.  The block is then written back
+// with 16-byte stores.
+constexpr uint32_t kSmallThreads = 512;
+constexpr uint32_t kSmallMaxLog2B = 15;               // positions fit the entries' low 15 bits
+constexpr uint32_t kSmallSweeps = kSmallMaxLog2B + 2;  // log2(B) + 1, and one that sees no pending entry
+constexpr uint32_t kSmallUnroll = 8;                   // match bytes per lane with their loads in flight
+constexpr uint32_t kSmallLoads = 4;                    // 16-byte block loads per thread in flight
+
+// One warp's current 32 matches, laid end to end: match j's bytes start at X[j].
+struct SmallWarp {
+  uint64_t S[32];
+  uint32_t D[32], L[32], X[33];
+};
+
+__host__ __device__ constexpr size_t small_smem_bytes(uint32_t log2B) {
+  return ((size_t)2 << log2B) + (kSmallThreads / 32) * ((sizeof(SmallWarp) + 15) & ~(size_t)15);
+}
+
+__global__ void __launch_bounds__(kSmallThreads, 1) match_small_kernel(DecodeArgs a) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  const uint32_t tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  if (__syncthreads_or(*(volatile uint32_t*)&a.sh->status != 0)) return;  // the same answer for the whole CTA
+  const uint32_t b = __ldg(a.items + blockIdx.x);
+  const uint64_t B = 1ull << a.log2B, bstart = (uint64_t)b << a.log2B;
+  const uint32_t blen = (uint32_t)min(B, a.total - bstart);
+  uint8_t* obase = a.out + bstart;
+  uint16_t* e = reinterpret_cast<uint16_t*>(smem);
+  SmallWarp& w = *reinterpret_cast<SmallWarp*>(smem + (2ull << a.log2B) +
+                                               (size_t)wid * ((sizeof(SmallWarp) + 15) & ~(size_t)15));
+  const uint64_t m0 = __ldg(a.match_ptr + b), nm = __ldg(a.match_ptr + b + 1) - m0;
+  const uint4* rec = reinterpret_cast<const uint4*>(a.recs + m0);
+  bool bad = false;
+  // the warp's first 32 match records load with the block
+  uint4 rn = make_uint4(0, 0, 0, 0);
+  if (32ull * wid + lane < nm) rn = __ldg(rec + 32 * wid + lane);
+
+  // every byte final with what the literal pass left; match bytes are
+  // overwritten next.  16-byte loads, kSmallLoads per thread in flight
+  // (obase is block-aligned, and B is a multiple of 256).
+  for (uint32_t j0 = 16 * tid; j0 < blen; j0 += 16 * kSmallThreads * kSmallLoads) {
+    uint4 v[kSmallLoads];
+#pragma unroll
+    for (uint32_t u = 0; u < kSmallLoads; u++) {
+      const uint32_t j = j0 + 16 * kSmallThreads * u;
+      v[u] = make_uint4(0, 0, 0, 0);
+      if (j + 16 <= blen) {
+        v[u] = *reinterpret_cast<const uint4*>(obase + j);
+      } else if (j < blen) {
+        uint32_t x[4];
+#pragma unroll
+        for (uint32_t q = 0; q < 4; q++) {
+          x[q] = 0;
+#pragma unroll
+          for (uint32_t k = 0; k < 4; k++)
+            if (j + 4 * q + k < blen) x[q] |= (uint32_t)obase[j + 4 * q + k] << (8 * k);
+        }
+        v[u] = make_uint4(x[0], x[1], x[2], x[3]);
+      }
+    }
+#pragma unroll
+    for (uint32_t u = 0; u < kSmallLoads; u++) {
+      const uint32_t j = j0 + 16 * kSmallThreads * u;
+      if (j >= blen) continue;
+      uint4* e4 = reinterpret_cast<uint4*>(e + j);
+      e4[0] = make_uint4(__byte_perm(v[u].x, 0x80u, 0x4140), __byte_perm(v[u].x, 0x80u, 0x4342),
+                         __byte_perm(v[u].y, 0x80u, 0x4140), __byte_perm(v[u].y, 0x80u, 0x4342));
+      e4[1] = make_uint4(__byte_perm(v[u].z, 0x80u, 0x4140), __byte_perm(v[u].z, 0x80u, 0x4342),
+                         __byte_perm(v[u].w, 0x80u, 0x4140), __byte_perm(v[u].w, 0x80u, 0x4342));
+    }
+  }
+  __syncthreads();
+
+  // match bytes: each warp takes 32 matches at a time; a byte whose source is
+  // in an earlier block reads it (final), one whose source is in this block
+  // points there
+  for (uint64_t t0 = 32ull * wid; t0 < nm; t0 += kSmallThreads) {
+    const uint64_t t = t0 + lane;
+    const uint4 r = rn;
+    if (t + kSmallThreads < nm) rn = __ldg(rec + t + kSmallThreads);  // the next 32
+    uint32_t len = 0;
+    uint64_t k0 = 1, k1 = 0;  // the earlier blocks this lane's match reads (none)
+    if (t < nm) {
+      const uint64_t S = (uint64_t)r.x | ((uint64_t)r.y << 32);
+      const uint32_t D = r.z, ml = r.w;
+      if (ml && (S >= bstart + D || (uint64_t)D + ml > blen)) {
+        bad = true;  // a source must precede its destination, which stays in the block
+      } else if (ml) {
+        len = ml;
+        w.S[lane] = S;
+        w.D[lane] = D;
+        w.L[lane] = ml;
+        if ((S >> a.log2B) < b) {
+          const uint64_t rend = S + min((uint64_t)ml, bstart + D - S);
+          k0 = S >> a.log2B;
+          k1 = min((rend - 1) >> a.log2B, (uint64_t)b - 1);
+        }
+      }
+    }
+    const uint32_t incl = warp_incl_sum(len, lane);
+    w.X[lane] = incl - len;
+    if (lane == 31) w.X[32] = incl;
+    const uint32_t total = __shfl_sync(kFull, incl, 31);
+    __syncwarp();
+    uint32_t jc = 0;
+    for (uint32_t c = 0; c < total; c += 32 * kSmallUnroll) {
+      uint32_t val[kSmallUnroll], dst[kSmallUnroll];
+#pragma unroll
+      for (uint32_t u = 0; u < kSmallUnroll; u++) {
+        const uint32_t p = c + 32 * u + lane;
+        dst[u] = ~0u;
+        val[u] = 0;
+        if (p < total) {
+          while (w.X[jc + 1] <= p) jc++;
+          const uint32_t i = p - w.X[jc], ml = w.L[jc], D = w.D[jc];
+          const uint64_t S = w.S[jc];
+          const uint64_t src = src_index(S, bstart + D - S, ml, i);
+          dst[u] = D + i;
+          val[u] = src < bstart ? 0x8000u | ld_src<true>(a.out + src) : (uint32_t)(src - bstart);
+        }
+      }
+#pragma unroll
+      for (uint32_t u = 0; u < kSmallUnroll; u++)
+        if (dst[u] != ~0u) e[dst[u]] = (uint16_t)val[u];
+    }
+    // those earlier blocks (at most two) belong to lower levels: checked
+    // after the copies, which a corrupt archive fails whatever they wrote
+    for (uint64_t k = k0; k <= k1; k++)
+      if (__ldg(a.level + k) >= a.cur_level) bad = true;
+    __syncwarp();
+  }
+  if (__syncthreads_or(bad)) {
+    if (tid == 0) record_error(&a.sh->status, &a.sh->err_block, &a.sh->err_where, ACE_E_CORRUPT, b, 39);
+    return;
+  }
+
+  // pointer jumping; every target precedes its entry, so the sweeps end.
+  // Entries change while others read them: each read sees an entry of the
+  // same chain, old or new, and 16-bit shared stores do not tear.
+  volatile uint16_t* ev = e;
+  uint32_t sweep = 0;
+  for (; sweep < kSmallSweeps; sweep++) {
+    int pending = 0;
+    for (uint32_t j = tid; j < blen; j += kSmallThreads) {
+      const uint32_t x = ev[j];
+      if (!(x & 0x8000u)) {
+        const uint32_t y = ev[x];
+        ev[j] = (uint16_t)y;
+        pending |= !(y & 0x8000u);
+      }
+    }
+    if (!__syncthreads_or(pending)) break;
+  }
+  if (sweep == kSmallSweeps) {  // cannot happen for the chains above
+    if (tid == 0) record_error(&a.sh->status, &a.sh->err_block, &a.sh->err_where, ACE_E_CORRUPT, b, 42);
+    return;
+  }
+
+  // the block's bytes: the low byte of each entry
+  for (uint32_t j = 16 * tid; j < blen; j += 16 * kSmallThreads) {
+    const uint4 lo = *reinterpret_cast<const uint4*>(e + j), hi = *reinterpret_cast<const uint4*>(e + j + 8);
+    const uint4 v = make_uint4(__byte_perm(lo.x, lo.y, 0x6420), __byte_perm(lo.z, lo.w, 0x6420),
+                               __byte_perm(hi.x, hi.y, 0x6420), __byte_perm(hi.z, hi.w, 0x6420));
+    if (j + 16 <= blen) {
+      *reinterpret_cast<uint4*>(obase + j) = v;
+    } else {
+      for (uint32_t k = 0; j + k < blen; k++) {
+        const uint32_t x = k < 4 ? v.x : k < 8 ? v.y : k < 12 ? v.z : v.w;
+        obase[j + k] = (uint8_t)(x >> (8 * (k & 3)));
+      }
+    }
   }
 }
 
@@ -1738,6 +1933,7 @@ struct ace_index {
   // occupancy of the decode kernels, per (seek?, pass, warps per CTA, window)
   mutable int occ_cache[2][3][9][9];
   mutable int occ_level[9][9];  // the per-level match kernel
+  mutable bool small_attr = false;  // match_small_kernel allowed its shared memory
   // whole decodes resolve matches with one launch per level when there are
   // at most kMaxLevelLaunches levels: level L's blocks are
   // order[level_start[L] .. level_start[L + 1])
@@ -2208,12 +2404,23 @@ ace_status decode_all_passes(const ace_index* idx, uint32_t passes, void* d_out,
     const ace_tune t = tune ? *tune : idx->tune;
     if (t.ctas_per_sm && t.ctas_per_sm < per_sm) per_sm = t.ctas_per_sm;
     a.level = idx->d_level;
+    // levels of at most two blocks per SM: a CTA per block (match_small_kernel)
+    const bool small_ok = idx->h.log2_block <= kSmallMaxLog2B;
+    const size_t small_smem = small_smem_bytes(idx->h.log2_block);
+    if (small_ok && small_smem > 48 * 1024 && !idx->small_attr) {
+      CUDA_TRY(cudaFuncSetAttribute(match_small_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)small_smem));
+      idx->small_attr = true;
+    }
     for (uint32_t l = 0; l < idx->n_levels; l++) {
       const uint32_t n = idx->level_start[l + 1] - idx->level_start[l];
       if (!n) continue;
       a.items = idx->d_order + idx->level_start[l];
       a.n_items = n;
       a.cur_level = l;
+      if (small_ok && n <= 2 * idx->num_sms) {
+        match_small_kernel<<<n, kSmallThreads, small_smem, s>>>(a);
+        continue;
+      }
       const uint32_t grid = (uint32_t)std::min<uint64_t>((uint64_t)idx->num_sms * per_sm, (n + L.warps - 1) / L.warps);
       match_level_kernel<<<grid, 32 * L.warps, (size_t)L.warps * L.smem[PASS_MATCH], s>>>(a);
     }
