@@ -1204,14 +1204,24 @@ constexpr uint32_t kSmallSweeps = kSmallMaxLog2B + 2;  // log2(B) + 1, and one t
 constexpr uint32_t kSmallUnroll = 8;                   // match bytes per lane with their loads in flight
 constexpr uint32_t kSmallLoads = 4;                    // 16-byte block loads per thread in flight
 
-// One warp's current 32 matches, laid end to end: match j's bytes start at X[j].
-struct SmallWarp {
+// The CTA's current kSmallThreads matches (one record per thread), laid end
+// to end: match j's bytes start at X[j], X[kSmallThreads] is their total.
+struct __align__(16) SmallChunk {
+  uint64_t S[kSmallThreads];
+  uint32_t D[kSmallThreads], L[kSmallThreads], X[kSmallThreads + 1];
+  uint32_t wsum[kSmallThreads / 32];
+};
+
+// One warp's current 32 matches, laid end to end (blocks of many matches).
+struct __align__(16) SmallWarp {
   uint64_t S[32];
   uint32_t D[32], L[32], X[33];
 };
+static_assert(kSmallThreads / 32 * sizeof(SmallWarp) <= 2 * sizeof(SmallChunk), "warp arrays fit the chunks'");
 
+// Two chunks' arrays alternate, so a chunk needs no barrier after its copies.
 __host__ __device__ constexpr size_t small_smem_bytes(uint32_t log2B) {
-  return ((size_t)2 << log2B) + (kSmallThreads / 32) * ((sizeof(SmallWarp) + 15) & ~(size_t)15);
+  return ((size_t)2 << log2B) + 2 * ((sizeof(SmallChunk) + 15) & ~(size_t)15);
 }
 
 __global__ void __launch_bounds__(kSmallThreads, 1) match_small_kernel(DecodeArgs a) {
@@ -1223,14 +1233,14 @@ __global__ void __launch_bounds__(kSmallThreads, 1) match_small_kernel(DecodeArg
   const uint32_t blen = (uint32_t)min(B, a.total - bstart);
   uint8_t* obase = a.out + bstart;
   uint16_t* e = reinterpret_cast<uint16_t*>(smem);
-  SmallWarp& w = *reinterpret_cast<SmallWarp*>(smem + (2ull << a.log2B) +
-                                               (size_t)wid * ((sizeof(SmallWarp) + 15) & ~(size_t)15));
+  SmallChunk* const chunks = reinterpret_cast<SmallChunk*>(smem + (2ull << a.log2B));
+  static_assert(sizeof(SmallChunk) % 16 == 0, "chunk arrays stay 16-byte aligned");
   const uint64_t m0 = __ldg(a.match_ptr + b), nm = __ldg(a.match_ptr + b + 1) - m0;
   const uint4* rec = reinterpret_cast<const uint4*>(a.recs + m0);
   bool bad = false;
-  // the warp's first 32 match records load with the block
+  // the first chunk's match records load with the block
   uint4 rn = make_uint4(0, 0, 0, 0);
-  if (32ull * wid + lane < nm) rn = __ldg(rec + 32 * wid + lane);
+  if (tid < nm) rn = __ldg(rec + tid);
 
   // every byte final with what the literal pass left; match bytes are
   // overwritten next.  16-byte loads, kSmallLoads per thread in flight
@@ -1268,47 +1278,100 @@ __global__ void __launch_bounds__(kSmallThreads, 1) match_small_kernel(DecodeArg
   }
   __syncthreads();
 
-  // match bytes: each warp takes 32 matches at a time; a byte whose source is
-  // in an earlier block reads it (final), one whose source is in this block
-  // points there
-  for (uint64_t t0 = 32ull * wid; t0 < nm; t0 += kSmallThreads) {
-    const uint64_t t = t0 + lane;
+  // match bytes: a byte whose source is in an earlier block reads it
+  // (final), one whose source is in this block points there.  Blocks of at
+  // most kSmallThreads matches lay them end to end over the whole CTA (every
+  // thread on bytes tid, tid + kSmallThreads, ...); with more, each warp
+  // takes 32 at a time on its own, without CTA barriers between them.
+  if (nm > kSmallThreads) {
+    SmallWarp& ww = reinterpret_cast<SmallWarp*>(chunks)[wid];
+    for (uint64_t t0 = 32ull * wid; t0 < nm; t0 += kSmallThreads) {
+      const uint64_t t = t0 + lane;
+      const uint4 r = rn;
+      if (t + kSmallThreads < nm) rn = __ldg(rec + t + kSmallThreads);  // the warp's next 32
+      uint32_t len = 0;
+      if (t < nm) {
+        const uint64_t S = (uint64_t)r.x | ((uint64_t)r.y << 32);
+        const uint32_t D = r.z, ml = r.w;
+        if (ml && (S >= bstart + D || (uint64_t)D + ml > blen)) {
+          bad = true;
+        } else {
+          len = ml;
+        }
+        ww.S[lane] = S;
+        ww.D[lane] = D;
+      }
+      ww.L[lane] = len;
+      const uint32_t incl = warp_incl_sum(len, lane);
+      ww.X[lane] = incl - len;
+      if (lane == 31) ww.X[32] = incl;
+      const uint32_t total = __shfl_sync(kFull, incl, 31);
+      __syncwarp();
+      uint32_t jc = 0;  // the match of the lane's byte only moves forward
+      for (uint32_t c = 0; c < total; c += 32 * kSmallUnroll) {
+        uint32_t val[kSmallUnroll], dst[kSmallUnroll];
+#pragma unroll
+        for (uint32_t u = 0; u < kSmallUnroll; u++) {
+          const uint32_t p = c + 32 * u + lane;
+          dst[u] = ~0u;
+          val[u] = 0;
+          if (p < total) {
+            while (ww.X[jc + 1] <= p) jc++;
+            const uint32_t i = p - ww.X[jc], ml = ww.L[jc], D = ww.D[jc];
+            const uint64_t S = ww.S[jc];
+            const uint64_t src = src_index(S, bstart + D - S, ml, i);
+            dst[u] = D + i;
+            val[u] = src < bstart ? 0x8000u | ld_src<true>(a.out + src) : (uint32_t)(src - bstart);
+          }
+        }
+#pragma unroll
+        for (uint32_t u = 0; u < kSmallUnroll; u++)
+          if (dst[u] != ~0u) e[dst[u]] = (uint16_t)val[u];
+      }
+      __syncwarp();  // the warp's next 32 reuse its arrays
+    }
+  }
+  for (uint64_t c0 = 0; nm <= kSmallThreads && c0 < nm; c0 += kSmallThreads) {
+    SmallChunk& w = chunks[(c0 / kSmallThreads) & 1];
+    const uint64_t t = c0 + tid;
     const uint4 r = rn;
-    if (t + kSmallThreads < nm) rn = __ldg(rec + t + kSmallThreads);  // the next 32
+    if (t + kSmallThreads < nm) rn = __ldg(rec + t + kSmallThreads);  // the next chunk
     uint32_t len = 0;
-    uint64_t k0 = 1, k1 = 0;  // the earlier blocks this lane's match reads (none)
     if (t < nm) {
       const uint64_t S = (uint64_t)r.x | ((uint64_t)r.y << 32);
       const uint32_t D = r.z, ml = r.w;
       if (ml && (S >= bstart + D || (uint64_t)D + ml > blen)) {
         bad = true;  // a source must precede its destination, which stays in the block
-      } else if (ml) {
+      } else {
         len = ml;
-        w.S[lane] = S;
-        w.D[lane] = D;
-        w.L[lane] = ml;
-        if ((S >> a.log2B) < b) {
-          const uint64_t rend = S + min((uint64_t)ml, bstart + D - S);
-          k0 = S >> a.log2B;
-          k1 = min((rend - 1) >> a.log2B, (uint64_t)b - 1);
-        }
       }
+      w.S[tid] = S;
+      w.D[tid] = D;
     }
+    w.L[tid] = len;
+    // exclusive scan of the lengths over the CTA
     const uint32_t incl = warp_incl_sum(len, lane);
-    w.X[lane] = incl - len;
-    if (lane == 31) w.X[32] = incl;
-    const uint32_t total = __shfl_sync(kFull, incl, 31);
-    __syncwarp();
-    uint32_t jc = 0;
-    for (uint32_t c = 0; c < total; c += 32 * kSmallUnroll) {
+    if (lane == 31) w.wsum[wid] = incl;
+    __syncthreads();
+    uint32_t before = 0, total = 0;
+#pragma unroll
+    for (uint32_t k = 0; k < kSmallThreads / 32; k++) {
+      const uint32_t x = w.wsum[k];
+      before += k < wid ? x : 0u;
+      total += x;
+    }
+    w.X[tid] = before + incl - len;
+    if (tid == 0) w.X[kSmallThreads] = total;
+    __syncthreads();
+    for (uint32_t c = 0; c < total; c += kSmallThreads * kSmallUnroll) {
       uint32_t val[kSmallUnroll], dst[kSmallUnroll];
 #pragma unroll
       for (uint32_t u = 0; u < kSmallUnroll; u++) {
-        const uint32_t p = c + 32 * u + lane;
+        const uint32_t p = c + kSmallThreads * u + tid;
         dst[u] = ~0u;
         val[u] = 0;
         if (p < total) {
-          while (w.X[jc + 1] <= p) jc++;
+          const uint32_t jc = upper_bound(kSmallThreads + 1, p, [&](uint32_t i) { return w.X[i]; }) - 1;
           const uint32_t i = p - w.X[jc], ml = w.L[jc], D = w.D[jc];
           const uint64_t S = w.S[jc];
           const uint64_t src = src_index(S, bstart + D - S, ml, i);
@@ -1320,11 +1383,6 @@ __global__ void __launch_bounds__(kSmallThreads, 1) match_small_kernel(DecodeArg
       for (uint32_t u = 0; u < kSmallUnroll; u++)
         if (dst[u] != ~0u) e[dst[u]] = (uint16_t)val[u];
     }
-    // those earlier blocks (at most two) belong to lower levels: checked
-    // after the copies, which a corrupt archive fails whatever they wrote
-    for (uint64_t k = k0; k <= k1; k++)
-      if (__ldg(a.level + k) >= a.cur_level) bad = true;
-    __syncwarp();
   }
   if (__syncthreads_or(bad)) {
     if (tid == 0) record_error(&a.sh->status, &a.sh->err_block, &a.sh->err_where, ACE_E_CORRUPT, b, 39);
@@ -1366,6 +1424,22 @@ __global__ void __launch_bounds__(kSmallThreads, 1) match_small_kernel(DecodeArg
         obase[j + k] = (uint8_t)(x >> (8 * (k & 3)));
       }
     }
+  }
+
+  // the earlier blocks a match reads (at most two) belong to lower levels:
+  // checked last, since a corrupt archive fails the call whatever was written
+  for (uint64_t t = tid; t < nm; t += kSmallThreads) {
+    const uint4 r = __ldg(rec + t);
+    const uint64_t S = (uint64_t)r.x | ((uint64_t)r.y << 32);
+    const uint32_t D = r.z, ml = r.w;
+    if (!ml || (S >> a.log2B) >= b) continue;
+    const uint64_t rend = S + min((uint64_t)ml, bstart + D - S);
+    const uint64_t k1 = min((rend - 1) >> a.log2B, (uint64_t)b - 1);
+    for (uint64_t k = S >> a.log2B; k <= k1; k++)
+      if (__ldg(a.level + k) >= a.cur_level) {
+        record_error(&a.sh->status, &a.sh->err_block, &a.sh->err_where, ACE_E_CORRUPT, b, 39);
+        return;
+      }
   }
 }
 
@@ -2407,8 +2481,9 @@ ace_status decode_all_passes(const ace_index* idx, uint32_t passes, void* d_out,
     // levels of at most two blocks per SM: a CTA per block (match_small_kernel)
     const bool small_ok = idx->h.log2_block <= kSmallMaxLog2B;
     const size_t small_smem = small_smem_bytes(idx->h.log2_block);
-    if (small_ok && small_smem > 48 * 1024 && !idx->small_attr) {
-      CUDA_TRY(cudaFuncSetAttribute(match_small_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)small_smem));
+    if (small_ok && !idx->small_attr) {  // one value for every block size, so no index lowers another's
+      CUDA_TRY(cudaFuncSetAttribute(match_small_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)small_smem_bytes(kSmallMaxLog2B)));
       idx->small_attr = true;
     }
     for (uint32_t l = 0; l < idx->n_levels; l++) {
