@@ -1217,11 +1217,13 @@ struct __align__(16) SmallWarp {
   uint64_t S[32];
   uint32_t D[32], L[32], X[33];
 };
-static_assert(kSmallThreads / 32 * sizeof(SmallWarp) <= 2 * sizeof(SmallChunk), "warp arrays fit the chunks'");
-
-// Two chunks' arrays alternate, so a chunk needs no barrier after its copies.
+// The entries, then the chunk's or the warps' arrays (one or the other per
+// block): 43 KB for 16 KiB blocks, within the default shared-memory limit.
+constexpr size_t kSmallArrays = sizeof(SmallChunk) > kSmallThreads / 32 * sizeof(SmallWarp)
+                                    ? sizeof(SmallChunk)
+                                    : kSmallThreads / 32 * sizeof(SmallWarp);
 __host__ __device__ constexpr size_t small_smem_bytes(uint32_t log2B) {
-  return ((size_t)2 << log2B) + 2 * ((sizeof(SmallChunk) + 15) & ~(size_t)15);
+  return ((size_t)2 << log2B) + kSmallArrays;
 }
 
 __global__ void __launch_bounds__(kSmallThreads, 1) match_small_kernel(DecodeArgs a) {
@@ -1331,11 +1333,10 @@ __global__ void __launch_bounds__(kSmallThreads, 1) match_small_kernel(DecodeArg
       __syncwarp();  // the warp's next 32 reuse its arrays
     }
   }
-  for (uint64_t c0 = 0; nm <= kSmallThreads && c0 < nm; c0 += kSmallThreads) {
-    SmallChunk& w = chunks[(c0 / kSmallThreads) & 1];
-    const uint64_t t = c0 + tid;
+  if (nm <= kSmallThreads && nm) {  // one chunk
+    SmallChunk& w = chunks[0];
+    const uint64_t t = tid;
     const uint4 r = rn;
-    if (t + kSmallThreads < nm) rn = __ldg(rec + t + kSmallThreads);  // the next chunk
     uint32_t len = 0;
     if (t < nm) {
       const uint64_t S = (uint64_t)r.x | ((uint64_t)r.y << 32);
@@ -2481,7 +2482,7 @@ ace_status decode_all_passes(const ace_index* idx, uint32_t passes, void* d_out,
     // levels of at most two blocks per SM: a CTA per block (match_small_kernel)
     const bool small_ok = idx->h.log2_block <= kSmallMaxLog2B;
     const size_t small_smem = small_smem_bytes(idx->h.log2_block);
-    if (small_ok && !idx->small_attr) {  // one value for every block size, so no index lowers another's
+    if (small_ok && small_smem > 48 * 1024 && !idx->small_attr) {  // one value for every block size
       CUDA_TRY(cudaFuncSetAttribute(match_small_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)small_smem_bytes(kSmallMaxLog2B)));
       idx->small_attr = true;
