@@ -46,6 +46,17 @@ def test_decode_all_library_archives(profile, log2b):
     assert np.array_equal(out, data)
 
 
+@pytest.mark.parametrize("profile", ["text", "fastq"])
+def test_decode_all_32k_blocks(profile):
+    """32 KiB blocks: the largest that levels of few blocks resolve a block
+    per CTA (15-bit positions, shared memory above the default limit)."""
+    data = synth.generate(profile, 3_000_000 + 999, 77)
+    arc = ace.ace_encode(data, 15, MIN_MATCH[profile])
+    st, out = gpu_decode(arc)
+    assert st == ace.ACE_OK, ace.ace_status_str(st)
+    assert np.array_equal(out, data)
+
+
 @pytest.mark.parametrize("profile", ["mixed", "fastq", "genome", "text"])
 @pytest.mark.parametrize("log2b", [8, 14])
 def test_decode_all_oracle_archives(profile, log2b):
