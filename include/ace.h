@@ -182,14 +182,18 @@ typedef struct {
 } ace_tune;
 
 /*
- * Whole-archive decode through both layers (Sections 2-3), in three
- * persistent passes on s.  The token pass rANS-decodes every block's length
- * and offset streams and leaves one record per match (absolute source,
- * destination, length) in scratch; the literal pass decodes every block's
- * literal stream straight to its positions in d_out (out_bytes >=
- * total_size); the match pass resolves every block's absolute-offset matches
- * in (level, block) order, each level after the blocks its matches read.
- * tune may be NULL.  Asynchronous; check with ace_sync.
+ * Whole-archive decode through both layers (Sections 2-3), in three passes
+ * on s.  The token pass rANS-decodes every block's length and offset streams
+ * and leaves one record per match (absolute source, destination, length) in
+ * scratch; the literal pass decodes every block's literal stream straight to
+ * its positions in d_out (out_bytes >= total_size); both are persistent
+ * launches over the blocks.  The match pass resolves every block's
+ * absolute-offset matches, each level after the blocks its matches read:
+ * one launch per dependency level (a CTA per block for levels of at most two
+ * blocks per SM and blocks of at most 32 KiB, a warp per block otherwise),
+ * or, for archives of more than 32 levels, one persistent launch in (level,
+ * block) order with bounded waits on the source blocks.  tune may be NULL.
+ * Asynchronous; check with ace_sync.
  */
 ace_status ace_decode_all(const ace_index *idx, void *d_out, uint64_t out_bytes, void *d_scratch,
                           uint64_t scratch_bytes, const ace_tune *tune, cudaStream_t s);

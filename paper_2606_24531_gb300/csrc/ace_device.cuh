@@ -403,12 +403,19 @@ __device__ __forceinline__ uint32_t rans_round_full(Stream& st, uint8_t* ring, c
   lookup(st, lut, slot, s, f, c);
   uint32_t xn = f * (x >> ACE_SCALE_BITS) + slot - c;
   bool p1 = xn < ACE_RANS_L, p2 = xn < (1u << 15);
-  uint32_t b1 = __ballot_sync(kFull, p1), b2 = __ballot_sync(kFull, p2);
-  uint32_t p = st.pos + __popc(b1 & lt) + __popc(b2 & lt);
-  uint32_t c0 = ring[p & (RING - 1)], c1 = ring[(p + 1) & (RING - 1)];
-  uint32_t x1 = (xn << 8) | c0, x2 = (x1 << 8) | c1;
-  st.x = p2 ? x2 : (p1 ? x1 : xn);
-  st.pos += __popc(b1) + __popc(b2);
+  uint32_t b1 = __ballot_sync(kFull, p1);
+  if (!__any_sync(kFull, p2)) {
+    uint32_t c0 = ring[(st.pos + __popc(b1 & lt)) & (RING - 1)];
+    st.x = p1 ? ((xn << 8) | c0) : xn;
+    st.pos += __popc(b1);
+  } else {
+    uint32_t b2 = __ballot_sync(kFull, p2);
+    uint32_t p = st.pos + __popc(b1 & lt) + __popc(b2 & lt);
+    uint32_t c0 = ring[p & (RING - 1)], c1 = ring[(p + 1) & (RING - 1)];
+    uint32_t x1 = (xn << 8) | c0, x2 = (x1 << 8) | c1;
+    st.x = p2 ? x2 : (p1 ? x1 : xn);
+    st.pos += __popc(b1) + __popc(b2);
+  }
   st.next += 32;
   return s;
 }
@@ -449,42 +456,54 @@ __device__ __forceinline__ uint32_t table_round(uint32_t& x, uint32_t& pos, cons
   const uint32_t fc = lut.fc[s];
   const uint32_t xn = (fc >> 16) * (x >> ACE_SCALE_BITS) + slot - (fc & 0xffffu);
   const bool p1 = xn < ACE_RANS_L, p2 = xn < (1u << 15);
-  const uint32_t b1 = __ballot_sync(kFull, p1), b2 = __ballot_sync(kFull, p2);
-  const uint32_t p = pos + __popc(b1 & lt) + __popc(b2 & lt);
-  const uint32_t c0 = ring[p & (RING - 1)], c1 = ring[(p + 1) & (RING - 1)];
-  const uint32_t x1 = (xn << 8) | c0, x2 = (x1 << 8) | c1;
-  x = p2 ? x2 : (p1 ? x1 : xn);
-  pos += __popc(b1) + __popc(b2);
+  const uint32_t b1 = __ballot_sync(kFull, p1);
+  if (!__any_sync(kFull, p2)) {  // no state takes two bytes (most rounds): one read per lane
+    const uint32_t p = pos + __popc(b1 & lt);
+    const uint32_t c0 = ring[p & (RING - 1)];
+    x = p1 ? ((xn << 8) | c0) : xn;
+    pos += __popc(b1);
+  } else {
+    const uint32_t b2 = __ballot_sync(kFull, p2);
+    const uint32_t p = pos + __popc(b1 & lt) + __popc(b2 & lt);
+    const uint32_t c0 = ring[p & (RING - 1)], c1 = ring[(p + 1) & (RING - 1)];
+    const uint32_t x1 = (xn << 8) | c0, x2 = (x1 << 8) | c1;
+    x = p2 ? x2 : (p1 ? x1 : xn);
+    pos += __popc(b1) + __popc(b2);
+  }
   return s;
 }
 
 // nfull full rounds in slot-table mode from a round boundary (st.next a
 // multiple of 32), handing each round's symbol to emit(s) in order.  The ring
-// is checked once per two rounds: a round reads at most 64 bytes, and after a
-// check the position is less than one segment into the ring, whose two oldest
-// segments have landed.
-template <uint32_t RING = kRing, class Emit>
+// is checked once per U rounds (U = 2 or 4): a round reads at most 64 bytes,
+// so U rounds after a check, which leaves the position less than one segment
+// into the ring, stay inside its first 1 + U / 2 segments; the check lets at
+// most RING / 128 - 1 - U / 2 segment fills stay in flight, and runs once
+// more at the end.
+template <uint32_t RING = kRing, uint32_t U = 2, class Emit>
 __device__ __forceinline__ void table_full_rounds(Stream& st, uint8_t* ring, const Lut& lut, uint32_t nfull,
                                                   uint32_t lane, uint32_t lt, Emit&& emit) {
+  static_assert(U == 2 || U == 4, "two or four rounds per ring check");
   uint32_t x = st.x, pos = st.pos, base = st.base;
   auto check = [&]() {
-    if (pos >= base + kSeg) {
+    while (pos >= base + kSeg) {
       ring_issue<RING>(st, ring, base + RING, lane);
       base += kSeg;
-      cp_async_wait<RING / kSeg - 2>();
+      cp_async_wait<RING / kSeg - 1 - U / 2>();
       __syncwarp();
     }
   };
   uint32_t r = 0;
-  for (; r + 2 <= nfull; r += 2) {
+  for (; r + U <= nfull; r += U) {
+    check();
+#pragma unroll
+    for (uint32_t u = 0; u < U; u++) emit(table_round<RING>(x, pos, ring, lut, lt));
+  }
+  for (; r < nfull; r++) {
     check();
     emit(table_round<RING>(x, pos, ring, lut, lt));
-    emit(table_round<RING>(x, pos, ring, lut, lt));
   }
-  if (r < nfull) {
-    check();
-    emit(table_round<RING>(x, pos, ring, lut, lt));
-  }
+  check();  // the single-round decoders that follow expect less than one segment consumed
   st.x = x;
   st.pos = pos;
   st.base = base;
