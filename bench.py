@@ -146,6 +146,15 @@ def make_workload(name, limit=None):
     return data, arc, stats
 
 
+def max_over_ranks(x, dist, device):
+    """The largest of every rank's x (the job's step time is its slowest rank's)."""
+    import torch
+
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def run_reference(args, rank):
     """The oracle (plain sequential C decoder) on the host cores."""
     if rank != 0:
@@ -256,9 +265,7 @@ def main():
     ms_median = statistics.median(times)
     ms_pass = [statistics.mean(e[p].elapsed_time(e[p + 1]) for e in ev) for p in range(3)]
     if dist:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+        ms = max_over_ranks(ms, dist, dev)
     value = world * total / (ms / 1e3) / 1e9
 
     peaks, peak_kind = measured_peaks()
@@ -437,6 +444,8 @@ def main():
         for sl in slots:
             e2e_finish(sl)
         torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
         t0 = time.perf_counter()
         for k in range(n_e2e):
             if k >= depth:
@@ -445,6 +454,8 @@ def main():
         for k in range(max(0, n_e2e - depth), n_e2e):
             e2e_finish(slots[k % depth])
         e2e_s = (time.perf_counter() - t0) / n_e2e
+        if dist:
+            e2e_s = max_over_ranks(e2e_s, dist, dev)
         for sl in slots:
             assert np.array_equal(sl["h_out"].numpy()[:4096], data[:4096])
             assert np.array_equal(sl["h_out"].numpy()[-4096:], data[-4096:])
