@@ -62,7 +62,7 @@ typedef struct {
     uint32_t min_match;  /* shortest match taken, >= 4 */
     uint32_t threads;    /* host threads; 0 = all hardware threads */
     uint32_t max_chain;  /* candidates tried per position in the in-block chain */
-    uint32_t off_width;  /* absolute-offset bytes: 0 = 4, or 5 above 2^32 bytes; 5 forces 5 */
+    uint32_t off_width;  /* absolute-offset bytes: 0 = 4 up to 2^32 input bytes, else 5; 5 forces 5; 4 above 2^32 is ACE_E_INVAL */
 } ace_encode_params;
 
 /*

@@ -160,7 +160,9 @@ def ace_encode_bound(n, log2_block):
 
 def ace_encode(h_in, log2_block=14, min_match=4, threads=0, max_chain=16, stats=False, off_width=0):
     """Encode host bytes (numpy uint8) into an archive (numpy uint8) on the
-    CPU; with stats=True also return the parse statistics as a dict."""
+    CPU; with stats=True also return the parse statistics as a dict.
+    off_width: absolute-offset bytes, 0 for the smallest that fits (4 up to
+    2^32 bytes of input, else 5), or 5 to force five."""
     a = np.ascontiguousarray(h_in, dtype=np.uint8)
     prm = ace_encode_params(log2_block, min_match, threads, max_chain, off_width)
     enc, n = _vp(), _u64()
