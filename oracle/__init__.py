@@ -55,6 +55,7 @@ def _L():
         lib.oracle_encode_bound.argtypes = [u64, u32]
         lib.oracle_encode_bound.restype = u64
         lib.oracle_encode.argtypes = [vp, u64, u32, u32, u32, vp, u64, vp]
+        lib.oracle_encode_adaptive.argtypes = [vp, u64, u32, u32, u32, u32, vp, u64, vp]
         lib.oracle_info.argtypes = [vp, u64, vp, vp, vp, vp]
         lib.oracle_decode.argtypes = [vp, u64, vp, u64]
         lib.oracle_decode_block_tokens.argtypes = [vp, u64, u64, vp, vp, vp, u32, vp]
@@ -62,6 +63,7 @@ def _L():
         lib.oracle_closure.argtypes = [vp, u64, u64, u64, vp]
         lib.oracle_seek.argtypes = [vp, u64, u64, u64, vp]
         for f in ("oracle_rans_freqs", "oracle_rans_encode", "oracle_rans_decode", "oracle_encode",
+                  "oracle_encode_adaptive",
                   "oracle_info", "oracle_decode", "oracle_decode_block_tokens", "oracle_levels",
                   "oracle_closure", "oracle_seek"):
             getattr(lib, f).restype = i32
@@ -124,14 +126,15 @@ def rans_decode(data, states, freq, n):
     return out[:n]
 
 
-def encode(data, log2_block=14, min_match=4, max_chain=64):
-    """Encode bytes into an archive (uint8 array)."""
+def encode(data, log2_block=14, min_match=4, max_chain=64, adaptive=False):
+    """Encode bytes into an archive (uint8 array); adaptive stores each
+    stream that rANS would not shrink."""
     a = _u8(data)
     cap = _L().oracle_encode_bound(a.size, log2_block)
     arc = np.zeros(cap, np.uint8)
     n = ctypes.c_uint64(0)
-    _check(_L().oracle_encode(_p(a), a.size, log2_block, min_match, max_chain, _p(arc), cap,
-                              ctypes.byref(n)), "encode")
+    _check(_L().oracle_encode_adaptive(_p(a), a.size, log2_block, min_match, max_chain, int(adaptive),
+                                       _p(arc), cap, ctypes.byref(n)), "encode")
     return arc[:n.value].copy()
 
 

@@ -12,12 +12,16 @@
  *   directory, 64 bytes per block: u64 stream_off[3] (relative to
  *     payload_off), u32 stream_bytes[3], u32 nsym[3], u32 ntok, u32 nesc,
  *     u8 mode[3], 5 zero bytes.  Stream 0 = literals, 1 = lengths,
- *     2 = absolute offsets.
+ *     2 = absolute offsets.  mode 0: rANS-coded; mode 1: stored, the
+ *     stream's symbols verbatim (stream_bytes = nsym), for streams that
+ *     rANS would not shrink (Section 4: entropy coding applied per stream,
+ *     measured at encode time).
  *   dependencies: u32 dep_ptr[n_blocks+1], then u32 (first, last) block
  *     pairs: the maximal runs of earlier blocks each block's matches read.
  *   payload: per non-empty stream, 16-byte aligned: u32 states[32],
  *     32-byte present-symbol bitmap, u16 freq per present symbol (ascending
- *     symbol order, zero-padded to a multiple of 16 bytes), renorm bytes.
+ *     symbol order, zero-padded to a multiple of 16 bytes), renorm bytes
+ *     (mode 0), or the symbols themselves (mode 1).
  * Token streams of a block:
  *   literals: the literal bytes in output order;
  *   lengths:  first nesc u16 escape values, then two one-byte codes per token
@@ -364,6 +368,19 @@ uint64_t oracle_encode_bound(uint64_t n, uint32_t log2_block)
 int oracle_encode(const uint8_t *in, uint64_t n, uint32_t log2_block, uint32_t min_match,
                   uint32_t max_chain, uint8_t *arc, uint64_t cap, uint64_t *arc_len)
 {
+    return oracle_encode_adaptive(in, n, log2_block, min_match, max_chain, 0, arc, cap, arc_len);
+}
+
+/*
+ * As oracle_encode; with adaptive set, each stream of each block is stored
+ * verbatim (mode 1) when its rANS coding would take at least as many bytes
+ * as its symbols (Section 4: whether entropy coding pays is data-dependent,
+ * so it is decided per stream at encode time).
+ */
+int oracle_encode_adaptive(const uint8_t *in, uint64_t n, uint32_t log2_block, uint32_t min_match,
+                           uint32_t max_chain, uint32_t adaptive, uint8_t *arc, uint64_t cap,
+                           uint64_t *arc_len)
+{
     if (log2_block < 8 || log2_block > 16 || min_match < 4) return ORC_E_INVAL;
     uint64_t B = 1ull << log2_block, nb = (n + B - 1) / B;
     int w = n > (1ull << 32) ? 5 : 4;
@@ -453,10 +470,17 @@ int oracle_encode(const uint8_t *in, uint64_t n, uint32_t log2_block, uint32_t m
             uint64_t nbytes = 0;
             pos = align16(pos);
             rc = write_stream(st[k]->d, st[k]->n, arc + pos, cap - pos, &nbytes);
+            uint8_t mode = 0; /* rANS */
+            if (rc == ORC_OK && adaptive && st[k]->n && nbytes >= st[k]->n) {
+                memcpy(arc + pos, st[k]->d, st[k]->n); /* stored: rANS did not shrink it */
+                memset(arc + pos + st[k]->n, 0, nbytes - st[k]->n);
+                nbytes = st[k]->n;
+                mode = 1;
+            }
             wr(dir + 8 * k, pos - payload_off, 8);
             wr(dir + 24 + 4 * k, nbytes, 4);
             wr(dir + 36 + 4 * k, st[k]->n, 4);
-            dir[56 + k] = 0; /* mode 0: rANS */
+            dir[56 + k] = mode;
             pos += nbytes;
         }
         wr(dir + 48, tl->ntok, 4);
@@ -541,12 +565,18 @@ static int read_stream(const uint8_t *arc, const header_t *h, uint64_t b, int k,
     uint64_t off = h->payload_off + rd(dir + 8 * k, 8);
     uint32_t nbytes = (uint32_t)rd(dir + 24 + 4 * k, 4);
     uint32_t n = (uint32_t)rd(dir + 36 + 4 * k, 4);
-    if (dir[56 + k] != 0) return ORC_E_CORRUPT; /* only rANS streams exist */
+    const uint8_t mode = dir[56 + k];
+    if (mode > 1) return ORC_E_CORRUPT; /* 0: rANS, 1: stored */
     uint8_t *sym = malloc(n ? n : 1);
     if (!sym) return ORC_E_NOMEM;
     *sym_out = sym;
     *nsym_out = n;
     if (n == 0) return nbytes == 0 ? ORC_OK : ORC_E_CORRUPT;
+    if (mode == 1) { /* stored: the bytes are the symbols */
+        if (nbytes != n || off + nbytes > h->arc_bytes) return ORC_E_CORRUPT;
+        memcpy(sym, arc + off, n);
+        return ORC_OK;
+    }
     if (off + nbytes > h->arc_bytes || nbytes < 160) return ORC_E_CORRUPT;
     const uint8_t *p = arc + off;
     uint32_t states[32];

@@ -21,6 +21,9 @@
  *   LZ layer        pinned: brute-force round trip, longest-match check,
  *                   source-reproduces-destination check
  *   whole archive   pinned: decode equals the regenerated original
+ *   stored streams  pinned: adaptive archives decode to the original, and a
+ *                   stream is stored exactly when its rANS coding is no
+ *                   smaller (checked against the rANS-only archive)
  *   seek            pinned: slice equals the original slice
  *   printed hashes  parity unpinned: the paper's FASTQ data (Section 5) is
  *                   not available, so its FNV values cannot be reproduced
@@ -55,6 +58,9 @@ int oracle_rans_decode(const uint8_t *bytes, uint32_t nbytes, const uint32_t sta
 uint64_t oracle_encode_bound(uint64_t n, uint32_t log2_block);
 int oracle_encode(const uint8_t *in, uint64_t n, uint32_t log2_block, uint32_t min_match,
                   uint32_t max_chain, uint8_t *arc, uint64_t cap, uint64_t *arc_len);
+int oracle_encode_adaptive(const uint8_t *in, uint64_t n, uint32_t log2_block, uint32_t min_match,
+                           uint32_t max_chain, uint32_t adaptive, uint8_t *arc, uint64_t cap,
+                           uint64_t *arc_len);
 int oracle_info(const uint8_t *arc, uint64_t arc_len, uint64_t *total, uint32_t *block_size,
                 uint64_t *n_blocks, uint32_t *off_width);
 int oracle_decode(const uint8_t *arc, uint64_t arc_len, uint8_t *out, uint64_t out_cap);
