@@ -258,10 +258,24 @@ void parse_block(const uint8_t* in, uint64_t n, uint64_t b, uint64_t bstart, uin
     for (uint64_t k = lo; k < hi; k++) w = std::max<uint32_t>(w, ps.wave[k - bstart]);
     return w + 1;
   };
+  // the global table and the sources it names are random accesses: the
+  // table slot of the key kAhead positions past the newest one looked up is
+  // prefetched, and half as far ahead the slot is read and its source line
+  // prefetched, so both are cached when the position is parsed
+  constexpr uint64_t kAhead = 16;
+  auto key_ok = [&](uint64_t x) { return g.bits && x + kKey <= n; };
   uint64_t p = bstart;
   uint32_t lit = 0;
   while (p < bend) {
     insert_upto(p);
+    {
+      const uint64_t xa = p + kStride - 1 + 2 * kAhead, xb = p + kStride - 1 + kAhead;
+      if (key_ok(xa)) __builtin_prefetch(&g.table[hash_key(in + xa, g.bits)]);
+      if (key_ok(xb)) {
+        const uint64_t qq = g.table[hash_key(in + xb, g.bits)];
+        if (qq != kEmpty && qq >= kStride) __builtin_prefetch(in + qq - kStride);
+      }
+    }
     uint64_t best_len = 0, best_q = 0;
     uint32_t best_w = 0;
     uint64_t room = bend - p;
@@ -296,11 +310,17 @@ void parse_block(const uint8_t* in, uint64_t n, uint64_t b, uint64_t bstart, uin
           consider(q, common(in + q, in + p, room));
         }
       }
+      uint64_t tried[kStride];
+      int nt = 0;
       for (int j = 0; j < kStride; j++) {  // earliest occurrence anywhere before p
         uint64_t qq = global_at(p + (uint64_t)j);
         if (qq == kEmpty || qq < (uint64_t)j) continue;
         uint64_t q = qq - (uint64_t)j;
         if (q >= p) continue;
+        bool seen = false;  // keys of one earlier occurrence name the same source
+        for (int t = 0; t < nt; t++) seen |= tried[t] == q;
+        if (seen) continue;
+        tried[nt++] = q;
         uint64_t l = common(in + q, in + p, room);
         if (q < bstart) l = al.span(q, b, l);
         consider(q, l);
