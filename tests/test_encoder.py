@@ -67,3 +67,35 @@ def test_five_byte_offsets_round_trip():
     assert np.array_equal(oracle.levels(a5), oracle.levels(a4))
     with pytest.raises(Exception):
         ace.ace_encode(data, 12, 4, off_width=3)
+
+
+@pytest.mark.parametrize("profile,mm,log2b", [("fastq", 16, 14), ("genome", 20, 12), ("text", 4, 10)])
+def test_stats_behind_the_roofline(profile, mm, log2b):
+    """The parse statistics that the benchmark's algorithmic bytes come from,
+    recounted from the oracle's decode of each block's tokens: matches,
+    literal bytes, matched bytes, and the source bytes a match reads
+    (min(length, distance): an overlapping match re-reads its own output),
+    plus the level count."""
+    data = synth.generate(profile, 600_000, 17)
+    arc, st = ace.ace_encode(data, log2b, mm, stats=True)
+    B = 1 << log2b
+    nb = oracle.info(arc)["n_blocks"]
+    toks = matches = lits = mbytes = src_bytes = 0
+    for b in range(nb):
+        lr, ml, src = oracle.block_tokens(arc, b)
+        dst = b * B
+        for t in range(len(lr)):
+            dst += int(lr[t])
+            if ml[t]:
+                matches += 1
+                mbytes += int(ml[t])
+                src_bytes += min(int(ml[t]), dst - int(src[t]))
+            dst += int(ml[t])
+        toks += len(lr)
+        lits += int(lr.sum())
+    assert st["n_tokens"] == toks
+    assert st["n_matches"] == matches
+    assert st["literal_bytes"] == lits
+    assert st["match_bytes"] == mbytes and lits + mbytes == data.size
+    assert st["match_src_bytes"] == src_bytes
+    assert st["n_levels"] == int(oracle.levels(arc).max()) + 1
