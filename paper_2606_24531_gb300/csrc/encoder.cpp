@@ -252,10 +252,25 @@ void parse_block(const uint8_t* in, uint64_t n, uint64_t b, uint64_t bstart, uin
   // kMaxWave are refused, and a shallower candidate within max(4, len/8)
   // bytes of the longest is preferred, so chains of match on match stay
   // short.  A source overlapping its own destination reads only [q, p).
+  // Waves are 0..3, so the largest over a range is read from two bit tests
+  // on the bytes, eight at a time: some byte 3 (both bits), else some byte
+  // with bit 1 (a 2), else any non-zero byte (a 1).
   auto wave_of = [&](uint64_t q, uint64_t len, uint64_t p) -> uint32_t {
+    static_assert(kMaxWave <= 3, "waves fit two bits");
     uint64_t lo = std::max(q, bstart), hi = std::min(q + len, p);
-    uint32_t w = 0;
-    for (uint64_t k = lo; k < hi; k++) w = std::max<uint32_t>(w, ps.wave[k - bstart]);
+    const uint8_t* wv = ps.wave.data() - bstart;
+    uint64_t any = 0, three = 0, k = lo;
+    for (; k + 8 <= hi; k += 8) {
+      const uint64_t x = load64(wv + k);
+      any |= x;
+      three |= x & (x >> 1);
+    }
+    for (; k < hi; k++) {
+      const uint64_t x = wv[k];
+      any |= x;
+      three |= x & (x >> 1);
+    }
+    const uint32_t w = (three & 0x0101010101010101ull) ? 3u : (any & 0x0202020202020202ull) ? 2u : any ? 1u : 0u;
     return w + 1;
   };
   // the global table and the sources it names are random accesses: the
