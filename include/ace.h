@@ -173,37 +173,54 @@ ace_status ace_scratch_init(const ace_index *idx, void *d_scratch, uint64_t scra
 
 /* ------------------------------------------------------------ decoding */
 
+/* How a decode is laid out in launches.
+ * ACE_SCHEDULE_PASSES: three passes -- tokens (length and offset streams
+ * into match records) and literals as persistent launches over the blocks,
+ * then the match pass, one launch per dependency level.
+ * ACE_SCHEDULE_FUSED: one persistent launch.  Each warp takes a block in
+ * (level, block) order and decodes its entropy layer, then holds the
+ * block's matches until every block of the lower levels is resolved,
+ * taking further blocks meanwhile (at most four held), so the entropy
+ * decode of some warps overlaps the match copies of others.
+ * ACE_SCHEDULE_AUTO (0): the library's choice, currently the passes.
+ * Seek batches through a block cache always run the passes; plain seeks
+ * take the fused schedule only for archives of at most 32 levels. */
+enum { ACE_SCHEDULE_AUTO = 0, ACE_SCHEDULE_PASSES = 1, ACE_SCHEDULE_FUSED = 2 };
+
 typedef struct {
     uint32_t warps_per_cta;   /* 1..8; 0 = default (4) */
     uint32_t ctas_per_sm;     /* 0 = as many as fit */
     uint32_t chunk_tokens;    /* tokens staged per step, 32..256, multiple of 32; 0 = 128 */
-    uint32_t reserved;
+    uint32_t schedule;        /* ACE_SCHEDULE_*; 0 = automatic; others: ACE_E_INVAL */
     uint64_t wait_timeout_ns; /* bound on each device-side wait; 0 = 2 s */
 } ace_tune;
 
 /*
- * Whole-archive decode through both layers (Sections 2-3), in three passes
- * on s.  The token pass rANS-decodes every block's length and offset streams
- * and leaves one record per match (absolute source, destination, length) in
- * scratch; the literal pass decodes every block's literal stream straight to
- * its positions in d_out (out_bytes >= total_size); both are persistent
- * launches over the blocks.  The match pass resolves every block's
- * absolute-offset matches, each level after the blocks its matches read:
- * one launch per dependency level (a CTA per block for levels of at most two
- * blocks per SM and blocks of at most 32 KiB, a warp per block otherwise),
- * or, for archives of more than 32 levels, one persistent launch in (level,
- * block) order with bounded waits on the source blocks.  tune may be NULL.
- * Asynchronous; check with ace_sync.
+ * Whole-archive decode through both layers (Sections 2-3) into d_out
+ * (out_bytes >= total_size), on s.  Each block's length and offset streams
+ * are rANS-decoded into one record per match (absolute source, destination,
+ * length), its literal stream is decoded straight to its positions in
+ * d_out, and its absolute-offset matches are resolved once the blocks they
+ * read are present (Section 2).  The pass schedule (the default) runs three
+ * passes: tokens and literals as persistent launches over the blocks, then
+ * the match pass one launch per dependency level (a CTA per block for levels
+ * of at most two blocks per SM and blocks of at most 32 KiB, a warp per
+ * block otherwise), or, for archives of more than 32 levels, one persistent
+ * launch in (level, block) order with bounded waits on source blocks' ready
+ * flags.  ACE_SCHEDULE_FUSED does all of it in one persistent launch.
+ * A source block whose level is not below its reader's makes the call
+ * report ACE_E_CORRUPT.  tune may be NULL.  Asynchronous; check with
+ * ace_sync.
  */
 ace_status ace_decode_all(const ace_index *idx, void *d_out, uint64_t out_bytes, void *d_scratch,
                           uint64_t scratch_bytes, const ace_tune *tune, cudaStream_t s);
 
 /*
- * The passes of ace_decode_all as separate calls, so that a caller can time
- * each one with events on s: ACE_PASS_TOKENS (which also resets the call's
- * status), ACE_PASS_LITERALS, then ACE_PASS_MATCH, same arguments, same
- * stream; together they are exactly ace_decode_all.  Any other pass value:
- * ACE_E_INVAL.
+ * The passes of ace_decode_all's pass schedule as separate calls, so that a
+ * caller can time each one with events on s: ACE_PASS_TOKENS (which also
+ * resets the call's status), ACE_PASS_LITERALS, then ACE_PASS_MATCH, same
+ * arguments, same stream; together they are exactly ace_decode_all with
+ * ACE_SCHEDULE_PASSES.  Any other pass value: ACE_E_INVAL.
  */
 enum { ACE_PASS_TOKENS = 0, ACE_PASS_LITERALS = 1, ACE_PASS_MATCH = 2 };
 ace_status ace_decode_pass(const ace_index *idx, int pass, void *d_out, uint64_t out_bytes, void *d_scratch,

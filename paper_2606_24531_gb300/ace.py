@@ -15,6 +15,7 @@ from . import build as _build
 
 ACE_OK, ACE_E_INVAL, ACE_E_CORRUPT, ACE_E_RANGE, ACE_E_NOMEM, ACE_E_TIMEOUT, ACE_E_CUDA = range(7)
 ACE_PASS_TOKENS, ACE_PASS_LITERALS, ACE_PASS_MATCH = 0, 1, 2
+ACE_SCHEDULE_AUTO, ACE_SCHEDULE_PASSES, ACE_SCHEDULE_FUSED = 0, 1, 2
 
 
 class AceError(RuntimeError):
@@ -45,7 +46,7 @@ class ace_info(ctypes.Structure):
 
 class ace_tune(ctypes.Structure):
     _fields_ = [("warps_per_cta", ctypes.c_uint32), ("ctas_per_sm", ctypes.c_uint32),
-                ("chunk_tokens", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
+                ("chunk_tokens", ctypes.c_uint32), ("schedule", ctypes.c_uint32),
                 ("wait_timeout_ns", ctypes.c_uint64)]
 
 
@@ -228,8 +229,8 @@ def ace_scratch_init(idx, d_scratch, scratch_bytes, stream=None):
 
 # ------------------------------------------------------------------ decoding
 
-def make_tune(warps_per_cta=0, ctas_per_sm=0, chunk_tokens=0, wait_timeout_ns=0):
-    return ace_tune(warps_per_cta, ctas_per_sm, chunk_tokens, 0, wait_timeout_ns)
+def make_tune(warps_per_cta=0, ctas_per_sm=0, chunk_tokens=0, wait_timeout_ns=0, schedule=0):
+    return ace_tune(warps_per_cta, ctas_per_sm, chunk_tokens, schedule, wait_timeout_ns)
 
 
 def ace_decode_all(idx, d_out, out_bytes, d_scratch, scratch_bytes, tune=None, stream=None):

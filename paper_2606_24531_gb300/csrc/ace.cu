@@ -259,6 +259,7 @@ struct DecodeArgs {
   ScratchHdr* sh;
   uint32_t* ready;         // per block: the epoch once the block is decoded
   const uint32_t* slot_of; // seek: block -> slot
+  uint32_t n_slots;        // seek: slots in the call's scratch (every slot_of entry read is checked against it)
   uint8_t* slice;          // seek: caller's output
   uint64_t coord, len;     // seek: requested range
   uint64_t timeout_ns;
@@ -266,9 +267,14 @@ struct DecodeArgs {
   uint64_t warp_scratch_bytes;
   MatchRec* recs;          // match records, from the token pass to the literal and match passes
   const uint64_t* match_ptr;  // whole decode: block -> first record; null: max_ntok records per slot
-  const uint32_t* level;   // whole decode by levels: each block's dependency level
+  const uint32_t* level;   // each block's dependency level
   uint32_t cur_level;      // whole decode by levels: the level this launch resolves
   bool closure_flags;      // seek: the closure marked its blocks' ready flags (kPendingFlag)
+  // fused schedule: per level the blocks whose matches are resolved, and
+  // (whole decodes) the blocks the level holds (seeks read them from the
+  // scratch header)
+  uint32_t* lv_done;
+  const uint32_t* lv_count;
 };
 
 // Shared memory of one warp in the token pass: one stream's tables at a
@@ -341,14 +347,23 @@ __device__ inline TokRec tok_records(uint8_t* base, uint64_t max_ntok) {
   return r;
 }
 
+// Slot of block k in a seek's scratch.  The entry is read back from scratch
+// that earlier calls may have left in another state, so it is clamped to the
+// call's slots: whatever it holds, the address stays inside the scratch (a
+// block outside the call's closure is rejected before its bytes are used).
+__device__ __forceinline__ uint32_t slot_index(const DecodeArgs& a, uint64_t k) {
+  const uint32_t s = __ldg(a.slot_of + k);
+  return s < a.n_slots ? s : 0u;
+}
+__device__ __forceinline__ uint64_t slot_base(const DecodeArgs& a, uint64_t k) {
+  return (uint64_t)slot_index(a, k) << a.log2B;
+}
+
 template <bool SEEK>
 struct Addr {
   // device address of absolute output position p
   __device__ __forceinline__ static const uint8_t* at(const DecodeArgs& a, uint64_t p) {
-    if (SEEK) {
-      uint64_t k = p >> a.log2B;
-      return a.out + ((uint64_t)__ldg(a.slot_of + k) << a.log2B) + (p & ((1ull << a.log2B) - 1));
-    }
+    if (SEEK) return a.out + slot_base(a, p >> a.log2B) + (p & ((1ull << a.log2B) - 1));
     return a.out + p;
   }
   // the same, with block b's own bytes at obase without a slot lookup
@@ -357,7 +372,7 @@ struct Addr {
       uint64_t k = p >> a.log2B;
       const uint64_t off = p & ((1ull << a.log2B) - 1);
       if (k == b) return obase + off;
-      return a.out + ((uint64_t)__ldg(a.slot_of + k) << a.log2B) + off;
+      return a.out + slot_base(a, k) + off;
     }
     return a.out + p;
   }
@@ -387,7 +402,7 @@ __device__ __forceinline__ uint64_t read_src(const uint8_t* q, uint32_t w) {
 template <bool SEEK>
 __device__ __forceinline__ MatchRec* recs_of(const DecodeArgs& a, uint32_t b) {
   if (!SEEK) return a.recs + __ldg(a.match_ptr + b);
-  return a.recs + (uint64_t)__ldg(a.slot_of + b) * a.max_ntok;
+  return a.recs + (uint64_t)slot_index(a, b) * a.max_ntok;
 }
 
 // n bytes from src to dst by one warp: 16-byte vectors, four per lane in
@@ -561,7 +576,7 @@ __device__ bool literal_block(const DecodeArgs& a, const LitMem& m, uint32_t b, 
   const uint32_t blen = (uint32_t)min(B, a.total - bstart);
   const uint32_t ntok = __shfl_sync(kFull, dv, 12);
   const uint32_t nm = ntok ? ntok - 1 : 0;
-  uint8_t* obase = SEEK ? a.out + ((uint64_t)__ldg(a.slot_of + b) << a.log2B) : a.out + bstart;
+  uint8_t* obase = SEEK ? a.out + slot_base(a, b) : a.out + bstart;
   const uint32_t lt = lanemask_lt();
   Stream sl;
   {
@@ -819,16 +834,18 @@ __device__ __forceinline__ uint32_t upper_bound(uint32_t n, uint32_t x, Key key)
 // are final after the literal pass.  The first pending match is always ready,
 // so every round makes progress, and a round's ready matches read no byte
 // another one writes.  Returns false if a record is corrupt or a wait gave up.
-template <bool SEEK, bool WAIT>
+template <bool SEEK, bool WAIT, bool L1 = !WAIT>
 __device__ bool match_block(const DecodeArgs& a, MatchRec* gm, uint32_t b, uint32_t lane, uint32_t epoch,
-                            uint32_t nm) {
-  // one launch per level: every source was written before the launch or by
-  // this warp, so source loads may go through L1
-  constexpr bool kL1 = !WAIT;
+                            uint32_t nm, uint32_t lvl = 0) {
+  // L1: every source was written before the launch or by this warp (one
+  // launch per level), so source loads may go through L1; otherwise other
+  // SMs wrote them during the launch and loads go to L2.  Without WAIT, lvl
+  // is the block's level: its sources must lie in lower ones.
+  constexpr bool kL1 = L1;
   bool ok = true, bad = false;
   const uint64_t B = (uint64_t)1 << a.log2B, bstart = (uint64_t)b << a.log2B;
   const uint32_t blen = (uint32_t)min(B, a.total - bstart);
-  uint8_t* obase = SEEK ? a.out + ((uint64_t)__ldg(a.slot_of + b) << a.log2B) : a.out + bstart;
+  uint8_t* obase = SEEK ? a.out + slot_base(a, b) : a.out + bstart;
   const uint4* rec = reinterpret_cast<const uint4*>(recs_of<SEEK>(a, b));
   uint64_t* gS = reinterpret_cast<uint64_t*>(gm);                 // [kMatchGroup] sources
   uint32_t* gD = reinterpret_cast<uint32_t*>(gS + kMatchGroup);   // [kMatchGroup] destinations in the block
@@ -900,6 +917,10 @@ __device__ bool match_block(const DecodeArgs& a, MatchRec* gm, uint32_t b, uint3
     }
     if (WAIT) {
       bool timeout = false;
+      // a source block must sit at a lower dependency level (work lists are
+      // in level order, so it was handed out before this block and the wait
+      // ends); the block cache keeps no levels and skips this check
+      const uint32_t my_level = a.level ? __ldg(a.level + b) : 0u;
 #pragma unroll
       for (uint32_t q = 0; q < kLaneMatches; q++) {
         if (!(ext >> q & 1)) continue;
@@ -907,11 +928,27 @@ __device__ bool match_block(const DecodeArgs& a, MatchRec* gm, uint32_t b, uint3
         const uint64_t S = gS[j], D = bstart + gD[j];
         const uint64_t rend = S + min((uint64_t)gL[j], D - S);
         const uint64_t k0 = S >> a.log2B, k1 = min((rend - 1) >> a.log2B, (uint64_t)b - 1);
+        if (a.level) {
+          bool low = true;
+          for (uint64_t k = k0; k <= k1; k++) low &= __ldg(a.level + k) < my_level;
+          if (!low) {
+            bad = true;  // the dependency table disagrees with the matches
+            continue;
+          }
+        }
+        if (SEEK && a.closure_flags) {
+          // every source block must be a member of this seek's closure: its
+          // flag carries the call's epoch (pending or published).  Anything
+          // else means the dependency table disagrees with the matches.
+          bool member = (f0[q] & ~kPendingFlag) == epoch && (f1[q] & ~kPendingFlag) == epoch;
+          for (uint64_t k = k0 + 1; member && k < k1; k++)
+            member = (ld_relaxed(a.ready + k) & ~kPendingFlag) == epoch;
+          if (!member) {
+            bad = true;
+            continue;
+          }
+        }
         if (f0[q] == epoch && f1[q] == epoch && k1 <= k0 + 1) continue;  // blocks between them: the bounded wait
-      if (SEEK && a.closure_flags && ((f0[q] & ~kPendingFlag) != epoch || (f1[q] & ~kPendingFlag) != epoch)) {
-        bad = true;  // a source block outside the seek's closure
-        continue;
-      }
         for (uint64_t k = k0; k <= k1 && !timeout; k++)
           if (!wait_flag(a.ready + k, epoch, a.timeout_ns, &a.sh->status)) timeout = true;
       }
@@ -1073,13 +1110,13 @@ __device__ bool match_block(const DecodeArgs& a, MatchRec* gm, uint32_t b, uint3
 #pragma unroll
       for (uint32_t q = 0; q < kLaneMatches; q++) {
         if (!(chk >> q & 1)) continue;
-        if (f0[q] >= a.cur_level || f1[q] >= a.cur_level) bad = true;
+        if (f0[q] >= lvl || f1[q] >= lvl) bad = true;
         const uint32_t j = lane + 32 * q;
         const uint64_t S = gS[j], D = bstart + gD[j];
         const uint64_t rend = S + min((uint64_t)gL[j], D - S);
         const uint64_t k0 = S >> a.log2B, k1 = min((rend - 1) >> a.log2B, (uint64_t)b - 1);
         for (uint64_t k = k0 + 1; k < k1; k++)  // a source spanning more than two earlier blocks
-          if (__ldg(a.level + k) >= a.cur_level) bad = true;
+          if (__ldg(a.level + k) >= lvl) bad = true;
       }
       if (__any_sync(kFull, bad)) fail(a, ok, ACE_E_CORRUPT, b, 39, lane);
       __syncwarp();
@@ -1094,10 +1131,15 @@ __device__ bool match_block(const DecodeArgs& a, MatchRec* gm, uint32_t b, uint3
 // PASS_MATCH resolves blocks in (level, block) order with bounded waits on
 // their source blocks (match_level_kernel resolves one level of a whole
 // decode without them).
-enum { PASS_TOKENS = 0, PASS_LITERALS = 1, PASS_MATCH = 2 };
+// PASS_FUSED runs all three for one block in one warp, block after block:
+// tokens, then literals, then matches with bounded waits on the source
+// blocks' flags, then the block's publication.  One launch covers the whole
+// decode, so the issue-bound entropy decode of some warps overlaps the
+// latency-bound match copies of others on the same SM.
+enum { PASS_TOKENS = 0, PASS_LITERALS = 1, PASS_MATCH = 2, PASS_FUSED = 3 };
 
 // Registers per thread allowed by each pass's launch bounds (256 threads).
-#define ACE_PASS_MIN_CTAS(P) ((P) == PASS_TOKENS ? 4 : (P) == PASS_LITERALS ? 4 : 2)
+#define ACE_PASS_MIN_CTAS(P) ((P) == PASS_TOKENS ? 4 : (P) == PASS_LITERALS ? 4 : (P) == PASS_FUSED ? 4 : 2)
 
 // The match pass keeps only its match-record area in shared memory.
 constexpr uint32_t kMatchSmem = 20 * kMatchGroup + 16;
@@ -1107,6 +1149,143 @@ __device__ __forceinline__ void publish(uint32_t* ready, uint32_t b, uint32_t ep
   __threadfence();
   __syncwarp();
   if (lane == 0) st_release(ready + b, epoch);
+}
+
+// Blocks level l of a fused call holds (whole decode: the index's level
+// histogram; seek: the closure's level ranges in the scratch header).
+template <bool SEEK>
+__device__ __forceinline__ uint32_t level_size(const DecodeArgs& a, uint32_t l) {
+  if (SEEK) return *(volatile uint32_t*)&a.sh->lv_start[l + 1] - *(volatile uint32_t*)&a.sh->lv_start[l];
+  return __ldg(a.lv_count + l);
+}
+
+// The work of one archive (whole decode or seek): its list, in level order.
+template <bool SEEK>
+struct ArchiveJobs {
+  const DecodeArgs& a;
+  __device__ const DecodeArgs& job(uint32_t v, uint32_t& b) const {
+    b = __ldg(a.items + v);
+    return a;
+  }
+  __device__ uint32_t below(const DecodeArgs& x, uint32_t L) const { return level_size<SEEK>(x, L - 1); }
+};
+
+// Deferred match jobs a warp holds at most; warps per CTA at most.
+constexpr uint32_t kDeferred = 4;
+constexpr uint32_t kMaxWarps = 8;
+
+// The fused schedule (Section 2's rule, a block decodes once the blocks its
+// matches read are present, applied inside one launch).  Warps take blocks
+// from the level-ordered list.  For each one a warp first decodes the
+// entropy layer (length, offset and literal streams; literals placed at
+// their output positions), then defers the block's match job until every
+// block of the lower levels has its matches resolved (the level counters).
+// A warp resolves its oldest deferred block as soon as that holds, and takes
+// a new block while it waits, up to kDeferred held; so issue-bound entropy
+// decode and latency-bound match copies of different warps share each SM
+// and no warp idles while there is entropy work left.  With kDeferred held,
+// or no blocks left, it waits (bounded, giving up on any recorded error).
+// This always ends: the earliest unresolved block of the list has every
+// lower level resolved (they come before it), and it is the oldest block of
+// the warp holding it.
+template <bool SEEK, class Jobs>
+__device__ void fused_loop(const Jobs& jobs, ScratchHdr* sh, uint32_t n_items, uint64_t timeout_ns, uint8_t* wsm,
+                           uint8_t* wreg, uint32_t lane, uint32_t epoch, uint32_t window, uint32_t max_ntok) {
+  uint32_t* const ticket = &sh->ticket;
+  const TokRec g = tok_records(wreg, max_ntok);
+  constexpr uint32_t ring = SEEK ? kSeekRing : kRing;
+  // list positions of the warp's deferred blocks, a ring in shared memory
+  // (registers are the scarce resource here): q[(q0 + k) % kDeferred]
+  __shared__ uint32_t qs[kMaxWarps][kDeferred];
+  uint32_t* const q = qs[threadIdx.x >> 5];
+  uint32_t q0 = 0, nq = 0;
+  bool more = true;  // blocks may remain in the list
+  while (true) {
+    if (*(volatile uint32_t*)&sh->status) break;
+    if (nq) {
+      uint32_t b;
+      auto&& a = jobs.job(q[q0], b);
+      const uint32_t L = __ldg(a.level + b);
+      const uint32_t need = L ? jobs.below(a, L) : 0u;
+      bool rdy = true;
+      if (lane == 0 && L) rdy = ld_acquire(a.lv_done + L - 1) == need;
+      rdy = __shfl_sync(kFull, rdy, 0);
+      if (rdy || nq == kDeferred || !more) {
+        if (!rdy) {  // nothing else to do: wait, bounded
+          uint32_t ok = 1;
+          if (lane == 0) {
+            const uint64_t t0 = globaltimer();
+            uint32_t ns = 32;
+            while (ld_acquire(a.lv_done + L - 1) != need) {
+              if (*(volatile uint32_t*)&sh->status) {
+                ok = 0;
+                break;
+              }
+              if (globaltimer() - t0 > timeout_ns) {
+                record_error(&sh->status, &sh->err_block, &sh->err_where, ACE_E_TIMEOUT, b, 38);
+                ok = 0;
+                break;
+              }
+              __nanosleep(ns);
+              if (ns < 1024) ns <<= 1;
+            }
+          }
+          if (!__shfl_sync(kFull, ok, 0)) break;
+        }
+        // The bytes of the blocks below were written by other SMs.  Source
+        // loads may still go through L1: a block's bytes are written by the
+        // one warp that holds it, and read by other warps only after the
+        // acquire below has seen its level complete, so no SM can hold an
+        // older copy of them.
+        fence_acquire();
+        const uint32_t ntok = __ldg(reinterpret_cast<const uint32_t*>(a.dir + b) + 12);
+        bool ok;
+        if (SEEK) {
+          // source blocks must be members of the closure; published ones
+          // carry the epoch without the pending bit, so the flag checks do
+          // not wait
+          ok = match_block<true, true, true>(a, reinterpret_cast<MatchRec*>(wsm), b, lane, epoch,
+                                             ntok ? ntok - 1 : 0);
+          if (ok && a.slice) {
+            uint64_t bs = (uint64_t)b << a.log2B, be = min(bs + ((uint64_t)1 << a.log2B), a.total);
+            uint64_t lo = max(bs, a.coord), hi = min(be, a.coord + a.len);
+            const uint8_t* src = a.out + slot_base(a, b) - bs;
+            if (hi > lo) warp_copy(a.slice + (lo - a.coord), src + lo, hi - lo, lane);
+          }
+          if (ok) publish(a.ready, b, epoch, lane);
+        } else {
+          ok = match_block<false, false, true>(a, reinterpret_cast<MatchRec*>(wsm), b, lane, epoch,
+                                               ntok ? ntok - 1 : 0, L);
+        }
+        if (!ok) break;  // the error is recorded; every warp stops
+        __threadfence();
+        __syncwarp();
+        if (lane == 0) atomicAdd(a.lv_done + L, 1u);
+        q0 = (q0 + 1) % kDeferred;
+        nq--;
+        continue;
+      }
+    }
+    if (!more) {
+      if (!nq) break;
+      continue;
+    }
+    uint32_t u = 0;
+    if (lane == 0) u = atomicAdd(ticket, 1u);
+    u = __shfl_sync(kFull, u, 0);
+    if (u >= n_items) {
+      more = false;
+      continue;
+    }
+    uint32_t b;
+    auto&& a = jobs.job(u, b);
+    bool ok = token_block<SEEK>(a, carve_tok(wsm), g, b, lane);
+    if (ok) ok = literal_block<SEEK, ring>(a, carve_lit(wsm, window, ring), b, lane);
+    if (!ok) break;
+    if (lane == 0) q[(q0 + nq) % kDeferred] = u;
+    __syncwarp();
+    nq++;
+  }
 }
 
 // One pass over a work list by persistent warps: the token pass decodes every
@@ -1122,8 +1301,13 @@ __global__ void __launch_bounds__(256, ACE_PASS_MIN_CTAS(PASS)) decode_kernel(De
   const uint32_t n_items = SEEK ? *(volatile uint32_t*)&a.sh->n_work : a.n_items;
   // the literal and match passes run only after every block's tokens decoded
   if (PASS != PASS_TOKENS && *(volatile uint32_t*)&a.sh->status) return;
-  uint32_t* ticket = PASS == PASS_TOKENS ? &a.sh->ticket : PASS == PASS_LITERALS ? &a.sh->ticket2 : &a.sh->ticket3;
   uint8_t* wsm = smem + (size_t)wid * a.warp_smem;
+  if (PASS == PASS_FUSED) {
+    uint8_t* wreg = a.warp_scratch + (size_t)(blockIdx.x * (blockDim.x >> 5) + wid) * a.warp_scratch_bytes;
+    fused_loop<SEEK>(ArchiveJobs<SEEK>{a}, a.sh, n_items, a.timeout_ns, wsm, wreg, lane, epoch, a.window, a.max_ntok);
+    return;
+  }
+  uint32_t* ticket = PASS == PASS_TOKENS ? &a.sh->ticket : PASS == PASS_LITERALS ? &a.sh->ticket2 : &a.sh->ticket3;
   while (true) {
     uint32_t it = 0;
     if (lane == 0) it = atomicAdd(ticket, 1u);
@@ -1147,7 +1331,7 @@ __global__ void __launch_bounds__(256, ACE_PASS_MIN_CTAS(PASS)) decode_kernel(De
       // copy the part of this block inside [coord, coord + len) to the caller
       uint64_t bs = (uint64_t)b << a.log2B, be = min(bs + ((uint64_t)1 << a.log2B), a.total);
       uint64_t lo = max(bs, a.coord), hi = min(be, a.coord + a.len);
-      const uint8_t* src = a.out + ((uint64_t)a.slot_of[b] << a.log2B) - bs;
+      const uint8_t* src = a.out + slot_base(a, b) - bs;
       if (hi > lo) warp_copy(a.slice + (lo - a.coord), src + lo, hi - lo, lane);
     }
     publish(a.ready, b, epoch, lane);
@@ -1179,7 +1363,7 @@ __global__ void __launch_bounds__(256, 2) match_level_kernel(DecodeArgs a) {
       bn = __ldg(a.items + nx);
       nmn = n_matches(bn);
     }
-    match_block<false, false>(a, gm, b, lane, 0, nm);
+    match_block<false, false>(a, gm, b, lane, 0, nm, a.cur_level);
     if (nx >= a.n_items) break;
     it = nx;
     b = bn;
@@ -1455,8 +1639,11 @@ struct ObjDesc {
   uint8_t* out;
   uint32_t* ready;
   const uint32_t* order;  // the archive's blocks in (level, block) order
+  const uint32_t* level;  // each block's dependency level
   MatchRec* recs;         // the archive's match records
   const uint64_t* match_ptr;
+  uint32_t* lv_done;         // fused schedule: blocks of each level with matches resolved
+  const uint32_t* lv_count;  // blocks per level
   uint32_t log2B, w, nb, pad;
 };
 
@@ -1471,49 +1658,81 @@ struct BatchArgs {
   uint64_t warp_scratch_bytes;
 };
 
+// The work of a batch: (archive, block) items, each archive's blocks in its
+// own level order.
+struct BatchJobs {
+  const BatchArgs& ba;
+  __device__ uint32_t obj_of(uint32_t it) const {
+    uint32_t lo = 0, hi = ba.n_objs;  // the archive o with item_start[o] <= it < item_start[o + 1]
+    while (hi - lo > 1) {
+      const uint32_t mid = (lo + hi) >> 1;
+      if (__ldg(ba.item_start + mid) <= it) lo = mid;
+      else hi = mid;
+    }
+    return lo;
+  }
+  __device__ DecodeArgs job(uint32_t v, uint32_t& b) const;
+  __device__ uint32_t below(const DecodeArgs& x, uint32_t L) const { return __ldg(x.lv_count + L - 1); }
+};
+
 // Thousands of independent archives in one persistent launch per pass:
 // warps take (archive, block) items from one ticket; each archive's items
 // are in its own (level, block) order, so in the match pass a warp only
 // ever waits on blocks of its archive that were handed out before its own.
+__device__ DecodeArgs batch_args(const BatchArgs& ba, const ObjDesc& od) {
+  DecodeArgs a{};
+  a.arc = od.arc;
+  a.dir = od.dir;
+  a.payload_off = od.payload_off;
+  a.total = od.total;
+  a.nb = od.nb;
+  a.log2B = od.log2B;
+  a.w = od.w;
+  a.window = ba.window;
+  a.esc_cap = ba.esc_cap;
+  a.warp_smem = ba.warp_smem;
+  a.max_ntok = ba.max_ntok;
+  a.out = od.out;
+  a.sh = ba.sh;
+  a.ready = od.ready;
+  a.timeout_ns = ba.timeout_ns;
+  a.recs = od.recs;
+  a.match_ptr = od.match_ptr;
+  a.level = od.level;
+  a.lv_done = od.lv_done;
+  a.lv_count = od.lv_count;
+  return a;
+}
+
+__device__ DecodeArgs BatchJobs::job(uint32_t v, uint32_t& b) const {
+  const uint32_t o = obj_of(v);
+  const ObjDesc od = ba.objs[o];
+  b = __ldg(od.order + (v - __ldg(ba.item_start + o)));
+  return batch_args(ba, od);
+}
+
 template <int PASS>
 __global__ void __launch_bounds__(256, ACE_PASS_MIN_CTAS(PASS)) batch_decode_kernel(BatchArgs ba) {
   extern __shared__ __align__(16) uint8_t smem[];
   const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  if (PASS != PASS_TOKENS && *(volatile uint32_t*)&ba.sh->status) return;
+  if (PASS != PASS_TOKENS && PASS != PASS_FUSED && *(volatile uint32_t*)&ba.sh->status) return;
   uint8_t* wsm = smem + (size_t)wid * ba.warp_smem;
   const uint32_t epoch = *(volatile uint32_t*)&ba.sh->epoch;
+  if (PASS == PASS_FUSED) {
+    uint8_t* wreg = ba.warp_scratch + (size_t)(blockIdx.x * (blockDim.x >> 5) + wid) * ba.warp_scratch_bytes;
+    fused_loop<false>(BatchJobs{ba}, ba.sh, ba.n_items, ba.timeout_ns, wsm, wreg, lane, epoch, ba.window,
+                      ba.max_ntok);
+    return;
+  }
   uint32_t* ticket = PASS == PASS_TOKENS ? &ba.sh->ticket : PASS == PASS_LITERALS ? &ba.sh->ticket2 : &ba.sh->ticket3;
+  const BatchJobs jobs{ba};
   while (true) {
     uint32_t it = 0;
     if (lane == 0) it = atomicAdd(ticket, 1u);
     it = __shfl_sync(kFull, it, 0);
     if (it >= ba.n_items) break;
-    uint32_t lo = 0, hi = ba.n_objs;  // the archive o with item_start[o] <= it < item_start[o + 1]
-    while (hi - lo > 1) {
-      uint32_t mid = (lo + hi) >> 1;
-      if (__ldg(ba.item_start + mid) <= it) lo = mid;
-      else hi = mid;
-    }
-    const ObjDesc od = ba.objs[lo];
-    DecodeArgs a{};
-    a.arc = od.arc;
-    a.dir = od.dir;
-    a.payload_off = od.payload_off;
-    a.total = od.total;
-    a.nb = od.nb;
-    a.log2B = od.log2B;
-    a.w = od.w;
-    a.window = ba.window;
-    a.esc_cap = ba.esc_cap;
-    a.warp_smem = ba.warp_smem;
-    a.max_ntok = ba.max_ntok;
-    a.out = od.out;
-    a.sh = ba.sh;
-    a.ready = od.ready;
-    a.timeout_ns = ba.timeout_ns;
-    a.recs = od.recs;
-    a.match_ptr = od.match_ptr;
-    uint32_t b = __ldg(od.order + (it - __ldg(ba.item_start + lo)));
+    uint32_t b;
+    const DecodeArgs a = jobs.job(it, b);
     if (PASS == PASS_TOKENS) {
       TokRec g = tok_records(ba.warp_scratch + (size_t)(blockIdx.x * (blockDim.x >> 5) + wid) * ba.warp_scratch_bytes,
                              ba.max_ntok);
@@ -1523,7 +1742,7 @@ __global__ void __launch_bounds__(256, ACE_PASS_MIN_CTAS(PASS)) batch_decode_ker
     } else {
       const uint32_t ntok = __ldg(reinterpret_cast<const uint32_t*>(a.dir + b) + 12);
       match_block<false, true>(a, reinterpret_cast<MatchRec*>(wsm), b, lane, epoch, ntok ? ntok - 1 : 0);
-      publish(od.ready, b, epoch, lane);
+      publish(a.ready, b, epoch, lane);
     }
   }
 }
@@ -1545,6 +1764,7 @@ struct ClosureArgs {
   const uint32_t* level; // by levels: each block's dependency level (else null)
   uint32_t n_levels;
   uint32_t* ready;       // closure blocks get the call's epoch with kPendingFlag set
+  uint32_t* lv_done;     // fused seeks: per-level counters, cleared here (null otherwise)
 };
 
 // The blocks a seek must decode: its target blocks and, transitively, every
@@ -1561,13 +1781,17 @@ __global__ void closure_kernel(ClosureArgs a) {
   __shared__ uint32_t lcnt[kMaxLevelLaunches + 1];
   const uint32_t tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
   if (tid == 0) {
-    a.sh->epoch += 1;
+    const uint32_t e = (a.sh->epoch + 1) & ~kPendingFlag;  // never 0, never with the pending bit
+    a.sh->epoch = e ? e : 1u;
     a.sh->ticket = 0;
     a.sh->ticket2 = 0;
     a.sh->ticket3 = 0;
     s_min = (uint32_t)a.first;
   }
-  if (tid <= kMaxLevelLaunches) lcnt[tid] = 0;
+  if (tid <= kMaxLevelLaunches) {
+    lcnt[tid] = 0;
+    if (a.lv_done) a.lv_done[tid] = 0;
+  }
   uint32_t ntar = (uint32_t)(a.last - a.first + 1);
   for (uint32_t i = tid; i < ntar; i += blockDim.x) {
     uint32_t b = (uint32_t)a.first + i;
@@ -1896,6 +2120,7 @@ __global__ void __launch_bounds__(256, ACE_PASS_MIN_CTAS(PASS)) cache_decode_ker
     a.sh = reinterpret_cast<ScratchHdr*>(c.h);
     a.ready = arc.ready;
     a.slot_of = arc.slot_of;
+    a.n_slots = c.n_slots;
     a.timeout_ns = ca.timeout_ns;
     a.recs = c.recs;
     a.match_ptr = nullptr;
@@ -1966,7 +2191,8 @@ __global__ void count_pattern_mismatch_kernel(const uint8_t* p, uint64_t n, uint
 
 // New call on a scratch buffer: next epoch, ticket back to zero.
 __global__ void begin_call_kernel(ScratchHdr* sh) {
-  sh->epoch += 1;
+  const uint32_t e = (sh->epoch + 1) & ~kPendingFlag;  // never 0, never with the pending bit
+  sh->epoch = e ? e : 1u;
   sh->ticket = 0;
   sh->ticket2 = 0;
   sh->ticket3 = 0;
@@ -2002,11 +2228,12 @@ struct ace_index {
   uint32_t max_ntok;
   uint64_t n_matches;
   uint64_t* d_match_ptr;
+  uint32_t* d_lv_count;  // blocks per level
   int device;
   int num_sms;
   ace_tune tune;
   // occupancy of the decode kernels, per (seek?, pass, warps per CTA, window)
-  mutable int occ_cache[2][3][9][9];
+  mutable int occ_cache[2][4][9][9];  // [3]: the fused pass
   mutable int occ_level[9][9];  // the per-level match kernel
   mutable bool small_attr = false;  // match_small_kernel allowed its shared memory
   // whole decodes resolve matches with one launch per level when there are
@@ -2040,7 +2267,7 @@ IndexLayout index_layout(uint64_t nb) {
 }
 
 struct ScratchLayout {
-  uint64_t ready, slot_of, work, marks, front0, front1, warps, tail, total;
+  uint64_t ready, slot_of, work, marks, front0, front1, lv_done, warps, tail, total;
   uint64_t n_warps;  // per-warp token regions available
 };
 
@@ -2074,6 +2301,8 @@ ScratchLayout scratch_layout(uint64_t nb, uint32_t log2B, uint64_t max_seek, int
   o = align256(o + 4 * nb);
   L.front1 = o;
   o = align256(o + 4 * nb);
+  L.lv_done = o;
+  o = align256(o + 4 * (nb + 1));
   uint64_t items = std::max<uint64_t>(nb, max_seek);
   L.n_warps = std::min<uint64_t>((uint64_t)num_sms * kMaxWarpsPerSM, items + 16);
   L.warps = o;
@@ -2158,48 +2387,61 @@ ace_status read_header(const void* d_src, void* h_dst, uint32_t bytes, cudaStrea
 // the token window; matches: the match records) and the grid.
 struct Launch {
   uint32_t warps, chunk;
-  uint32_t smem[3];
-  uint32_t grid[3];
+  uint32_t smem[4];  // [PASS_FUSED]: the largest of the three (its phases reuse one area)
+  uint32_t grid[4];
   uint64_t timeout;
+  uint32_t schedule;
 };
 
 template <class K>
 ace_status occupancy(K kernel, int device, uint32_t warps, size_t smem, int* occ) {
   int optin = 0;
   CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device));
-  if (smem > (size_t)optin) {
+  cudaFuncAttributes fa;
+  CUDA_TRY(cudaFuncGetAttributes(&fa, kernel));
+  const size_t dyn_max = (size_t)optin - fa.sharedSizeBytes;  // the kernel's static shared memory counts too
+  if (smem > dyn_max) {
     *occ = -1;  // this many warps with this much shared memory do not fit one CTA
     return ACE_OK;
   }
   // allow every configuration up to the opt-in limit, so launches planned
   // earlier with other shapes stay valid
-  CUDA_TRY(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+  CUDA_TRY(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_max));
   int o = 0;
   CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kernel, 32 * warps, smem));
   *occ = o > 0 ? o : -1;
   return ACE_OK;
 }
 
-// occ_cache: 3 x 9 x 9 ints (pass, warps per CTA, window / 32), 0 = unknown
-template <class K0, class K1, class K2>
+// occ_cache: 4 x 9 x 9 ints (pass, warps per CTA, window / 32), 0 = unknown;
+// k3 is the fused pass
+template <class K0, class K1, class K2, class K3>
 ace_status plan_launch(const ace_index* idx, const ace_tune* tune, uint32_t log2B, uint64_t max_items,
-                       uint64_t max_warps, K0 k0, K1 k1, K2 k2, int* occ_cache, Launch* L, uint32_t lit_ring = kRing) {
+                       uint64_t max_warps, K0 k0, K1 k1, K2 k2, K3 k3, int* occ_cache, Launch* L,
+                       uint32_t lit_ring = kRing) {
   ace_tune t = tune ? *tune : idx->tune;
   L->warps = t.warps_per_cta ? t.warps_per_cta : 4;
   L->chunk = t.chunk_tokens ? t.chunk_tokens : 128;
   if (L->warps > kMaxWarpsPerCta || (L->chunk & 31) || L->chunk > kMaxWindow) return ACE_E_INVAL;
   L->timeout = t.wait_timeout_ns ? t.wait_timeout_ns : kDefaultTimeoutNs;
+  L->schedule = t.schedule;
+  if (L->schedule > ACE_SCHEDULE_FUSED) return ACE_E_INVAL;
+  // automatic: the pass schedule, measured faster on every profile (the
+  // fused launch's match jobs of the first levels form a serial chain)
+  if (L->schedule == ACE_SCHEDULE_AUTO) L->schedule = ACE_SCHEDULE_PASSES;
   L->smem[PASS_TOKENS] = tok_smem_bytes(esc_cap(log2B));
   L->smem[PASS_LITERALS] = lit_smem_bytes(L->chunk, lit_ring);
   L->smem[PASS_MATCH] = kMatchSmem;
-  int per[3];
-  for (int p = 0; p < 3; p++) {
+  L->smem[PASS_FUSED] = std::max(std::max(L->smem[PASS_TOKENS], L->smem[PASS_LITERALS]), L->smem[PASS_MATCH]);
+  int per[4];
+  for (int p = 0; p < 4; p++) {
     int& c = occ_cache[(p * 9 + L->warps) * 9 + L->chunk / 32];
     if (c == 0) {
       const size_t smem = (size_t)L->warps * L->smem[p];
-      ace_status rc = p == 0 ? occupancy(k0, idx->device, L->warps, smem, &c)
+      ace_status rc = p == 0   ? occupancy(k0, idx->device, L->warps, smem, &c)
                       : p == 1 ? occupancy(k1, idx->device, L->warps, smem, &c)
-                               : occupancy(k2, idx->device, L->warps, smem, &c);
+                      : p == 2 ? occupancy(k2, idx->device, L->warps, smem, &c)
+                               : occupancy(k3, idx->device, L->warps, smem, &c);
       if (rc) return rc;
     }
     if (c < 0) return ACE_E_INVAL;
@@ -2207,12 +2449,15 @@ ace_status plan_launch(const ace_index* idx, const ace_tune* tune, uint32_t log2
     if (t.ctas_per_sm && (int)t.ctas_per_sm < per[p]) per[p] = (int)t.ctas_per_sm;
   }
   uint64_t need = std::max<uint64_t>(1, (max_items + L->warps - 1) / L->warps);
-  // the token pass keeps per-warp token records in scratch: at most max_warps warps
+  // the token and fused passes keep per-warp records in scratch: at most
+  // max_warps warps
   uint64_t g0 = std::min<uint64_t>((uint64_t)idx->num_sms * per[0], max_warps / L->warps);
-  if (g0 < 1) return ACE_E_NOMEM;
+  uint64_t g3 = std::min<uint64_t>((uint64_t)idx->num_sms * per[3], max_warps / L->warps);
+  if (g0 < 1 || g3 < 1) return ACE_E_NOMEM;
   L->grid[PASS_TOKENS] = (uint32_t)std::min(g0, need);
   L->grid[PASS_LITERALS] = (uint32_t)std::min<uint64_t>((uint64_t)idx->num_sms * per[1], need);
   L->grid[PASS_MATCH] = (uint32_t)std::min<uint64_t>((uint64_t)idx->num_sms * per[2], need);
+  L->grid[PASS_FUSED] = (uint32_t)std::min(g3, need);
   return ACE_OK;
 }
 
@@ -2221,7 +2466,8 @@ ace_status plan_index_launch(const ace_index* idx, const ace_tune* tune, uint64_
                              Launch* L) {
   return plan_launch(idx, tune, idx->h.log2_block, max_items, max_warps, decode_kernel<SEEK, PASS_TOKENS>,
                      decode_kernel<SEEK, PASS_LITERALS>, decode_kernel<SEEK, PASS_MATCH>,
-                     &idx->occ_cache[SEEK][0][0][0], L, SEEK ? kSeekRing : kRing);
+                     decode_kernel<SEEK, PASS_FUSED>, &idx->occ_cache[SEEK][0][0][0], L,
+                     SEEK ? kSeekRing : kRing);
 }
 
 // Launches the passes in the mask (bit p: pass p) in order on s, each with
@@ -2243,19 +2489,29 @@ void launch_passes(const Launch& L, uint32_t passes, K0 k0, K1 k1, K2 k2, Args a
   }
 }
 
+// The fused pass: one launch for the whole decode.
+template <class K3, class Args>
+void launch_fused(const Launch& L, K3 k3, Args a, cudaStream_t s) {
+  a.warp_smem = L.smem[PASS_FUSED];
+  k3<<<L.grid[PASS_FUSED], 32 * L.warps, (size_t)L.warps * L.smem[PASS_FUSED], s>>>(a);
+}
+
 template <bool SEEK>
 void launch_three_pass(const Launch& L, const DecodeArgs& a, cudaStream_t s) {
   launch_passes(L, 7, decode_kernel<SEEK, PASS_TOKENS>, decode_kernel<SEEK, PASS_LITERALS>,
                 decode_kernel<SEEK, PASS_MATCH>, a, s);
 }
 
-// A seek after its closure kernel: tokens and literals over the work list,
-// then one match launch over the level-ordered list that waits, bounded, on
-// the pending members of the closure.  (One launch per level, as whole
-// decodes do, is slower for a seek's hundred-odd blocks.)
+// A seek after its closure kernel, over the level-ordered work list: by
+// default one fused launch (each warp decodes a block through both layers,
+// waiting, bounded, only on pending members of the closure); with the pass
+// schedule, tokens and literals over the list, then one match launch that
+// waits the same way.  (One launch per level, as whole decodes by passes do,
+// is slower for a seek's hundred-odd blocks.)
 ace_status launch_seek(const ace_index* idx, const Launch& L, const DecodeArgs& a, cudaStream_t s) {
   (void)idx;
-  launch_three_pass<true>(L, a, s);
+  if (L.schedule == ACE_SCHEDULE_FUSED) launch_fused(L, decode_kernel<true, PASS_FUSED>, a, s);
+  else launch_three_pass<true>(L, a, s);
   return ACE_OK;
 }
 
@@ -2330,6 +2586,7 @@ ace_status ace_index_build(const void* d_archive, uint64_t archive_bytes, const 
   a.lv_cursor = reinterpret_cast<uint32_t*>(idx->d_mem + L.lv_cursor);
   a.match_ptr = reinterpret_cast<uint64_t*>(idx->d_mem + L.match_ptr);
   idx->d_match_ptr = a.match_ptr;
+  idx->d_lv_count = a.lv_count;
   a.nb = h.n_blocks;
   a.total = h.total_size;
   a.payload_off = h.payload_off;
@@ -2464,6 +2721,17 @@ ace_status decode_all_passes(const ace_index* idx, uint32_t passes, void* d_out,
   a.warp_scratch_bytes = warp_scratch_bytes(idx->max_ntok);
   a.recs = reinterpret_cast<MatchRec*>(static_cast<uint8_t*>(d_scratch) + SL.tail);
   a.match_ptr = idx->d_match_ptr;
+  a.level = idx->d_level;
+  if (passes == 7 && L.schedule == ACE_SCHEDULE_FUSED) {
+    // one launch over the (level, block) order; the level counters start at 0
+    a.lv_done = reinterpret_cast<uint32_t*>(static_cast<uint8_t*>(d_scratch) + SL.lv_done);
+    a.lv_count = idx->d_lv_count;
+    CUDA_TRY(cudaMemsetAsync(a.lv_done, 0, 4ull * idx->n_levels, s));
+    begin_call_kernel<<<1, 1, 0, s>>>(sh);
+    launch_fused(L, decode_kernel<false, PASS_FUSED>, a, s);
+    CUDA_TRY(cudaGetLastError());
+    return ACE_OK;
+  }
   if (passes & 1) begin_call_kernel<<<1, 1, 0, s>>>(sh);
   launch_passes(L, passes & (idx->by_levels ? 3u : 7u), decode_kernel<false, PASS_TOKENS>,
                 decode_kernel<false, PASS_LITERALS>, decode_kernel<false, PASS_MATCH>, a, s);
@@ -2478,7 +2746,6 @@ ace_status decode_all_passes(const ace_index* idx, uint32_t passes, void* d_out,
     uint32_t per_sm = (uint32_t)occ;
     const ace_tune t = tune ? *tune : idx->tune;
     if (t.ctas_per_sm && t.ctas_per_sm < per_sm) per_sm = t.ctas_per_sm;
-    a.level = idx->d_level;
     // levels of at most two blocks per SM: a CTA per block (match_small_kernel)
     const bool small_ok = idx->h.log2_block <= kSmallMaxLog2B;
     const size_t small_smem = small_smem_bytes(idx->h.log2_block);
@@ -2555,6 +2822,9 @@ ace_status ace_seek(const ace_index* idx, uint64_t coord, uint64_t len, void* d_
   Launch L;
   ace_status rc = plan_index_launch<true>(idx, nullptr, cap, S1.n_warps, &L);
   if (rc) return rc;
+  // the fused schedule needs the closure's work list in level order
+  if (!idx->by_levels) L.schedule = ACE_SCHEDULE_PASSES;
+  c.lv_done = L.schedule == ACE_SCHEDULE_FUSED ? reinterpret_cast<uint32_t*>(base + S1.lv_done) : nullptr;
   closure_kernel<<<1, 1024, 0, s>>>(c);
   DecodeArgs a{};
   a.arc = idx->d_arc;
@@ -2573,6 +2843,7 @@ ace_status ace_seek(const ace_index* idx, uint64_t coord, uint64_t len, void* d_
   a.sh = sh;
   a.ready = reinterpret_cast<uint32_t*>(base + S1.ready);
   a.slot_of = c.slot_of;
+  a.n_slots = (uint32_t)cap;
   a.slice = static_cast<uint8_t*>(d_out);
   a.coord = coord;
   a.len = len;
@@ -2583,6 +2854,7 @@ ace_status ace_seek(const ace_index* idx, uint64_t coord, uint64_t len, void* d_
   a.match_ptr = nullptr;
   a.level = idx->d_level;
   a.closure_flags = true;
+  a.lv_done = c.lv_done;
   rc = launch_seek(idx, L, a, s);
   if (rc) return rc;
   CUDA_TRY(cudaGetLastError());
@@ -2663,21 +2935,22 @@ struct ace_batch {
   uint32_t n;
   uint8_t* d_scratch;
   uint64_t scratch_bytes;
+  uint64_t lv_done_off, lv_done_bytes;  // the fused schedule's level counters
   BatchArgs args;
   Launch L;
-  int occ[3][9][9];
+  int occ[4][9][9];
 };
 
 namespace {
 
 struct BatchLayout {
-  uint64_t objs, item_start, ready, warps, recs, total, n_warps, max_ntok, items, n_matches;
+  uint64_t objs, item_start, ready, lv_done, lv_done_bytes, warps, recs, total, n_warps, max_ntok, items, n_matches;
   uint32_t max_log2B;
 };
 
 ace_status batch_layout(const ace_index* const* idx, uint32_t n, BatchLayout* B) {
   if (!idx || n == 0) return ACE_E_INVAL;
-  uint64_t ready = 0, items = 0, max_ntok = 0, matches = 0;
+  uint64_t ready = 0, items = 0, max_ntok = 0, matches = 0, levels = 0;
   uint32_t max_log2B = 0;
   int dev = idx[0] ? idx[0]->device : -1, sms = idx[0] ? idx[0]->num_sms : 0;
   for (uint32_t i = 0; i < n; i++) {
@@ -2685,6 +2958,7 @@ ace_status batch_layout(const ace_index* const* idx, uint32_t n, BatchLayout* B)
     items += idx[i]->h.n_blocks;
     ready += align256(4 * idx[i]->h.n_blocks);
     matches += idx[i]->n_matches;
+    levels += idx[i]->n_levels;
     max_ntok = std::max<uint64_t>(max_ntok, idx[i]->max_ntok);
     max_log2B = std::max<uint32_t>(max_log2B, idx[i]->h.log2_block);
   }
@@ -2696,6 +2970,9 @@ ace_status batch_layout(const ace_index* const* idx, uint32_t n, BatchLayout* B)
   o = align256(o + 4ull * (n + 1));
   B->ready = o;
   o += ready;
+  B->lv_done = o;
+  B->lv_done_bytes = 4 * levels;
+  o = align256(o + 4 * levels);
   B->n_warps = std::min<uint64_t>((uint64_t)sms * kMaxWarpsPerSM, items + 16);
   B->warps = o;
   o = align256(o + B->n_warps * warp_scratch_bytes(max_ntok));
@@ -2731,7 +3008,7 @@ ace_status ace_batch_create(const ace_index* const* idx, uint32_t n, void* const
   uint8_t* base = static_cast<uint8_t*>(d_scratch);
   std::vector<ObjDesc> od(n);
   std::vector<uint32_t> start(n + 1);
-  uint64_t ready = B.ready, items = 0, recs = B.recs;
+  uint64_t ready = B.ready, items = 0, recs = B.recs, lvd = B.lv_done;
   for (uint32_t i = 0; i < n; i++) {
     const ace_index* x = idx[i];
     if (out_bytes[i] < x->h.total_size || (!d_outs[i] && x->h.total_size)) return ACE_E_NOMEM;
@@ -2742,8 +3019,11 @@ ace_status ace_batch_create(const ace_index* const* idx, uint32_t n, void* const
                     static_cast<uint8_t*>(d_outs[i]),
                     reinterpret_cast<uint32_t*>(base + ready),
                     x->d_order,
+                    x->d_level,
                     reinterpret_cast<MatchRec*>(base + recs),
                     x->d_match_ptr,
+                    reinterpret_cast<uint32_t*>(base + lvd),
+                    x->d_lv_count,
                     x->h.log2_block,
                     x->h.off_width,
                     (uint32_t)x->h.n_blocks,
@@ -2752,6 +3032,7 @@ ace_status ace_batch_create(const ace_index* const* idx, uint32_t n, void* const
     items += x->h.n_blocks;
     ready += align256(4 * x->h.n_blocks);
     recs += 16 * x->n_matches;
+    lvd += 4ull * x->n_levels;
   }
   start[n] = (uint32_t)items;
   ace_batch* b = new (std::nothrow) ace_batch();
@@ -2760,9 +3041,12 @@ ace_status ace_batch_create(const ace_index* const* idx, uint32_t n, void* const
   b->n = n;
   b->d_scratch = base;
   b->scratch_bytes = scratch_bytes;
+  b->lv_done_off = B.lv_done;
+  b->lv_done_bytes = B.lv_done_bytes;
   // the launch shape uses the largest block size's escape table
   rc = plan_launch(idx[0], tune, B.max_log2B, B.items, B.n_warps, batch_decode_kernel<PASS_TOKENS>,
-                   batch_decode_kernel<PASS_LITERALS>, batch_decode_kernel<PASS_MATCH>, &b->occ[0][0][0], &b->L);
+                   batch_decode_kernel<PASS_LITERALS>, batch_decode_kernel<PASS_MATCH>,
+                   batch_decode_kernel<PASS_FUSED>, &b->occ[0][0][0], &b->L);
   if (rc == ACE_OK &&
       (cudaMemsetAsync(base, 0, B.warps, s) != cudaSuccess ||
        cudaMemcpyAsync(base + B.objs, od.data(), n * sizeof(ObjDesc), cudaMemcpyHostToDevice, s) != cudaSuccess ||
@@ -2794,9 +3078,14 @@ ace_status ace_decode_batch(const ace_batch* b, cudaStream_t s) {
   if (!b) return ACE_E_INVAL;
   if (!b->args.n_items) return ACE_OK;
   const Launch& L = b->L;
+  if (L.schedule == ACE_SCHEDULE_FUSED && b->lv_done_bytes)
+    CUDA_TRY(cudaMemsetAsync(b->d_scratch + b->lv_done_off, 0, b->lv_done_bytes, s));
   begin_call_kernel<<<1, 1, 0, s>>>(b->args.sh);
-  launch_passes(L, 7, batch_decode_kernel<PASS_TOKENS>, batch_decode_kernel<PASS_LITERALS>,
-                batch_decode_kernel<PASS_MATCH>, b->args, s);
+  if (L.schedule == ACE_SCHEDULE_FUSED)
+    launch_fused(L, batch_decode_kernel<PASS_FUSED>, b->args, s);
+  else
+    launch_passes(L, 7, batch_decode_kernel<PASS_TOKENS>, batch_decode_kernel<PASS_LITERALS>,
+                  batch_decode_kernel<PASS_MATCH>, b->args, s);
   CUDA_TRY(cudaGetLastError());
   return ACE_OK;
 }
@@ -2837,7 +3126,7 @@ struct ace_cache {
   CacheDecodeArgs dargs;
   Launch L;
   uint64_t req_off;  // requests are staged here by ace_seek_batch_host
-  int occ[3][9][9];
+  int occ[4][9][9];
 };
 
 namespace {
@@ -2946,9 +3235,11 @@ ace_status ace_cache_create(const ace_index* const* idx, uint32_t n, void* const
   c->mem = base;
   c->bytes = bytes;
   c->req_off = C.reqs;
+  // seek batches run the three passes (their work list is in block order,
+  // not level order); the fused entry only sizes like the match pass
   rc = plan_launch(idx[0], tune, log2B, n_slots, C.n_warps, cache_decode_kernel<PASS_TOKENS>,
-                   cache_decode_kernel<PASS_LITERALS>, cache_decode_kernel<PASS_MATCH>, &c->occ[0][0][0], &c->L,
-                   kSeekRing);
+                   cache_decode_kernel<PASS_LITERALS>, cache_decode_kernel<PASS_MATCH>,
+                   cache_decode_kernel<PASS_MATCH>, &c->occ[0][0][0], &c->L, kSeekRing);
   // header (epoch 1: no block is cached, since every ready flag starts at 0)
   CacheHdr h{};
   h.epoch = 1;
@@ -3117,7 +3408,11 @@ ace_status ace_seek_noalloc(const ace_index* idx, uint64_t coord, uint64_t len, 
   uint64_t first = coord >> log2B, last = (coord + len - 1) >> log2B;
   if (last - first + 1 > cap) return ACE_E_NOMEM;  // more target blocks than slots
   ScratchHdr* sh = reinterpret_cast<ScratchHdr*>(base);
-  // the closure marks must start clear; the array may hold another archive's layout
+  // The array may hold what a call on another archive, with another layout,
+  // left there.  The closure marks must start clear, and so must the ready
+  // flags: a stale word equal to this call's epoch would pass a block outside
+  // the closure as a member (epochs are never 0).
+  CUDA_TRY(cudaMemsetAsync(base + S.ready, 0, S.slot_of - S.ready, s));
   CUDA_TRY(cudaMemsetAsync(base + S.marks, 0, S.front0 - S.marks, s));
   CUDA_TRY(cudaMemsetAsync(base, 0, 3 * sizeof(uint32_t), s));  // status word
   ClosureArgs c;
@@ -3139,6 +3434,8 @@ ace_status ace_seek_noalloc(const ace_index* idx, uint64_t coord, uint64_t len, 
   Launch L;
   rc = plan_index_launch<true>(idx, nullptr, cap, S.n_warps, &L);
   if (rc) return rc;
+  if (!idx->by_levels) L.schedule = ACE_SCHEDULE_PASSES;
+  c.lv_done = L.schedule == ACE_SCHEDULE_FUSED ? reinterpret_cast<uint32_t*>(base + S.lv_done) : nullptr;
   closure_kernel<<<1, 1024, 0, s>>>(c);
   DecodeArgs a{};
   a.arc = idx->d_arc;
@@ -3157,6 +3454,7 @@ ace_status ace_seek_noalloc(const ace_index* idx, uint64_t coord, uint64_t len, 
   a.sh = sh;
   a.ready = reinterpret_cast<uint32_t*>(base + S.ready);
   a.slot_of = c.slot_of;
+  a.n_slots = (uint32_t)cap;
   a.slice = static_cast<uint8_t*>(d_out);
   a.coord = coord;
   a.len = len;
@@ -3167,6 +3465,7 @@ ace_status ace_seek_noalloc(const ace_index* idx, uint64_t coord, uint64_t len, 
   a.match_ptr = nullptr;
   a.level = idx->d_level;
   a.closure_flags = true;
+  a.lv_done = c.lv_done;
   rc = launch_seek(idx, L, a, s);
   if (rc) return rc;
   CUDA_TRY(cudaGetLastError());

@@ -89,3 +89,35 @@ def test_batch_mixes_offset_widths():
     assert db.sync() == ace.ACE_OK
     _check_all(db, datas)
     db.close()
+
+
+def test_batch_with_deep_chain_oracle_archives():
+    """The batch decoder's match phase waits on ready flags.  Archives written
+    by the oracle (most-recent-first sources: hundreds of dependency levels
+    at small blocks) mixed with library archives in one batch: every output
+    bit-exact, in a plain decode and in graph replays, with both schedules."""
+    import oracle
+    import synth
+    datas, arcs = [], []
+    for k, (p, n, log2b) in enumerate([("text", 300_000, 8), ("mixed", 250_000, 10), ("fastq", 200_000, 8),
+                                       ("genome", 180_000, 9), ("text", 120_000, 12), ("mixed", 90_000, 8)]):
+        d = synth.generate(p, n, 40 + k)
+        datas.append(d)
+        arcs.append(oracle.encode(d, log2b, 4, 16))
+        d2 = synth.generate(p, n // 2 + 777, 60 + k)
+        datas.append(d2)
+        arcs.append(ace.ace_encode(d2, 12, 4))
+    assert max(oracle.levels(a).max() for a in arcs[::2]) > 32
+    for schedule in (ace.ACE_SCHEDULE_FUSED, ace.ACE_SCHEDULE_PASSES):
+        db = DeviceBatch(arcs, tune=ace.make_tune(schedule=schedule))
+        db.decode()
+        assert db.sync() == ace.ACE_OK
+        _check_all(db, datas)
+        g = db.capture()
+        for _ in range(2):
+            db.out.zero_()
+            g.replay()
+            assert db.sync() == ace.ACE_OK
+            _check_all(db, datas)
+        del g
+        db.close()

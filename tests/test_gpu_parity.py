@@ -9,6 +9,7 @@ import pytest
 import oracle
 import synth
 import __graft_entry__
+from conftest import with_dep_removed
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -36,12 +37,18 @@ def gpu_decode(arc, tune=None):
 MIN_MATCH = {"mixed": 4, "text": 4, "fastq": 16, "genome": 20}
 
 
+SCHEDULES = {"fused": ace.ACE_SCHEDULE_FUSED, "passes": ace.ACE_SCHEDULE_PASSES}
+
+
+@pytest.mark.parametrize("schedule", sorted(SCHEDULES))
 @pytest.mark.parametrize("profile", ["mixed", "fastq", "genome", "text"])
 @pytest.mark.parametrize("log2b", [8, 12, 14, 16])
-def test_decode_all_library_archives(profile, log2b):
+def test_decode_all_library_archives(profile, log2b, schedule):
+    """Both decode schedules (one fused launch; three passes with the match
+    pass by level) give the original bytes."""
     data = synth.generate(profile, 3_000_000 + 12345, 100 + log2b)
     arc = ace.ace_encode(data, log2b, MIN_MATCH[profile])
-    st, out = gpu_decode(arc)
+    st, out = gpu_decode(arc, ace.make_tune(schedule=SCHEDULES[schedule]))
     assert st == ace.ACE_OK, ace.ace_status_str(st)
     assert np.array_equal(out, data)
 
@@ -57,18 +64,39 @@ def test_decode_all_32k_blocks(profile):
     assert np.array_equal(out, data)
 
 
+@pytest.mark.parametrize("schedule", sorted(SCHEDULES))
 @pytest.mark.parametrize("profile", ["mixed", "fastq", "genome", "text"])
 @pytest.mark.parametrize("log2b", [8, 14])
-def test_decode_all_oracle_archives(profile, log2b):
+def test_decode_all_oracle_archives(profile, log2b, schedule):
     """Archives written by the oracle (most-recent-first sources, deep
     dependency chains) decode to the oracle's own output."""
     data = synth.generate(profile, 400_000, 7)
     arc = oracle.encode(data, log2b, 4, 16)
     ref = oracle.decode(arc)
     assert np.array_equal(ref, data)
-    st, out = gpu_decode(arc)
+    st, out = gpu_decode(arc, ace.make_tune(schedule=SCHEDULES[schedule]))
     assert st == ace.ACE_OK, ace.ace_status_str(st)
     assert np.array_equal(out, ref)
+
+
+@pytest.mark.parametrize("schedule", sorted(SCHEDULES))
+def test_seeks_under_both_schedules(schedule):
+    """Seeks through the fused launch and through the three passes, on a
+    library archive and on a deep-chain oracle archive, equal the original."""
+    for arc_of, n in ((lambda d: ace.ace_encode(d, 12, 4), 2_000_000), (lambda d: oracle.encode(d, 10, 4, 16), 300_000)):
+        data = synth.generate("text", n, 33)
+        arc = arc_of(data)
+        da = DeviceArchive(arc, max_seek_blocks=n // 1024 + 8)
+        ace.ace_index_set_tune(da.idx, ace.make_tune(schedule=SCHEDULES[schedule]))
+        rng = np.random.default_rng(8)
+        cases = [(0, 1), (n - 1, 1), (n // 2, 5000)] + [(int(c), int(rng.integers(1, 60_000)))
+                                                        for c in rng.integers(0, n - 60_000, 10)]
+        for coord, length in cases:
+            out = da.seek(coord, length)
+            st = da.sync()
+            assert st == ace.ACE_OK, (coord, length, ace.ace_status_str(st))
+            assert np.array_equal(out.cpu().numpy(), data[coord:coord + length]), (coord, length)
+        da.close()
 
 
 def test_plain_small_config_decode_seek_and_three_phase():
@@ -239,20 +267,6 @@ def test_seek_closure_larger_than_scratch_reports_nomem():
     da2.close()
 
 
-def _with_dep_removed(arc, block):
-    """The archive with one block's dependency intervals pointed at block 0:
-    its real source blocks leave the seek closure (a host-made corruption)."""
-    bad = arc.copy()
-    nb = oracle.info(arc)["n_blocks"]
-    deps_off = int(arc[40:48].view(np.uint64)[0])
-    ptr = bad[deps_off:deps_off + 4 * (nb + 1)].view(np.uint32)
-    ivs = bad[deps_off + 4 * (nb + 1):].view(np.uint32)
-    for i in range(int(ptr[block]), int(ptr[block + 1])):
-        ivs[2 * i] = 0
-        ivs[2 * i + 1] = 0
-    return bad
-
-
 def test_seek_outside_its_closure_is_reported_at_once():
     """A seek whose closure misses a source block (its dependency list was
     emptied on the host) finds the block's flag unmarked by the closure and
@@ -262,7 +276,7 @@ def test_seek_outside_its_closure_is_reported_at_once():
     b = 30
     deps = oracle.deps(arc)[b]
     assert deps and deps != [(0, 0)]
-    bad = _with_dep_removed(arc, b)
+    bad = with_dep_removed(arc, b)
     da = DeviceArchive(bad, max_seek_blocks=64)
     ace.ace_index_set_tune(da.idx, ace.make_tune(wait_timeout_ns=2_000_000_000))
     t0 = time.perf_counter()
@@ -285,7 +299,7 @@ def test_wait_gives_up_with_timeout_status():
     data = synth.generate("text", 200_000, 12)
     arc = oracle.encode(data, 12, 4, 16)
     b = 30
-    bad = _with_dep_removed(arc, b)
+    bad = with_dep_removed(arc, b)
     da = DeviceArchive(bad, max_seek_blocks=64)
     c = SeekCache([da], n_slots=64, max_reqs=4, pool_bytes=1 << 16,
                   tune=ace.make_tune(wait_timeout_ns=2_000_000))
@@ -307,7 +321,7 @@ def test_library_archive_seek_with_a_dependency_removed():
     arc = ace.ace_encode(data, 14, 16)
     deps = oracle.deps(arc)
     b = next(k for k in range(len(deps)) if deps[k] and deps[k] != [(0, 0)] and k > 70)
-    bad = _with_dep_removed(arc, b)
+    bad = with_dep_removed(arc, b)
     da = DeviceArchive(bad, max_seek_blocks=256)
     assert da.info["n_levels"] <= 32
     s = da.seek(b * 16384, 16384)
@@ -331,7 +345,7 @@ def test_decode_all_with_a_dependency_removed():
         arc = oracle.encode(data, log2b, 4, 16)
         deps = oracle.deps(arc)[b]
         assert deps and deps != [(0, 0)]
-        bad = _with_dep_removed(arc, b)
+        bad = with_dep_removed(arc, b)
         da = DeviceArchive(bad)
         ace.ace_index_set_tune(da.idx, ace.make_tune(wait_timeout_ns=20_000_000))
         out = da.decode_all()

@@ -9,8 +9,10 @@ failure has run every other test before this one."""
 import numpy as np
 import pytest
 
+import oracle
 import synth
 import __graft_entry__
+from conftest import with_dep_removed
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -63,3 +65,35 @@ def test_noalloc_seek_rejects_requests_beyond_its_scratch():
     assert st == ace.ACE_OK
     assert np.array_equal(out[:65536].cpu().numpy(), data[5 << 20:(5 << 20) + 65536])
     da.close()
+
+
+def test_noalloc_seek_reports_a_corrupt_archive_after_another_layout():
+    """The fixed scratch keeps whatever the last call left in it.  After calls
+    on an archive of another shape (another block size, other block counts
+    and token records), an archive whose block lost its dependency list on the
+    host must come back as ACE_E_CORRUPT -- its source blocks are outside the
+    seek's closure -- and never read through a stale block-to-slot entry.  A
+    clean seek still works afterwards."""
+    data_a = synth.generate("mixed", 3_000_000, 24)
+    arc_a = ace.ace_encode(data_a, 14, 4)
+    da = DeviceArchive(arc_a)
+    out = torch.empty(300_000, dtype=torch.uint8, device="cuda")
+    for coord, length in [(0, 16384), (1_000_000, 300_000), (2_990_000, 10_000)]:
+        assert ace.ace_seek_noalloc(da.idx, coord, length, out, length) == ace.ACE_OK
+        assert np.array_equal(out[:length].cpu().numpy(), data_a[coord:coord + length])
+    data_b = synth.generate("text", 200_000, 12)
+    arc_b = oracle.encode(data_b, 12, 4, 16)
+    b = 30
+    assert oracle.deps(arc_b)[b] not in ([], [(0, 0)])
+    db = DeviceArchive(with_dep_removed(arc_b, b))
+    for _ in range(2):
+        st = ace.ace_seek_noalloc(db.idx, b * 4096, 100, out, 100)
+        assert st == ace.ACE_E_CORRUPT, ace.ace_status_str(st)
+    st = ace.ace_seek_noalloc(db.idx, 0, 4096, out, 4096)
+    assert st == ace.ACE_OK, ace.ace_status_str(st)
+    assert np.array_equal(out[:4096].cpu().numpy(), data_b[:4096])
+    # and the first archive again, on the same array
+    assert ace.ace_seek_noalloc(da.idx, 5000, 70_000, out, 70_000) == ace.ACE_OK
+    assert np.array_equal(out[:70_000].cpu().numpy(), data_a[5000:75_000])
+    da.close()
+    db.close()
