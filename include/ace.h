@@ -287,26 +287,35 @@ ace_status ace_batch_free(ace_batch *batch);
  * Many seeks, over several resident archives, in one pass: the serving
  * pattern.  A decoded-block cache (caller memory) holds n_slots decoded
  * blocks; every archive attached to it has a small per-archive state (ready
- * flags, slot map, closure marks; ace_archive_state_size).  A seek batch:
+ * flags, slot map, closure marks, work positions; ace_archive_state_size).
+ * A seek batch:
  *   1. finds every target block that is not cached and, transitively, every
  *      uncached block their matches read (Section 2), in ascending block
- *      order per archive, and gives each a free slot;
+ *      order per archive, and gives each a slot from a clock over the slots:
+ *      slots the batch itself uses are passed over, a slot used since the
+ *      hand last passed it gets a second chance, and a slot taken from a
+ *      cached block evicts that block;
  *   2. decodes those blocks through both layers into their slots (Section 3
  *      entry point, Section 2 match layer), waiting bounded on sources;
  *   3. copies each request's bytes [coord, coord + len) to d_pool + out_off.
- * Blocks stay cached across batches until the slots run out: a batch that
- * needs more free slots than remain records ACE_E_NOMEM and copies nothing;
- * the caller then calls ace_cache_reset (every block uncached, every slot
- * free) and resubmits.  After any other error, reset as well.
+ * Blocks stay cached across batches until evicted.  A batch whose new
+ * blocks exceed the blocks one batch may decode (ace_cache_limits) or the
+ * slots it does not use itself records ACE_E_NOMEM and copies nothing; the
+ * cache stays valid, and the caller submits fewer requests (a single
+ * request that still fails can never be served by this cache).  After any
+ * other error, call ace_cache_reset (every block uncached, every slot free).
  *
  * All archives of a cache share one device and one block size.  Batches on
  * one cache must be ordered on one stream; separate caches (each with its
  * own per-archive states) may run concurrently on separate streams.
- * ace_seek_batch reads device-resident requests and enqueues three kernels;
- * ace_seek_batch_host validates host requests against the archives' sizes
- * (h_totals, may be NULL) and the pool, stages them in the cache memory
- * (n <= max_reqs) and calls it.  ace_cache_sync returns (then clears) the
- * first device error; ace_cache_usage reports slots in use.
+ * ace_seek_batch reads device-resident requests and enqueues three kernels
+ * plus the passes; ace_seek_batch_host validates host requests against the
+ * archives' sizes (h_totals, may be NULL) and the pool, stages them in the
+ * cache memory (n <= max_reqs) and calls it.  ace_cache_sync returns (then
+ * clears) the first device error; ace_cache_usage reports slots holding a
+ * block; ace_cache_counters the blocks evicted and decoded since creation;
+ * ace_cache_limits the slots, the blocks one batch may decode and the
+ * requests one batch may hold.
  */
 typedef struct {
     uint32_t archive;  /* position of the archive in the cache's list */
@@ -330,6 +339,8 @@ ace_status ace_seek_batch_host(const ace_cache *cache, const ace_seek_req *h_req
 ace_status ace_cache_sync(const ace_cache *cache, cudaStream_t s);
 ace_status ace_cache_usage(const ace_cache *cache, uint32_t *used_slots, uint32_t *n_slots, cudaStream_t s);
 ace_status ace_cache_reset(const ace_cache *cache, cudaStream_t s);
+ace_status ace_cache_counters(const ace_cache *cache, uint64_t *h_evicted, uint64_t *h_decoded, cudaStream_t s);
+ace_status ace_cache_limits(const ace_cache *cache, uint32_t *h_n_slots, uint32_t *h_max_work, uint32_t *h_max_reqs);
 ace_status ace_cache_free(ace_cache *cache);
 
 /* ---------------------------------------------------------- verification */

@@ -98,6 +98,8 @@ _SIGS = {
     "ace_cache_sync": ([_vp, _vp], _i32),
     "ace_cache_usage": ([_vp, _P(_u32), _P(_u32), _vp], _i32),
     "ace_cache_reset": ([_vp, _vp], _i32),
+    "ace_cache_counters": ([_vp, _P(_u64), _P(_u64), _vp], _i32),
+    "ace_cache_limits": ([_vp, _P(_u32), _P(_u32), _P(_u32)], _i32),
     "ace_cache_free": ([_vp], _i32),
 }
 
@@ -374,6 +376,20 @@ def ace_cache_usage(cache, stream=None):
 
 def ace_cache_reset(cache, stream=None):
     _check(lib().ace_cache_reset(cache, _stream(stream)), "ace_cache_reset")
+
+
+def ace_cache_counters(cache, stream=None):
+    """(blocks evicted, blocks decoded) since the cache was created."""
+    e, d = _u64(), _u64()
+    _check(lib().ace_cache_counters(cache, ctypes.byref(e), ctypes.byref(d), _stream(stream)), "ace_cache_counters")
+    return e.value, d.value
+
+
+def ace_cache_limits(cache):
+    """(slots, blocks one batch may decode, requests one batch may hold)."""
+    a, b, c = _u32(), _u32(), _u32()
+    _check(lib().ace_cache_limits(cache, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)), "ace_cache_limits")
+    return a.value, b.value, c.value
 
 
 def ace_cache_free(cache):

@@ -71,24 +71,31 @@ TUNE_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "ace_gb300", "tune.
 
 
 def autotune(db, candidates=None, reps=3, cache_key=None, cache_path=TUNE_CACHE):
-    """Times each (warps per CTA, token window) candidate on the batch and
-    keeps the fastest; results are cached by cache_key in a JSON file."""
+    """Times each (warps per CTA, token window, schedule) candidate on the
+    batch and keeps the fastest; results are cached by cache_key in a JSON
+    file."""
+    def tune_of(c):
+        return ace.make_tune(c["warps_per_cta"], 0, c["window"], schedule=c.get("schedule", 0))
+
     if cache_key is not None and os.path.exists(cache_path):
         try:
             with open(cache_path) as f:
                 hit = json.load(f).get(cache_key)
             if hit:
-                db.retune(ace.make_tune(hit["warps_per_cta"], 0, hit["window"]))
+                db.retune(tune_of(hit))
                 return hit
         except (OSError, ValueError):
             pass
     if candidates is None:
-        candidates = [(w, c) for w in (1, 2, 4, 8) for c in (64, 128, 256)]
+        candidates = [(w, c, s) for s in (ace.ACE_SCHEDULE_PASSES, ace.ACE_SCHEDULE_FUSED)
+                      for w in (1, 2, 4, 8) for c in (64, 128, 256)]
     best = None
     results = []
-    for w, c in candidates:
+    for cand in candidates:
+        w, c = cand[0], cand[1]
+        sch = cand[2] if len(cand) > 2 else ace.ACE_SCHEDULE_PASSES
         try:
-            db.retune(ace.make_tune(w, 0, c))
+            db.retune(ace.make_tune(w, 0, c, schedule=sch))
         except ace.AceError:
             continue
         db.decode()
@@ -103,10 +110,11 @@ def autotune(db, candidates=None, reps=3, cache_key=None, cache_path=TUNE_CACHE)
             e1.synchronize()
             times.append(e0.elapsed_time(e1))
         ms = float(np.median(times))
-        results.append({"warps_per_cta": w, "window": c, "ms": ms})
+        row = {"warps_per_cta": w, "window": c, "schedule": sch, "ms": ms}
+        results.append(row)
         if best is None or ms < best["ms"]:
-            best = {"warps_per_cta": w, "window": c, "ms": ms}
-    db.retune(ace.make_tune(best["warps_per_cta"], 0, best["window"]))
+            best = dict(row)
+    db.retune(tune_of(best))
     best = dict(best, sweep=results)
     if cache_key is not None:
         try:
@@ -123,12 +131,12 @@ def autotune(db, candidates=None, reps=3, cache_key=None, cache_path=TUNE_CACHE)
     return best
 
 
-def make_objects(count, seed=4, min_size=4096, max_size=1 << 26, seed_base=1000, workers=0):
-    """The uneven batch workload: (originals, archives) for count objects with
-    log-uniform sizes, a random profile and block size each (the synth
-    module's object table).  Objects are generated and encoded on a thread
-    pool (the native calls release the interpreter lock), one encoder thread
-    each."""
+def make_objects(count, seed=4, min_size=4096, max_size=1 << 26, seed_base=1000, workers=0, stats=False):
+    """The uneven batch workload: (originals, archives[, parse statistics])
+    for count objects with log-uniform sizes, a random profile and block size
+    each (the synth module's object table).  Objects are generated and
+    encoded on a thread pool (the native calls release the interpreter
+    lock), one encoder thread each."""
     from concurrent.futures import ThreadPoolExecutor
 
     import synth
@@ -139,30 +147,43 @@ def make_objects(count, seed=4, min_size=4096, max_size=1 << 26, seed_base=1000,
     def one(k):
         d = synth.generate(int(profiles[k]), int(sizes[k]), int(seeds[k]))
         log2b = int(bsz[k]).bit_length() - 1
-        return d, ace.ace_encode(d, log2b, mm[int(profiles[k])], threads=1)
+        arc, st = ace.ace_encode(d, log2b, mm[int(profiles[k])], threads=1, stats=True)
+        return d, arc, st
 
+    # the largest objects first, so the pool ends on small ones
+    order = sorted(range(count), key=lambda k: -int(sizes[k]))
+    res = [None] * count
     with ThreadPoolExecutor(workers or os.cpu_count() or 4) as ex:
-        res = list(ex.map(one, range(count)))
+        for k, r in zip(order, ex.map(one, order)):
+            res[k] = r
+    if stats:
+        return [r[0] for r in res], [r[1] for r in res], [r[2] for r in res]
     return [r[0] for r in res], [r[1] for r in res]
 
 
 def time_per_object(items, out_views, reps=1):
-    """The plain alternative: one ace_decode_all launch per object; returns
-    the total device time in ms (events around the whole sequence)."""
+    """The plain alternative: one ace_decode_all launch sequence per object,
+    on one stream; returns the total device time in ms (events around the
+    whole sequence).  One scratch buffer, sized for the largest object,
+    serves every call: calls on one stream run in order, and a whole decode
+    of these archives (at most 32 dependency levels) uses only the scratch
+    header, its per-warp records and its match records, each rewritten by
+    the call."""
     st = torch.cuda.current_stream()
-    scratch = [torch.empty(ace.ace_scratch_size(x.idx, 0), dtype=torch.uint8, device=x.device) for x in items]
-    for x, s in zip(items, scratch):
-        ace.ace_scratch_init(x.idx, s, s.numel(), st)
+    nbytes = max(ace.ace_scratch_size(x.idx, 0) for x in items)
+    scratch = torch.empty(nbytes, dtype=torch.uint8, device=items[0].device)
+    assert all(x.info["n_levels"] <= 32 for x in items)
+    for x in items:
+        ace.ace_scratch_init(x.idx, scratch, nbytes, st)
     best = None
     for _ in range(reps):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(st)
-        for x, o, s in zip(items, out_views, scratch):
-            ace.ace_decode_all(x.idx, o, o.numel(), s, s.numel(), None, st)
+        for x, o in zip(items, out_views):
+            ace.ace_decode_all(x.idx, o, o.numel(), scratch, nbytes, None, st)
         e1.record(st)
         e1.synchronize()
         ms = e0.elapsed_time(e1)
         best = ms if best is None else min(best, ms)
-    for x, s in zip(items, scratch):
-        assert ace.ace_sync(x.idx, s, st) == ace.ACE_OK
+    assert ace.ace_sync(items[0].idx, scratch, st) == ace.ACE_OK
     return best

@@ -275,6 +275,9 @@ struct DecodeArgs {
   // scratch header)
   uint32_t* lv_done;
   const uint32_t* lv_count;
+  // seek batches: match records per work item rather than per slot
+  const uint32_t* rec_index;
+  uint32_t n_rec_slots;
 };
 
 // Shared memory of one warp in the token pass: one stream's tables at a
@@ -398,10 +401,17 @@ __device__ __forceinline__ uint64_t read_src(const uint8_t* q, uint32_t w) {
   return S;
 }
 
-// The records of block b (slot-addressed modes keep max_ntok per slot).
+// The records of block b: whole decodes by the index's prefix count of
+// matches; seeks max_ntok per slot; seek batches max_ntok per work item
+// (rec_index: block -> its place in the batch's work list).
 template <bool SEEK>
 __device__ __forceinline__ MatchRec* recs_of(const DecodeArgs& a, uint32_t b) {
   if (!SEEK) return a.recs + __ldg(a.match_ptr + b);
+  if (a.rec_index) {
+    uint32_t w = __ldg(a.rec_index + b);
+    if (w >= a.n_rec_slots) w = 0;  // the closure wrote it this batch; clamped all the same
+    return a.recs + (uint64_t)w * a.max_ntok;
+  }
   return a.recs + (uint64_t)slot_index(a, b) * a.max_ntok;
 }
 
@@ -1908,7 +1918,8 @@ struct CacheArc {
   uint32_t* ready;    // == cache epoch: the block sits decoded in its slot
   uint32_t* slot_of;
   uint32_t* marks;    // closure marks, clear between calls
-  uint32_t nb, w, pad0, pad1;
+  uint32_t* wpos;     // a block decoded by the current batch: its place in the work list
+  uint32_t nb, w;
 };
 
 // Header of a cache (first 256 bytes of its memory).
@@ -1917,12 +1928,15 @@ struct CacheHdr {
   uint32_t epoch;      // blocks whose ready flag equals it are cached
   uint32_t ticket;
   uint32_t n_work;
-  uint32_t next_slot;  // slots handed out in this epoch
+  uint32_t n_cached;   // slots holding a decoded block
   uint32_t n_front;
-  uint32_t pad0[4];
+  uint32_t hand;       // clock hand: the next slot the allocation looks at
+  uint32_t serial;     // batches run: the slots a batch uses carry its serial
+  uint64_t evicted;    // cached blocks evicted to make room, since creation
   uint32_t ticket2;    // next work item of the literal pass
   uint32_t ticket3;    // next work item of the match pass
-  uint32_t pad[50];
+  uint64_t decoded;    // blocks decoded, since creation
+  uint32_t pad[48];
 };
 static_assert(sizeof(CacheHdr) == 256, "cache header");
 static_assert(offsetof(CacheHdr, ticket2) == offsetof(ScratchHdr, ticket2), "shared header fields");
@@ -1937,49 +1951,73 @@ struct CacheArgs {
   uint32_t n_arcs;
   uint32_t log2B;
   uint32_t n_slots;
-  uint32_t front_cap;
-  uint32_t* front0;   // (archive, block) pairs
+  uint32_t front_cap;    // blocks one batch may decode (work items), and the frontier's capacity
+  uint32_t* front0;      // (archive, block) pairs
   uint32_t* front1;
-  uint32_t* work;     // (archive, block) pairs in decode order
+  uint32_t* work;        // (archive, block) pairs in decode order
+  uint32_t* taken;       // the slots the allocation took, one per work item
   uint32_t* arc_minmax;  // per archive: smallest, largest block marked
+  uint32_t* owner_arc;   // per slot: the archive and block it holds (archive ~0: none)
+  uint32_t* owner_blk;
+  uint32_t* ref;         // per slot: the clock's reference bit
+  uint32_t* use;         // per slot: the serial of the last batch that used it
   uint8_t* slots;
-  MatchRec* recs;     // max_ntok match records per slot
+  MatchRec* recs;        // max_ntok match records per work item
   const ace_seek_req* reqs;
   uint32_t n_reqs;
 };
 
-__device__ __forceinline__ bool cache_mark(const CacheArgs& c, uint32_t a, uint32_t b, uint32_t epoch) {
+// A block the batch needs: a cached one has its slot kept from eviction for
+// this batch and its reference bit set (true: nothing to decode); an
+// uncached one is marked for decoding (returns whether it was newly marked).
+__device__ __forceinline__ bool cache_visit(const CacheArgs& c, uint32_t a, uint32_t b, uint32_t epoch,
+                                            uint32_t serial, bool& cached) {
   const CacheArc& ca = c.arcs[a];
   // flags are set by earlier launches on this stream, ordered before this one
-  if (ld_relaxed(ca.ready + b) == epoch) return false;  // already cached
-  uint32_t bit = 1u << (b & 31);
+  cached = ld_relaxed(ca.ready + b) == epoch;
+  if (cached) {
+    const uint32_t sl = ca.slot_of[b];
+    if (sl < c.n_slots) {
+      c.use[sl] = serial;
+      c.ref[sl] = 1;
+    }
+    return false;
+  }
+  const uint32_t bit = 1u << (b & 31);
   return !(atomicOr(ca.marks + (b >> 5), bit) & bit);
 }
 
 // The blocks a batch of seeks must decode: every target block that is not
 // cached and, transitively, every uncached block their matches read
-// (Section 2), listed archive by archive in ascending block order, each with
-// a fresh slot.  One CTA.
+// (Section 2), listed archive by archive in ascending block order.  Each
+// gets a slot from a clock over the slots: slots this batch uses are passed
+// over, a slot whose reference bit is set gets a second chance (the bit is
+// cleared), and a slot taken from a cached block evicts it.  One CTA.
 __global__ void cache_closure_kernel(CacheArgs c) {
-  __shared__ uint32_t n_next, carry, overflow;
+  __shared__ uint32_t n_next, carry, overflow, s_serial;
+  __shared__ uint32_t s_taken, s_hand, s_scanned, s_stop;
   __shared__ uint32_t wsum[32];
   const uint32_t tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
   const uint32_t epoch = c.h->epoch;
   if (tid == 0) {
     n_next = 0;
     overflow = 0;
+    s_serial = c.h->serial + 1;
+    c.h->serial = s_serial;
   }
   for (uint32_t a = tid; a < c.n_arcs; a += blockDim.x) {
     c.arc_minmax[2 * a] = 0xffffffffu;
     c.arc_minmax[2 * a + 1] = 0;
   }
   __syncthreads();
+  const uint32_t serial = s_serial;
   // targets: a thread per request
   for (uint32_t r = tid; r < c.n_reqs; r += blockDim.x) {
     const ace_seek_req q = c.reqs[r];
     uint64_t first = q.coord >> c.log2B, last = (q.coord + q.len - 1) >> c.log2B;
-    for (uint64_t b = first; b <= last; b++)
-      if (cache_mark(c, q.archive, (uint32_t)b, epoch)) {
+    for (uint64_t b = first; b <= last; b++) {
+      bool cached;
+      if (cache_visit(c, q.archive, (uint32_t)b, epoch, serial, cached)) {
         uint32_t i = atomicAdd(&n_next, 1u);
         if (i < c.front_cap) {
           c.front0[2 * i] = q.archive;
@@ -1990,6 +2028,7 @@ __global__ void cache_closure_kernel(CacheArgs c) {
         atomicMin(&c.arc_minmax[2 * q.archive], (uint32_t)b);
         atomicMax(&c.arc_minmax[2 * q.archive + 1], (uint32_t)b);
       }
+    }
   }
   __syncthreads();
   uint32_t n_front = min(n_next, c.front_cap);
@@ -2004,8 +2043,9 @@ __global__ void cache_closure_kernel(CacheArgs c) {
       const CacheArc& ca = c.arcs[a];
       const uint32_t e1 = ca.dep_ptr[b + 1];
       for (uint32_t e = ca.dep_ptr[b] + lane; e < e1; e += 32)
-        for (uint32_t k = ca.dep_iv[2 * e]; k <= ca.dep_iv[2 * e + 1]; k++)
-          if (cache_mark(c, a, k, epoch)) {
+        for (uint32_t k = ca.dep_iv[2 * e]; k <= ca.dep_iv[2 * e + 1]; k++) {
+          bool cached;
+          if (cache_visit(c, a, k, epoch, serial, cached)) {
             uint32_t j = atomicAdd(&n_next, 1u);
             if (j < c.front_cap) {
               nxt[2 * j] = a;
@@ -2015,6 +2055,7 @@ __global__ void cache_closure_kernel(CacheArgs c) {
             }
             atomicMin(&c.arc_minmax[2 * a], k);
           }
+        }
     }
     __syncthreads();
     n_front = min(n_next, c.front_cap);
@@ -2023,10 +2064,10 @@ __global__ void cache_closure_kernel(CacheArgs c) {
     nxt = t;
     __syncthreads();
   }
-  // ordered compaction, archive by archive, clearing the marks behind it
+  // ordered compaction into the work list, archive by archive, clearing the
+  // marks behind it
   if (tid == 0) carry = 0;
   __syncthreads();
-  const uint32_t slot0 = c.h->next_slot;
   for (uint32_t a = 0; a < c.n_arcs; a++) {
     uint32_t lo = c.arc_minmax[2 * a], hi = c.arc_minmax[2 * a + 1];
     if (lo > hi) continue;
@@ -2049,10 +2090,9 @@ __global__ void cache_closure_kernel(CacheArgs c) {
         uint32_t bit = __ffs(bits) - 1;
         bits &= bits - 1;
         uint32_t b = wi * 32 + bit;
-        if (slot0 + pos < c.n_slots) {
+        if (pos < c.front_cap) {
           c.work[2 * pos] = a;
           c.work[2 * pos + 1] = b;
-          ca.slot_of[b] = slot0 + pos;
         }
         pos++;
       }
@@ -2062,15 +2102,99 @@ __global__ void cache_closure_kernel(CacheArgs c) {
       __syncthreads();
     }
   }
+  const uint32_t n = carry;
   if (tid == 0) {
-    uint32_t n = carry;
-    if (overflow || slot0 + n > c.n_slots) {
-      record_error(&c.h->status, &c.h->err_block, &c.h->err_where, ACE_E_NOMEM, n, 51);
-      n = 0;
-    } else {
-      c.h->next_slot = slot0 + n;
+    s_taken = 0;
+    s_hand = c.h->hand;
+    s_scanned = 0;
+  }
+  __syncthreads();
+  // the clock: at most two turns over the slots (after one, every bit of a
+  // slot this batch does not use is clear)
+  const uint64_t limit = overflow || n > c.front_cap ? 0ull : 2ull * c.n_slots;
+  while (true) {
+    const uint32_t taken = s_taken, hand = s_hand, scanned = s_scanned;
+    if (taken >= n || scanned >= limit) break;
+    const uint64_t room = limit - scanned;
+    const uint32_t win = (uint32_t)min(min((uint64_t)blockDim.x, (uint64_t)c.n_slots), room);
+    const uint32_t sl = (uint32_t)(((uint64_t)hand + tid) % c.n_slots);
+    bool pinned = false, refd = false, elig = false;
+    if (tid < win) {
+      pinned = c.use[sl] == serial;
+      refd = c.ref[sl] != 0;
+      elig = !pinned && !refd;
     }
-    c.h->n_work = n;
+    const uint32_t e = elig ? 1u : 0u;
+    const uint32_t incl = warp_incl_sum(e, lane);
+    if (lane == 31) wsum[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+      uint32_t v = lane < nw ? wsum[lane] : 0;
+      uint32_t vi = warp_incl_sum(v, lane);
+      if (lane < nw) wsum[lane] = vi - v;
+      if (lane == nw - 1) s_stop = vi;  // the window's eligible total, for a moment
+    }
+    __syncthreads();
+    const uint32_t total = s_stop, rank = wsum[wid] + incl - e, rem = n - taken;
+    __syncthreads();
+    // the hand stops just after the rem-th eligible slot, else at the window's end
+    if (total >= rem) {
+      if (elig && rank == rem - 1) s_stop = tid;
+    } else if (tid == 0) {
+      s_stop = win - 1;
+    }
+    __syncthreads();
+    const uint32_t stop = s_stop;
+    if (tid <= stop && tid < win) {
+      if (!pinned && refd) c.ref[sl] = 0;  // second chance
+      if (elig && rank < rem) {
+        c.taken[taken + rank] = sl;
+        c.use[sl] = serial;  // taken: the next turn of the hand passes it over
+      }
+    }
+    __syncthreads();
+    if (tid == 0) {
+      s_taken = taken + min(total, rem);
+      s_hand = (uint32_t)(((uint64_t)hand + stop + 1) % c.n_slots);
+      s_scanned = scanned + stop + 1;
+    }
+    __syncthreads();
+  }
+  const bool fits = !overflow && n <= c.front_cap && s_taken >= n;
+  // each work item into its slot, evicting the slot's cached block
+  if (fits) {
+    for (uint32_t i = tid; i < n; i += blockDim.x) {
+      const uint32_t sl = c.taken[i], a = c.work[2 * i], b = c.work[2 * i + 1];
+      const uint32_t oa = c.owner_arc[sl], ob = c.owner_blk[sl];
+      if (oa < c.n_arcs) {
+        const CacheArc& o = c.arcs[oa];
+        if (o.slot_of[ob] == sl && o.ready[ob] == epoch) {
+          o.ready[ob] = 0;
+          atomicAdd(reinterpret_cast<unsigned long long*>(&c.h->evicted), 1ull);
+        }
+      } else {
+        atomicAdd(&c.h->n_cached, 1u);
+      }
+      c.owner_arc[sl] = a;
+      c.owner_blk[sl] = b;
+      c.use[sl] = serial;
+      c.ref[sl] = 1;
+      const CacheArc& ca = c.arcs[a];
+      ca.slot_of[b] = sl;
+      ca.wpos[b] = i;
+    }
+  }
+  __syncthreads();
+  if (tid == 0) {
+    c.h->hand = s_hand;
+    uint32_t nn = n;
+    if (!fits) {
+      record_error(&c.h->status, &c.h->err_block, &c.h->err_where, ACE_E_NOMEM, n, 51);
+      nn = 0;
+    } else {
+      c.h->decoded += n;
+    }
+    c.h->n_work = nn;
     c.h->ticket = 0;
     c.h->ticket2 = 0;
     c.h->ticket3 = 0;
@@ -2121,6 +2245,8 @@ __global__ void __launch_bounds__(256, ACE_PASS_MIN_CTAS(PASS)) cache_decode_ker
     a.ready = arc.ready;
     a.slot_of = arc.slot_of;
     a.n_slots = c.n_slots;
+    a.rec_index = arc.wpos;
+    a.n_rec_slots = c.front_cap;
     a.timeout_ns = ca.timeout_ns;
     a.recs = c.recs;
     a.match_ptr = nullptr;
@@ -2158,10 +2284,12 @@ __global__ void cache_copy_kernel(CacheArgs c, uint8_t* pool) {
   }
 }
 
-// New cache epoch: every cached block is forgotten, every slot is free.
+// New cache epoch: every cached block is forgotten, every slot is free
+// (owners left behind no longer match their blocks' flags).
 __global__ void cache_reset_kernel(CacheHdr* h) {
   h->epoch += 1;
-  h->next_slot = 0;
+  h->n_cached = 0;
+  h->hand = 0;
   h->ticket = 0;
   h->ticket2 = 0;
   h->ticket3 = 0;
@@ -3126,42 +3254,64 @@ struct ace_cache {
   CacheDecodeArgs dargs;
   Launch L;
   uint64_t req_off;  // requests are staged here by ace_seek_batch_host
+  uint64_t owner_off;  // per-slot owners, cleared by a reset
   int occ[4][9][9];
 };
 
 namespace {
 
 struct CacheLayout {
-  uint64_t arcs, minmax, front0, front1, work, reqs, warps, slots, recs, total, n_warps, max_ntok;
+  uint64_t arcs, minmax, front0, front1, work, taken, owner_arc, owner_blk, ref, use, reqs, warps, slots, recs, total,
+      n_warps, max_ntok, max_work;
 };
+
+// Blocks one seek batch may decode at most (work items): 32 per request the
+// batch may hold, at least 1024, at most the slots.  Its match records are
+// sized by it rather than by the slot count, since only the blocks a batch
+// decodes need records, and only while it runs.
+inline uint64_t cache_max_work(uint64_t n_slots, uint32_t max_reqs) {
+  return std::min<uint64_t>(n_slots, std::max<uint64_t>(1024, 32ull * max_reqs));
+}
 
 CacheLayout cache_layout(const ace_index* const* idx, uint32_t n, uint64_t n_slots, uint32_t max_reqs,
                          uint32_t log2B) {
   CacheLayout C;
   uint64_t max_ntok = 0;
   for (uint32_t i = 0; i < n; i++) max_ntok = std::max<uint64_t>(max_ntok, idx[i]->max_ntok);
+  const uint64_t mw = cache_max_work(n_slots, max_reqs);
   uint64_t o = sizeof(CacheHdr);
   C.arcs = o;
   o = align256(o + n * sizeof(CacheArc));
   C.minmax = o;
   o = align256(o + 8ull * n);
   C.front0 = o;
-  o = align256(o + 8 * n_slots);
+  o = align256(o + 8 * mw);
   C.front1 = o;
-  o = align256(o + 8 * n_slots);
+  o = align256(o + 8 * mw);
   C.work = o;
-  o = align256(o + 8 * n_slots);
+  o = align256(o + 8 * mw);
+  C.taken = o;
+  o = align256(o + 4 * mw);
+  C.owner_arc = o;
+  o = align256(o + 4 * n_slots);
+  C.owner_blk = o;
+  o = align256(o + 4 * n_slots);
+  C.ref = o;
+  o = align256(o + 4 * n_slots);
+  C.use = o;
+  o = align256(o + 4 * n_slots);
   C.reqs = o;
   o = align256(o + sizeof(ace_seek_req) * (uint64_t)max_reqs);
-  C.n_warps = std::min<uint64_t>((uint64_t)idx[0]->num_sms * kMaxWarpsPerSM, n_slots + 16);
+  C.n_warps = std::min<uint64_t>((uint64_t)idx[0]->num_sms * kMaxWarpsPerSM, mw + 16);
   C.warps = o;
   o = align256(o + C.n_warps * warp_scratch_bytes(max_ntok));
   C.slots = o;
   o = align256(o + (n_slots << log2B));
   C.recs = o;
-  o = align256(o + 16 * max_ntok * n_slots);
+  o = align256(o + 16 * max_ntok * mw);
   C.total = o;
   C.max_ntok = max_ntok;
+  C.max_work = mw;
   return C;
 }
 
@@ -3187,7 +3337,7 @@ ace_status ace_cache_size(const ace_index* const* idx, uint32_t n, uint64_t n_sl
 ace_status ace_archive_state_size(const ace_index* idx, uint64_t* bytes) {
   if (!idx || !bytes) return ACE_E_INVAL;
   uint64_t nb = idx->h.n_blocks;
-  *bytes = align256(4 * nb) * 2 + align256(4 * ((nb + 31) / 32));
+  *bytes = align256(4 * nb) * 3 + align256(4 * ((nb + 31) / 32));  // ready, slot_of, wpos; marks
   return ACE_OK;
 }
 
@@ -3215,11 +3365,10 @@ ace_status ace_cache_create(const ace_index* const* idx, uint32_t n, void* const
                        x->d_dep_iv,
                        reinterpret_cast<uint32_t*>(st),
                        reinterpret_cast<uint32_t*>(st + align256(4 * nb)),
+                       reinterpret_cast<uint32_t*>(st + 3 * align256(4 * nb)),
                        reinterpret_cast<uint32_t*>(st + 2 * align256(4 * nb)),
                        (uint32_t)nb,
-                       x->h.off_width,
-                       0,
-                       0};
+                       x->h.off_width};
     uint64_t sb = 0;
     ace_archive_state_size(x, &sb);
     if (cudaMemsetAsync(st, 0, sb, s) != cudaSuccess) return ACE_E_CUDA;
@@ -3230,22 +3379,26 @@ ace_status ace_cache_create(const ace_index* const* idx, uint32_t n, void* const
   c->n_arcs = n;
   c->log2B = log2B;
   c->n_slots = (uint32_t)n_slots;
-  c->front_cap = (uint32_t)n_slots;
+  c->front_cap = (uint32_t)C.max_work;
   c->max_reqs = max_reqs;
   c->mem = base;
   c->bytes = bytes;
   c->req_off = C.reqs;
+  c->owner_off = C.owner_arc;
   // seek batches run the three passes (their work list is in block order,
   // not level order); the fused entry only sizes like the match pass
-  rc = plan_launch(idx[0], tune, log2B, n_slots, C.n_warps, cache_decode_kernel<PASS_TOKENS>,
+  rc = plan_launch(idx[0], tune, log2B, C.max_work, C.n_warps, cache_decode_kernel<PASS_TOKENS>,
                    cache_decode_kernel<PASS_LITERALS>, cache_decode_kernel<PASS_MATCH>,
                    cache_decode_kernel<PASS_MATCH>, &c->occ[0][0][0], &c->L, kSeekRing);
   // header (epoch 1: no block is cached, since every ready flag starts at 0)
   CacheHdr h{};
   h.epoch = 1;
+  // every slot free (owner archive ~0), reference bits and batch serials 0
   if (rc == ACE_OK &&
       (cudaMemcpyAsync(base, &h, sizeof h, cudaMemcpyHostToDevice, s) != cudaSuccess ||
        cudaMemcpyAsync(base + C.arcs, arcs.data(), n * sizeof(CacheArc), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+       cudaMemsetAsync(base + C.owner_arc, 0xff, 4 * n_slots, s) != cudaSuccess ||
+       cudaMemsetAsync(base + C.ref, 0, C.reqs - C.ref, s) != cudaSuccess ||
        cudaStreamSynchronize(s) != cudaSuccess))
     rc = ACE_E_CUDA;
   if (rc) {
@@ -3258,10 +3411,15 @@ ace_status ace_cache_create(const ace_index* const* idx, uint32_t n, void* const
   a.n_arcs = n;
   a.log2B = log2B;
   a.n_slots = (uint32_t)n_slots;
-  a.front_cap = (uint32_t)n_slots;
+  a.front_cap = (uint32_t)C.max_work;
   a.front0 = reinterpret_cast<uint32_t*>(base + C.front0);
   a.front1 = reinterpret_cast<uint32_t*>(base + C.front1);
   a.work = reinterpret_cast<uint32_t*>(base + C.work);
+  a.taken = reinterpret_cast<uint32_t*>(base + C.taken);
+  a.owner_arc = reinterpret_cast<uint32_t*>(base + C.owner_arc);
+  a.owner_blk = reinterpret_cast<uint32_t*>(base + C.owner_blk);
+  a.ref = reinterpret_cast<uint32_t*>(base + C.ref);
+  a.use = reinterpret_cast<uint32_t*>(base + C.use);
   a.arc_minmax = reinterpret_cast<uint32_t*>(base + C.minmax);
   a.slots = base + C.slots;
   a.recs = reinterpret_cast<MatchRec*>(base + C.recs);
@@ -3331,7 +3489,7 @@ ace_status ace_cache_usage(const ace_cache* c, uint32_t* used_slots, uint32_t* n
   CacheHdr h;
   ace_status rc = read_header(c->mem, &h, sizeof h, s);
   if (rc) return rc;
-  if (used_slots) *used_slots = h.next_slot;
+  if (used_slots) *used_slots = h.n_cached;
   if (n_slots) *n_slots = c->n_slots;
   return ACE_OK;
 }
@@ -3340,6 +3498,25 @@ ace_status ace_cache_reset(const ace_cache* c, cudaStream_t s) {
   if (!c) return ACE_E_INVAL;
   cache_reset_kernel<<<1, 1, 0, s>>>(c->args.h);
   CUDA_TRY(cudaGetLastError());
+  CUDA_TRY(cudaMemsetAsync(c->mem + c->owner_off, 0xff, 4ull * c->n_slots, s));
+  return ACE_OK;
+}
+
+ace_status ace_cache_counters(const ace_cache* c, uint64_t* h_evicted, uint64_t* h_decoded, cudaStream_t s) {
+  if (!c) return ACE_E_INVAL;
+  CacheHdr h;
+  ace_status rc = read_header(c->mem, &h, sizeof h, s);
+  if (rc) return rc;
+  if (h_evicted) *h_evicted = h.evicted;
+  if (h_decoded) *h_decoded = h.decoded;
+  return ACE_OK;
+}
+
+ace_status ace_cache_limits(const ace_cache* c, uint32_t* h_n_slots, uint32_t* h_max_work, uint32_t* h_max_reqs) {
+  if (!c) return ACE_E_INVAL;
+  if (h_n_slots) *h_n_slots = c->n_slots;
+  if (h_max_work) *h_max_work = c->front_cap;
+  if (h_max_reqs) *h_max_reqs = c->max_reqs;
   return ACE_OK;
 }
 

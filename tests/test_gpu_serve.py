@@ -63,16 +63,50 @@ def test_seek_batch_equals_originals_and_single_seeks():
     c.close()
 
 
-def test_cache_exhaustion_reports_nomem_and_recovers():
+def test_cache_exhaustion_reports_nomem_and_stays_valid():
+    """A batch whose new blocks exceed the slots is refused with ACE_E_NOMEM
+    and copies nothing; the cache stays valid without a reset, and
+    run_batch serves a refused batch in halves."""
     datas, das = _archives(2_000_000, profiles=("mixed", "text"))
     c = SeekCache(das, n_slots=40, max_reqs=64, pool_bytes=8 << 20)
     r = c.plan([(0, 0, 30 * 16384), (1, 0, 30 * 16384)])  # 60 target blocks > 40 slots
     c.submit(r)
     assert c.sync() == ace.ACE_E_NOMEM
-    c.reset()
     outs = c.seek_many([(0, 16384 * 3, 20000), (1, 5, 16384 * 10)])
     assert np.array_equal(outs[0].cpu().numpy(), datas[0][16384 * 3:16384 * 3 + 20000])
     assert np.array_equal(outs[1].cpu().numpy(), datas[1][5:5 + 16384 * 10])
+    reqs = [(0, 16384 * 20, 16384 * 16), (1, 16384 * 40, 16384 * 16), (0, 16384 * 40, 16384 * 16)]
+    r = c.plan(reqs)
+    c.submit(r)  # 48 new blocks in one batch: more than the 40 slots
+    assert c.sync() == ace.ACE_E_NOMEM
+    c.run_batch(r)  # refused whole, served in halves (16 blocks, then 32)
+    for q, (a, co, n) in zip(r, reqs):
+        o = int(q["out_off"])
+        assert np.array_equal(c.pool[o:o + n].cpu().numpy(), datas[a][co:co + n])
+    c.close()
+
+
+def test_cache_evicts_least_recently_used_blocks():
+    """Many batches over more distinct blocks than the cache holds: blocks
+    are evicted by the clock (no reset), every result stays exact, and the
+    slots a batch reads from are never taken by its own new blocks."""
+    datas, das = _archives(3_000_000, profiles=("fastq", "text", "genome"))
+    c = SeekCache(das, n_slots=400, max_reqs=64, pool_bytes=16 << 20)
+    rng = np.random.default_rng(1)
+    for it in range(60):
+        reqs = []
+        for _ in range(int(rng.integers(1, 12))):
+            a = int(rng.integers(0, len(das)))
+            n = int(rng.integers(1, 120_000))
+            co = int(rng.integers(0, len(datas[a]) - n))
+            reqs.append((a, co, n))
+        outs = c.seek_many(reqs)
+        for (a, co, n), o in zip(reqs, outs):
+            assert np.array_equal(o.cpu().numpy(), datas[a][co:co + n]), (it, a, co, n)
+    evicted, decoded = c.counters()
+    used, n_slots = ace.ace_cache_usage(c.cache)
+    assert evicted > 0 and decoded > n_slots
+    assert used == n_slots == 400
     c.close()
 
 
