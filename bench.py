@@ -22,9 +22,12 @@ Also measured, each at the size its configuration states:
     launch sequence per object;
   - serving: 8 resident archives of 5 GiB (40 GiB decompressed) under a
     20 GB device working-set budget, Poisson arrivals 10k - 1M requests/s;
+  - beyond device memory: a 50 GB genome whose archive stays in host
+    memory, the range decode of blocks 0..1000 and a long range streamed to
+    host memory in sub-ranges;
   - the oracle on the host cores beside each decode.
---quick caps the batched objects at 2 MiB and the served archives at
-256 MiB (labelled as reduced in the output).
+--quick caps the batched objects at 2 MiB, the served archives at 256 MiB
+and the host-resident genome at 4 GiB (labelled as reduced in the output).
 
 Prints one JSON line.  Under torchrun each rank decodes its own replica
 (replicas only: no data-path collective).
@@ -582,7 +585,7 @@ def measure_batched(ace, dev, stream, flush, max_size, reduced):
            "per_object_launches_ms": per_obj_ms, "per_object_GBps": btotal / (per_obj_ms / 1e3) / 1e9,
            "roofline_whole": {"algorithmic_bytes": alg, "achieved_gbs": alg / (gms / 1e3) / 1e9,
                               "peak": peaks["hbm_gbs"], "frac": alg / (gms / 1e3) / 1e9 / peaks["hbm_gbs"]},
-           "tuned": {k_: tuned[k_] for k_ in ("warps_per_cta", "window", "schedule")},
+           "tuned": {k_: tuned[k_] for k_ in ("warps_per_cta", "window", "schedule", "copy_width")},
            "host_prep_s": prep_s,
            "cpu_baseline": {"value": acc / odt / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
                             "sample": "the first %d objects (%d bytes), one thread (%.2f s)" % (k, acc, odt)}}
@@ -659,6 +662,72 @@ def measure_serve(ace, DeviceArchive, dev, arch_bytes, budget, reduced):
     return out
 
 
+def measure_beyond_vram(ace, dev, stream, total_bytes, reduced):
+    """Range decode of an archive kept in host memory (the paper's 50 GB
+    genome case, where output plus archive exceed a GPU's memory): the
+    archive's bytes pinned and mapped, read by the GPU in place; the index
+    built on the device.  Times the range decode of blocks 0..1000, a long
+    range streamed to host memory in sub-ranges, and a whole decode into
+    device memory with the archive still on the host."""
+    import torch
+    import synth
+    from paper_2606_24531_gb300.archive import HostArchive
+
+    t0 = time.perf_counter()
+    data = synth.generate("genome", total_bytes, 3)
+    arc = ace.ace_encode(data, 14, 20, off_width=5 if total_bytes > (1 << 32) else 0)
+    prep_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    ha = HostArchive(arc, max_seek_blocks=4096, device=dev)
+    index_ms = 1e3 * (time.perf_counter() - t0)
+    B = ha.block_size
+    first = torch.empty(1001 * B, dtype=torch.uint8, device=dev)
+    lat = []
+    for k in range(13):
+        t1 = time.perf_counter()
+        ace.ace_seek(ha.idx, 0, 1001 * B, first, first.numel(), ha.d_scratch, ha.scratch_bytes, stream)
+        st = ace.ace_sync(ha.idx, ha.d_scratch, stream)
+        lat.append(time.perf_counter() - t1)
+        assert st == ace.ACE_OK
+    assert torch.equal(first, torch.from_numpy(data[:1001 * B]).to(dev))
+    span = min(8 << 30, ha.total)
+    h_out = torch.empty(span, dtype=torch.uint8).pin_memory()
+    ha.decode_range_to_host(0, 64 * B, h_out[:64 * B], chunk_blocks=4096)  # warm-up
+    t1 = time.perf_counter()
+    ha.decode_range_to_host(0, span, h_out, chunk_blocks=4096)
+    stream_s = time.perf_counter() - t1
+    hv = h_out.numpy()
+    for c in np.linspace(0, span - 4096, 64).astype(np.int64):
+        assert np.array_equal(hv[c:c + 4096], data[c:c + 4096]), "streamed range differs at %d" % c
+    del h_out, hv
+    whole = None
+    free, _ = torch.cuda.mem_get_info(dev)
+    if ha.total + (2 << 30) < free:
+        out = torch.empty(ha.total, dtype=torch.uint8, device=dev)
+        ha.decode_all(out)
+        assert ha.sync() == ace.ACE_OK
+        ms = timed(stream, lambda: ha.decode_all(out), 3, 1)
+        assert ha.sync() == ace.ACE_OK
+        for c in np.linspace(0, ha.total - 4096, 64).astype(np.int64):
+            assert torch.equal(out[c:c + 4096].cpu(), torch.from_numpy(data[c:c + 4096]))
+        whole = {"ms": statistics.median(ms), "GBps": ha.total / (statistics.median(ms) / 1e3) / 1e9,
+                 "where": "archive in host memory, output in device memory"}
+        del out
+    res = {"workload": "genome-%dB-16KiB-blocks-host-resident%s" % (total_bytes, "-reduced" if reduced else ""),
+           "bytes": ha.total, "blocks": ha.info["n_blocks"], "archive_bytes": int(arc.size),
+           "index_build_ms": index_ms, "host_prep_s": prep_s,
+           "range_blocks_0_1000": {"p50_ms": 1e3 * float(np.percentile(lat[3:], 50)),
+                                   "p99_ms": 1e3 * float(np.percentile(lat[3:], 99)),
+                                   "paper_context_ms": 0.654},
+           "streamed_to_host": {"bytes": span, "seconds": stream_s, "GBps": span / stream_s / 1e9,
+                                "sub_range_blocks": 4096},
+           "whole_decode": whole}
+    ha.close()
+    del data, arc
+    torch.cuda.empty_cache()
+    return res
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -671,6 +740,7 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="decode steps only (for profiler runs)")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched measurement")
+    ap.add_argument("--no-beyond-vram", action="store_true", help="skip the host-resident range decode")
     ap.add_argument("--quick", action="store_true",
                     help="reduced batched (2 MiB objects) and serving (256 MiB archives) configurations")
     args = ap.parse_args()
@@ -791,6 +861,9 @@ def main():
             else:
                 cfgs["serve"] = measure_serve(ace, DeviceArchive, dev, 5 << 30, 20 * 10**9, False)
             torch.cuda.empty_cache()
+        if not args.no_beyond_vram:
+            cfgs["beyond_vram"] = measure_beyond_vram(ace, dev, stream, (4 << 30) if args.quick else 50 * 10**9,
+                                                      args.quick)
         result["configs"] = cfgs
     if rank == 0:
         print(json.dumps(result), flush=True)

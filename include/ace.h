@@ -63,6 +63,8 @@ typedef struct {
     uint32_t threads;    /* host threads; 0 = all hardware threads */
     uint32_t max_chain;  /* candidates tried per position in the in-block chain */
     uint32_t off_width;  /* absolute-offset bytes: 0 = 4 up to 2^32 input bytes, else 5; 5 forces 5; 4 above 2^32 is ACE_E_INVAL */
+    uint32_t adaptive;   /* 1: store a block's stream verbatim (mode 1) when its rANS coding takes at least as many
+                            bytes as its symbols (Section 6.1: entropy coding pays only on some streams); 0: rANS always */
 } ace_encode_params;
 
 /*
@@ -106,6 +108,36 @@ typedef struct {
     uint32_t reserved;
 } ace_encode_stats;
 ace_status ace_encode_get_stats(const ace_encoder *enc, ace_encode_stats *h_stats);
+
+/*
+ * GPU encoder: the whole encode on the device, from d_in[0, n) (device
+ * memory) to an archive in d_arc (device memory, 256-byte aligned) in the
+ * layout of ace_format.h.  Section 2's global match search as a table of
+ * the earliest occurrence of every 16-byte key at 8-byte strides (built with
+ * atomic minima), in-block repeats through 4-byte hash chains (a warp per
+ * block), candidates measured for every position at once (a thread per
+ * position), then a greedy walk per block (a thread per block) that takes
+ * the longest allowed candidate, refusing in-block resolution waves deeper
+ * than 3 and preferring a shallower candidate nearly as long; blocks in
+ * windows of 64 that take no sources from each other, the first three
+ * windows in order, every later block taking external sources only from
+ * them (dependency levels at most 3).  Each block's literal, length and
+ * offset streams rANS-coded by a warp (Section 3; the host encoder's
+ * frequency quantisation, 32 interleaved states), stored verbatim with
+ * params->adaptive where rANS would not shrink them (Section 6.1).  The
+ * parse differs from the host encoder's; every decoder reads both.
+ * params->threads is read as the blocks parsed per launch (0: 64 MiB of
+ * input's worth); max_chain <= 64.  ace_encode_gpu_size gives the scratch
+ * (256-byte aligned) and a d_arc size that always suffices; a smaller d_arc
+ * may do (the archive plus room for the largest dependency table), and the
+ * call returns ACE_E_NOMEM when it does not.  Synchronises s; *h_arc_len
+ * gets the archive's bytes, h_stats (may be NULL) the parse statistics.
+ */
+ace_status ace_encode_gpu_size(uint64_t n, const ace_encode_params *params, uint64_t *scratch_bytes,
+                               uint64_t *arc_bound);
+ace_status ace_encode_gpu(const void *d_in, uint64_t n, const ace_encode_params *params, void *d_scratch,
+                          uint64_t scratch_bytes, void *d_arc, uint64_t arc_cap, uint64_t *h_arc_len,
+                          ace_encode_stats *h_stats, cudaStream_t s);
 
 /* ------------------------------------------------------------ the index */
 
@@ -156,6 +188,42 @@ ace_status ace_index_levels(const ace_index *idx, uint32_t *h_counts, uint32_t n
 /* Releases the host handle; the caller frees the device buffers. */
 ace_status ace_index_free(ace_index *idx);
 
+/*
+ * A stored index: the index memory written to host bytes (h_blob, for a
+ * file) so that a later process loads it instead of rebuilding it (the
+ * storage format of Section 8's next step: a prepared archive and its index
+ * loaded from disk).  ace_index_export_size gives the bytes;
+ * ace_index_export copies the index memory after a 256-byte header holding
+ * the archive's header and an FNV-1a 64 of the index bytes, and
+ * synchronises s.  ace_index_import takes the same arguments as
+ * ace_index_build plus the blob: it checks that the blob belongs to this
+ * archive and is whole (ACE_E_CORRUPT otherwise), copies it to d_index_mem,
+ * and, instead of iterating the level rule, verifies the stored levels
+ * against the archive's dependency table in one sweep and the stored order
+ * as a level-sorted permutation of the blocks; the archive's directory is
+ * validated as at a build.  Synchronises s; on success *out is a new handle.
+ */
+ace_status ace_index_export_size(const ace_index *idx, uint64_t *bytes);
+ace_status ace_index_export(const ace_index *idx, void *h_blob, uint64_t blob_bytes, cudaStream_t s);
+ace_status ace_index_import(const void *d_archive, uint64_t archive_bytes, const void *h_header, uint64_t header_bytes,
+                            const void *h_blob, uint64_t blob_bytes, void *d_index_mem, uint64_t index_bytes,
+                            cudaStream_t s, ace_index **out);
+
+/*
+ * Archives larger than device memory (Section 7: the output and the archive
+ * together exceed VRAM, so ranges are decoded instead).  The archive may
+ * stay in host memory: ace_host_register pins and maps h_p[0, bytes) (a file
+ * read or mapped into memory) and returns in *d_p the address the GPU reads
+ * it through (over the chip-to-chip link on Grace hosts); pass *d_p as
+ * d_archive to ace_index_build or ace_index_import, and seek ranges of it as
+ * usual.  read_only = 1 for archives (the GPU never writes them); 0 for a
+ * host buffer that decodes write into.  ace_host_unregister undoes it, after
+ * every call that reads the memory has finished.  This pins host memory; it
+ * allocates no device memory.  ACE_E_CUDA when the runtime refuses.
+ */
+ace_status ace_host_register(void *h_p, uint64_t bytes, uint32_t read_only, void **d_p);
+ace_status ace_host_unregister(void *h_p);
+
 /* ------------------------------------------------------------- scratch */
 
 /*
@@ -193,11 +261,15 @@ typedef struct {
     uint32_t chunk_tokens;    /* tokens staged per step, 32..256, multiple of 32; 0 = 128 */
     uint32_t schedule;        /* ACE_SCHEDULE_*; 0 = automatic; others: ACE_E_INVAL */
     uint64_t wait_timeout_ns; /* bound on each device-side wait; 0 = 2 s */
+    uint32_t copy_width;      /* match copies: 16 = every non-overlapping match above 32 bytes in aligned
+                                 16-byte pieces; 8 = 8-byte words up to 32 bytes, bytewise up to 511,
+                                 16-byte pieces from 512; 0 = the library's choice; others: ACE_E_INVAL */
+    uint32_t reserved;        /* 0 */
 } ace_tune;
 
 /*
  * Whole-archive decode through both layers (Sections 2-3) into d_out
- * (out_bytes >= total_size), on s.  Each block's length and offset streams
+ * (16-byte aligned, out_bytes >= total_size), on s.  Each block's length and offset streams
  * are rANS-decoded into one record per match (absolute source, destination,
  * length), its literal stream is decoded straight to its positions in
  * d_out, and its absolute-offset matches are resolved once the blocks they
@@ -260,12 +332,14 @@ ace_status ace_sync(const ace_index *idx, void *d_scratch, cudaStream_t s);
  *
  * ace_batch_scratch_size sizes the batch scratch (256-byte aligned).
  * ace_batch_create records the archives (all on the current device) and
- * their outputs (out_bytes[i] >= the archive's total size) in the scratch,
+ * their outputs (16-byte aligned, out_bytes[i] >= the archive's total size;
+ * ACE_E_INVAL for an unaligned one) in the scratch,
  * plans the launch from tune (NULL = defaults), and synchronises s.  It
- * allocates no device memory.  ace_decode_batch then enqueues exactly four
- * kernels on s (a header reset and the token, literal and match passes) and
- * no host synchronisation, so it can be captured into a CUDA graph and
- * replayed; each replay decodes every archive again.
+ * allocates no device memory.  ace_decode_batch then enqueues, with no host
+ * synchronisation, a header reset and the token, literal and match passes
+ * (pass schedule) or a memset of the level counters, a header reset and one
+ * fused launch (ACE_SCHEDULE_FUSED), so it can be captured into a CUDA graph
+ * and replayed; each replay decodes every archive again.
  * ace_batch_sync synchronises s and returns (then clears) the first device
  * error.  ace_batch_launch_shape reports the planned grid, warps per CTA and
  * token window.

@@ -26,9 +26,9 @@
  *                             multiple of 8 entries (16 bytes)
  *   u8  renorm[]              renormalisation bytes in decode order
  * Stream payload (mode 1, stored): the nsym symbols verbatim,
- *   stream_bytes = nsym; for streams that rANS would not shrink (entropy
- *   coding chosen per stream at encode time).  The oracle reads it; this
- *   library's index build still rejects it as corrupt.
+ *   stream_bytes = nsym, 16-byte aligned like every stream; for streams that
+ *   rANS would not shrink (entropy coding chosen per stream at encode time,
+ *   Section 6.1).
  * A stream with nsym = 0 has stream_bytes = 0 and no payload.
  *
  * Token streams of one block:
@@ -83,7 +83,7 @@ typedef struct {
     uint32_t nsym[3];
     uint32_t ntok;
     uint32_t nesc;
-    uint8_t mode[3];          /* 0 = rANS, 1 = stored (not yet decoded here); others rejected */
+    uint8_t mode[3];          /* 0 = rANS, 1 = stored; others rejected */
     uint8_t reserved[5];
 } ace_block_dir; /* 64 bytes */
 

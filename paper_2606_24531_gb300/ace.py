@@ -27,7 +27,7 @@ class AceError(RuntimeError):
 class ace_encode_params(ctypes.Structure):
     _fields_ = [("log2_block", ctypes.c_uint32), ("min_match", ctypes.c_uint32),
                 ("threads", ctypes.c_uint32), ("max_chain", ctypes.c_uint32),
-                ("off_width", ctypes.c_uint32)]
+                ("off_width", ctypes.c_uint32), ("adaptive", ctypes.c_uint32)]
 
 
 class ace_encode_stats(ctypes.Structure):
@@ -47,7 +47,8 @@ class ace_info(ctypes.Structure):
 class ace_tune(ctypes.Structure):
     _fields_ = [("warps_per_cta", ctypes.c_uint32), ("ctas_per_sm", ctypes.c_uint32),
                 ("chunk_tokens", ctypes.c_uint32), ("schedule", ctypes.c_uint32),
-                ("wait_timeout_ns", ctypes.c_uint64)]
+                ("wait_timeout_ns", ctypes.c_uint64), ("copy_width", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32)]
 
 
 class ace_verify_report(ctypes.Structure):
@@ -69,11 +70,19 @@ _SIGS = {
     "ace_encode_write": ([_vp, _vp, _u64], _i32),
     "ace_encode_free": ([_vp], _i32),
     "ace_encode_get_stats": ([_vp, _P(ace_encode_stats)], _i32),
+    "ace_encode_gpu_size": ([_u64, _P(ace_encode_params), _P(_u64), _P(_u64)], _i32),
+    "ace_encode_gpu": ([_vp, _u64, _P(ace_encode_params), _vp, _u64, _vp, _u64, _P(_u64), _P(ace_encode_stats), _vp],
+                       _i32),
     "ace_index_size": ([_vp, _u64, _P(_u64)], _i32),
     "ace_index_build": ([_vp, _u64, _vp, _u64, _vp, _u64, _vp, _P(_vp)], _i32),
     "ace_index_info": ([_vp, _P(ace_info)], _i32),
     "ace_index_levels": ([_vp, _P(_u32), _u32, _vp], _i32),
     "ace_index_free": ([_vp], _i32),
+    "ace_index_export_size": ([_vp, _P(_u64)], _i32),
+    "ace_index_export": ([_vp, _vp, _u64, _vp], _i32),
+    "ace_index_import": ([_vp, _u64, _vp, _u64, _vp, _u64, _vp, _u64, _vp, _P(_vp)], _i32),
+    "ace_host_register": ([_vp, _u64, _u32, _P(_vp)], _i32),
+    "ace_host_unregister": ([_vp], _i32),
     "ace_scratch_size": ([_vp, _u64, _P(_u64)], _i32),
     "ace_scratch_init": ([_vp, _vp, _u64, _vp], _i32),
     "ace_decode_all": ([_vp, _vp, _u64, _vp, _u64, _P(ace_tune), _vp], _i32),
@@ -161,13 +170,14 @@ def ace_encode_bound(n, log2_block):
     return out.value
 
 
-def ace_encode(h_in, log2_block=14, min_match=4, threads=0, max_chain=16, stats=False, off_width=0):
+def ace_encode(h_in, log2_block=14, min_match=4, threads=0, max_chain=16, stats=False, off_width=0, adaptive=False):
     """Encode host bytes (numpy uint8) into an archive (numpy uint8) on the
     CPU; with stats=True also return the parse statistics as a dict.
     off_width: absolute-offset bytes, 0 for the smallest that fits (4 up to
-    2^32 bytes of input, else 5), or 5 to force five."""
+    2^32 bytes of input, else 5), or 5 to force five.  adaptive: store each
+    block's stream verbatim when rANS would not shrink it."""
     a = np.ascontiguousarray(h_in, dtype=np.uint8)
-    prm = ace_encode_params(log2_block, min_match, threads, max_chain, off_width)
+    prm = ace_encode_params(log2_block, min_match, threads, max_chain, off_width, 1 if adaptive else 0)
     enc, n = _vp(), _u64()
     _check(lib().ace_encode_run(a.ctypes.data, a.size, ctypes.byref(prm), ctypes.byref(enc),
                                 ctypes.byref(n)), "ace_encode_run")
@@ -181,6 +191,50 @@ def ace_encode(h_in, log2_block=14, min_match=4, threads=0, max_chain=16, stats=
     if stats:
         return arc, {k: getattr(st, k) for k, _ in ace_encode_stats._fields_ if k != "reserved"}
     return arc
+
+
+def ace_encode_gpu(d_in, log2_block=14, min_match=4, max_chain=16, stats=False, off_width=0, adaptive=False,
+                   chunk_blocks=0, stream=None):
+    """Encode device bytes (a uint8 CUDA tensor) into an archive on the same
+    device; returns the archive as a CUDA tensor view (and, with stats=True,
+    the parse statistics).  Scratch and archive memory come from PyTorch:
+    first a buffer for the archive at about the input's size plus the
+    dependency table's room, and the bound when that is too small."""
+    import torch
+
+    n = d_in.numel()
+    prm = ace_encode_params(log2_block, min_match, chunk_blocks, max_chain, off_width, 1 if adaptive else 0)
+    sb, bound = _u64(), _u64()
+    _check(lib().ace_encode_gpu_size(n, ctypes.byref(prm), ctypes.byref(sb), ctypes.byref(bound)),
+           "ace_encode_gpu_size")
+    scratch = torch.empty(sb.value, dtype=torch.uint8, device=d_in.device)
+    nb = (n + (1 << log2_block) - 1) >> log2_block
+    reserve = bound.value - _enc_payload_room(nb, log2_block, min_match)  # header, directory, dependency room
+    guess = min(bound.value, reserve + n + n // 8 + nb * 2048 + (1 << 20))
+    for cap in (guess, bound.value):
+        arc = torch.empty(cap, dtype=torch.uint8, device=d_in.device)
+        ln, st = _u64(), ace_encode_stats()
+        rc = lib().ace_encode_gpu(_ptr(d_in), n, ctypes.byref(prm), _ptr(scratch), sb.value, _ptr(arc), cap,
+                                  ctypes.byref(ln), ctypes.byref(st), _stream(stream))
+        if rc == ACE_E_NOMEM and cap < bound.value:
+            del arc
+            continue
+        _check(rc, "ace_encode_gpu")
+        out = arc[:ln.value]
+        if stats:
+            return out, {k: getattr(st, k) for k, _ in ace_encode_stats._fields_ if k != "reserved"}
+        return out
+    raise AssertionError("unreachable")
+
+
+def _enc_payload_room(nb, log2_block, min_match):
+    """The part of the GPU encoder's archive bound that is payload room (the
+    bound less the header, directory and dependency-table room)."""
+    B = 1 << log2_block
+    tok_cap = B // min_match + 2
+    sym_cap = (B + 11 * tok_cap + 15) & ~15
+    pay_cap = (3 * (160 + 512 + 16) + 2 * sym_cap + 64 + 15) & ~15
+    return nb * pay_cap + 256
 
 
 # --------------------------------------------------------------------- index
@@ -219,6 +273,37 @@ def ace_index_free(idx):
     lib().ace_index_free(idx)
 
 
+def ace_index_export(idx, stream=None):
+    """The stored form of an index (numpy uint8), for a file."""
+    n = _u64()
+    _check(lib().ace_index_export_size(idx, ctypes.byref(n)), "ace_index_export_size")
+    blob = np.empty(n.value, np.uint8)
+    _check(lib().ace_index_export(idx, blob.ctypes.data, blob.size, _stream(stream)), "ace_index_export")
+    return blob
+
+
+def ace_index_import(d_archive, archive_bytes, h_header, h_blob, d_index_mem, index_bytes, stream=None):
+    h = np.ascontiguousarray(h_header[:64], dtype=np.uint8)
+    b = np.ascontiguousarray(h_blob, dtype=np.uint8)
+    out = _vp()
+    _check(lib().ace_index_import(_ptr(d_archive), archive_bytes, h.ctypes.data, h.size, b.ctypes.data, b.size,
+                                  _ptr(d_index_mem), index_bytes, _stream(stream), ctypes.byref(out)),
+           "ace_index_import")
+    return out
+
+
+def ace_host_register(h_array, read_only=True):
+    """Pins and maps a host numpy array; returns the device address of it."""
+    d = _vp()
+    _check(lib().ace_host_register(h_array.ctypes.data, h_array.nbytes, 1 if read_only else 0, ctypes.byref(d)),
+           "ace_host_register")
+    return d.value
+
+
+def ace_host_unregister(h_array):
+    _check(lib().ace_host_unregister(h_array.ctypes.data), "ace_host_unregister")
+
+
 def ace_scratch_size(idx, max_seek_blocks=0):
     out = _u64()
     _check(lib().ace_scratch_size(idx, max_seek_blocks, ctypes.byref(out)), "ace_scratch_size")
@@ -231,8 +316,8 @@ def ace_scratch_init(idx, d_scratch, scratch_bytes, stream=None):
 
 # ------------------------------------------------------------------ decoding
 
-def make_tune(warps_per_cta=0, ctas_per_sm=0, chunk_tokens=0, wait_timeout_ns=0, schedule=0):
-    return ace_tune(warps_per_cta, ctas_per_sm, chunk_tokens, schedule, wait_timeout_ns)
+def make_tune(warps_per_cta=0, ctas_per_sm=0, chunk_tokens=0, wait_timeout_ns=0, schedule=0, copy_width=0):
+    return ace_tune(warps_per_cta, ctas_per_sm, chunk_tokens, schedule, wait_timeout_ns, copy_width, 0)
 
 
 def ace_decode_all(idx, d_out, out_bytes, d_scratch, scratch_bytes, tune=None, stream=None):

@@ -71,11 +71,12 @@ TUNE_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "ace_gb300", "tune.
 
 
 def autotune(db, candidates=None, reps=3, cache_key=None, cache_path=TUNE_CACHE):
-    """Times each (warps per CTA, token window, schedule) candidate on the
-    batch and keeps the fastest; results are cached by cache_key in a JSON
-    file."""
+    """Times each (warps per CTA, token window, schedule, copy width)
+    candidate on the batch and keeps the fastest; results are cached by
+    cache_key in a JSON file."""
     def tune_of(c):
-        return ace.make_tune(c["warps_per_cta"], 0, c["window"], schedule=c.get("schedule", 0))
+        return ace.make_tune(c["warps_per_cta"], 0, c["window"], schedule=c.get("schedule", 0),
+                             copy_width=c.get("copy_width", 0))
 
     if cache_key is not None and os.path.exists(cache_path):
         try:
@@ -87,15 +88,16 @@ def autotune(db, candidates=None, reps=3, cache_key=None, cache_path=TUNE_CACHE)
         except (OSError, ValueError):
             pass
     if candidates is None:
-        candidates = [(w, c, s) for s in (ace.ACE_SCHEDULE_PASSES, ace.ACE_SCHEDULE_FUSED)
-                      for w in (1, 2, 4, 8) for c in (64, 128, 256)]
+        candidates = [(w, c, s, cw) for s in (ace.ACE_SCHEDULE_PASSES, ace.ACE_SCHEDULE_FUSED)
+                      for w in (1, 2, 4, 8) for c in (64, 128, 256) for cw in (8, 16)]
     best = None
     results = []
     for cand in candidates:
         w, c = cand[0], cand[1]
         sch = cand[2] if len(cand) > 2 else ace.ACE_SCHEDULE_PASSES
+        cw = cand[3] if len(cand) > 3 else 0
         try:
-            db.retune(ace.make_tune(w, 0, c, schedule=sch))
+            db.retune(ace.make_tune(w, 0, c, schedule=sch, copy_width=cw))
         except ace.AceError:
             continue
         db.decode()
@@ -110,7 +112,7 @@ def autotune(db, candidates=None, reps=3, cache_key=None, cache_path=TUNE_CACHE)
             e1.synchronize()
             times.append(e0.elapsed_time(e1))
         ms = float(np.median(times))
-        row = {"warps_per_cta": w, "window": c, "schedule": sch, "ms": ms}
+        row = {"warps_per_cta": w, "window": c, "schedule": sch, "copy_width": cw, "ms": ms}
         results.append(row)
         if best is None or ms < best["ms"]:
             best = dict(row)

@@ -19,7 +19,7 @@ BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libace.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-CU_SOURCES = ["ace.cu"]
+CU_SOURCES = ["ace.cu", "encoder_gpu.cu"]
 CPP_SOURCES = ["encoder.cpp"]
 
 

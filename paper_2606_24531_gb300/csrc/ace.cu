@@ -66,10 +66,11 @@ __global__ void validate_kernel(IndexArgs a) {
   uint64_t blen = min(B, a.total - bstart);
   uint32_t where = 0;
   for (int k = 0; k < 3 && !where; k++) {
-    if (d.mode[k] != 0) where = 1;
+    if (d.mode[k] > 1) where = 1;  // 0: rANS, 1: stored
     else if (d.nsym[k] == 0 && d.stream_bytes[k] != 0) where = 2;
     else if (d.nsym[k] != 0) {
-      if (d.stream_bytes[k] < ACE_STREAM_HEAD || (d.stream_off[k] & 15)) where = 3;
+      if (d.mode[k] == 1 ? d.stream_bytes[k] != d.nsym[k] : d.stream_bytes[k] < ACE_STREAM_HEAD) where = 3;
+      else if (d.stream_off[k] & 15) where = 3;
       else if (a.payload_off + d.stream_off[k] + d.stream_bytes[k] > a.arc_bytes ||
                d.stream_off[k] > a.arc_bytes)
         where = 4;
@@ -240,6 +241,50 @@ __global__ void level_scatter_kernel(IndexArgs a) {
   if (b < a.nb) a.order[atomicAdd(&a.lv_cursor[a.level[b]], 1u)] = (uint32_t)b;
 }
 
+// An index read back from storage, checked against its archive instead of
+// rebuilt.  Each block's level must be the fixed point of the level rule
+// (0 without dependencies, else 1 + the deepest block it reads): one sweep
+// verifies what the build reaches by iterating.  A warp per block.
+__global__ void level_verify_kernel(IndexArgs a) {
+  if (*(volatile uint32_t*)&a.ih->status) return;
+  const uint32_t lane = threadIdx.x & 31;
+  const uint64_t nw = (uint64_t)gridDim.x * (blockDim.x >> 5);
+  for (uint64_t b = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5; b < a.nb; b += nw) {
+    uint32_t lv = 0;
+    const uint32_t e1 = a.dep_ptr[b + 1];
+    for (uint32_t e = a.dep_ptr[b] + lane; e < e1; e += 32)
+      for (uint32_t k = a.dep_iv[2 * e]; k <= a.dep_iv[2 * e + 1]; k++) lv = max(lv, a.level[k] + 1);
+#pragma unroll
+    for (int d = 16; d; d >>= 1) lv = max(lv, __shfl_xor_sync(kFull, lv, d));
+    if (lane == 0 && (lv != a.level[b] || lv >= a.ih->n_levels))
+      record_error(&a.ih->status, &a.ih->err_block, &a.ih->err_where, ACE_E_CORRUPT, (uint32_t)b, 60);
+  }
+}
+
+// The decode order of a stored index: a permutation of the blocks (seen
+// marks each once), in non-decreasing level, position i inside its level's
+// range of the order (the level's end in lv_cursor, its size in lv_count).
+__global__ void order_verify_kernel(IndexArgs a, uint32_t* seen) {
+  if (*(volatile uint32_t*)&a.ih->status) return;
+  const uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  // the first levels' sizes in the header (the host's level ranges) match
+  if (i < 33 && i < a.ih->n_levels && i <= a.nb && a.ih->lvc[i] != a.lv_count[i])
+    record_error(&a.ih->status, &a.ih->err_block, &a.ih->err_where, ACE_E_CORRUPT, (uint32_t)i, 62);
+  if (i >= a.nb) return;
+  const uint32_t b = a.order[i];
+  bool bad = b >= a.nb;
+  if (!bad) {
+    bad = atomicExch(seen + b, 1u) != 0;
+    const uint32_t L = a.level[b];
+    bad |= L >= a.ih->n_levels || L > a.nb;
+    if (!bad) {
+      const uint32_t end = a.lv_cursor[L], cnt = a.lv_count[L];
+      bad |= i >= end || end < cnt || i < end - cnt;
+    }
+  }
+  if (bad) record_error(&a.ih->status, &a.ih->err_block, &a.ih->err_where, ACE_E_CORRUPT, (uint32_t)i, 61);
+}
+
 // ----------------------------------------------------------- decode kernel
 
 struct DecodeArgs {
@@ -278,6 +323,7 @@ struct DecodeArgs {
   // seek batches: match records per work item rather than per slot
   const uint32_t* rec_index;
   uint32_t n_rec_slots;
+  uint32_t long_min;       // matches at least this long (not overlapping) copy in 16-byte pieces
 };
 
 // Shared memory of one warp in the token pass: one stream's tables at a
@@ -471,6 +517,7 @@ __device__ bool token_block(const DecodeArgs& a, const TokMem& m, const TokRec& 
   const uint32_t w = a.w;
   const uint32_t ntok = __shfl_sync(kFull, dv, 12), nesc = __shfl_sync(kFull, dv, 13);
   const uint32_t nlit = __shfl_sync(kFull, dv, 9 + ACE_S_LIT);
+  const uint32_t modes = __shfl_sync(kFull, dv, 14);  // mode[k] in byte k
   const uint32_t lt = lanemask_lt();
 
   Stream sn, so;
@@ -479,7 +526,7 @@ __device__ bool token_block(const DecodeArgs& a, const TokMem& m, const TokRec& 
     uint64_t soff = (uint64_t)__shfl_sync(kFull, dv, 2 * k) | ((uint64_t)__shfl_sync(kFull, dv, 2 * k + 1) << 32);
     uint32_t sbytes = __shfl_sync(kFull, dv, 6 + k), nsym = __shfl_sync(kFull, dv, 9 + k);
     if (!stream_open(a.arc + a.payload_off + soff, sbytes, nsym, m.ring + (k - ACE_S_LEN) * kRing,
-                     k == ACE_S_LEN ? sn : so, lane))
+                     k == ACE_S_LEN ? sn : so, lane, (modes >> (8 * k)) & 0xffu))
       fail(a, ok, ACE_E_CORRUPT, b, 20 + k, lane);
   }
   if (!ok || ntok > a.max_ntok) {
@@ -540,7 +587,7 @@ __device__ bool token_block(const DecodeArgs& a, const TokMem& m, const TokRec& 
     auto put = [&](bool act, uint32_t i, uint32_t s) {
       if (act) g.offb[i] = (uint8_t)s;
     };
-    if (ok && so.k == 0 && oend >= 64) {  // slot-table streams: full rounds in the fast loop
+    if (ok && !so.stored && so.k == 0 && oend >= 64) {  // slot-table streams: full rounds in the fast loop
       uint32_t i = lane;
       table_full_rounds(so, ro, *m.lut, oend >> 5, lane, lt, [&](uint32_t s) {
         g.offb[i] = (uint8_t)s;
@@ -593,7 +640,9 @@ __device__ bool literal_block(const DecodeArgs& a, const LitMem& m, uint32_t b, 
     const int k = ACE_S_LIT;
     uint64_t soff = (uint64_t)__shfl_sync(kFull, dv, 2 * k) | ((uint64_t)__shfl_sync(kFull, dv, 2 * k + 1) << 32);
     uint32_t sbytes = __shfl_sync(kFull, dv, 6 + k), nsym = __shfl_sync(kFull, dv, 9 + k);
-    if (!stream_open<RING>(a.arc + a.payload_off + soff, sbytes, nsym, m.ring, sl, lane)) fail(a, ok, ACE_E_CORRUPT, b, 20, lane);
+    const uint32_t mode = __shfl_sync(kFull, dv, 14) & 0xffu;
+    if (!stream_open<RING>(a.arc + a.payload_off + soff, sbytes, nsym, m.ring, sl, lane, mode))
+      fail(a, ok, ACE_E_CORRUPT, b, 20, lane);
   }
   cp_async_wait<RING / kSeg - 2>();
   __syncwarp();
@@ -646,7 +695,7 @@ __device__ bool literal_block(const DecodeArgs& a, const LitMem& m, uint32_t b, 
           obase[cur_dst + (i - cur_lit)] = (uint8_t)s;
         }
       };
-      if (sl.k == 0 && lend - sl.next >= 64) {
+      if (!sl.stored && sl.k == 0 && lend - sl.next >= 64) {
         // slot-table streams: a partial round up to a round boundary, then
         // full rounds, each lane's literal pointer moving 32 bytes a round
         // until its literal index passes into the next token's run
@@ -695,10 +744,14 @@ constexpr uint32_t kCopyUnroll = 8;
 // 16-byte pieces in flight per lane in the copy of a round's long matches.
 constexpr uint32_t kLongUnroll = 2;
 // Copy classes: a non-overlapping match of at most kShortMax bytes is copied
-// by one lane, one of at least kLongMin bytes by the whole warp in 16-byte
-// pieces, every other one bytewise with the round's other such matches.
+// by one lane in aligned 8-byte words, one of at least the call's long_min
+// bytes by the whole warp in aligned 16-byte pieces, every other one
+// bytewise with the round's other such matches.  long_min is the copy-width
+// knob: kLongMinWide (16-byte pieces for everything above the short class)
+// or kLongMinNarrow (bytewise up to 511 bytes).
 constexpr uint32_t kShortMax = 32;
-constexpr uint32_t kLongMin = 512;
+constexpr uint32_t kLongMinNarrow = 512;
+constexpr uint32_t kLongMinWide = kShortMax + 1;
 
 // A load of match source bytes.  L1: through the SM's L1 cache, for a pass
 // whose sources were all written by earlier launches or by this warp (one
@@ -762,15 +815,20 @@ __device__ __forceinline__ void short_store(uint8_t* dp, uint32_t off, uint32_t 
   }
 }
 
-// 16 bytes at p, bytes outside [lo, hi) read as zero.
-template <bool L1>
-__device__ __forceinline__ uint4 ld16_in(const uint8_t* p, const uint8_t* lo, const uint8_t* hi) {
-  if (p >= lo && p + 16 <= hi) return ld_src<L1>(reinterpret_cast<const uint4*>(p));
+// The 16 bytes at absolute output position q (a multiple of 16, possibly
+// negative), bytes outside [0, total) read as zero.  An aligned piece never
+// straddles a block (blocks are multiples of 256 bytes), so a seek finds it
+// in one slot.
+template <bool SEEK, bool L1>
+__device__ __forceinline__ uint4 ld16_abs(const DecodeArgs& a, int64_t q, uint64_t b, const uint8_t* obase) {
+  if (q >= 0 && (uint64_t)q + 16 <= a.total)
+    return ld_src<L1>(reinterpret_cast<const uint4*>(Addr<SEEK>::at(a, (uint64_t)q, b, obase)));
   uint4 v = make_uint4(0, 0, 0, 0);
 #pragma unroll 1
   for (uint32_t k = 0; k < 16; k++) {
-    if (p + k < lo || p + k >= hi) continue;
-    const uint32_t x = (uint32_t)ld_src<L1>(p + k) << (8 * (k & 3));
+    const int64_t p = q + k;
+    if (p < 0 || (uint64_t)p >= a.total) continue;
+    const uint32_t x = (uint32_t)ld_src<L1>(Addr<SEEK>::at(a, (uint64_t)p, b, obase)) << (8 * (k & 3));
     if (k < 4) v.x |= x;
     else if (k < 8) v.y |= x;
     else if (k < 12) v.z |= x;
@@ -987,7 +1045,7 @@ __device__ bool match_block(const DecodeArgs& a, MatchRec* gm, uint32_t b, uint3
         const uint32_t j = lane + 32 * q, ml = gL[j];
         if (bstart + gD[j] - gS[j] < ml) continue;  // overlapping: bytewise
         if (ml <= kShortMax) sgo |= 1u << q;
-        else if (!SEEK && ml >= kLongMin) lgo |= 1u << q;
+        else if (ml >= a.long_min) lgo |= 1u << q;
       }
       if (sgo) {  // short: the next match's loads go out before the previous one's stores
         uint64_t cur[5], nxt[5];
@@ -1019,14 +1077,15 @@ __device__ bool match_block(const DecodeArgs& a, MatchRec* gm, uint32_t b, uint3
         if (lane == 31) gX[32] = incl;
         const uint32_t T = __shfl_sync(kFull, incl, 31);
         __syncwarp();
+        // in absolute output positions (block bases are 16-byte aligned in
+        // the output and in seek slots): the source of destination byte
+        // D - hd, rounded down to 16, is the match's first source piece
         auto piece = [&](uint32_t c, uint32_t& jp) -> uint4 {
           const uint32_t j = upper_bound(33, c, [&](uint32_t i) { return gX[i]; }) - 1;
           const uint32_t pc = c - gX[j];
           jp = j | (pc << 5);
-          uint8_t* dpj = obase + gD[j];
-          const uint8_t* s0 = a.out + gS[j] - (reinterpret_cast<uintptr_t>(dpj) & 15);
-          const uint8_t* sal = s0 - (reinterpret_cast<uintptr_t>(s0) & 15);
-          return ld16_in<kL1>(sal + 16ull * pc, a.out, a.out + a.total);
+          const int64_t s0 = (int64_t)gS[j] - (int64_t)(gD[j] & 15);
+          return ld16_abs<SEEK, kL1>(a, (s0 & ~(int64_t)15) + 16 * (int64_t)pc, b, obase);
         };
         for (uint32_t c0 = 0; c0 < T; c0 += 32 * kLongUnroll) {
           uint4 A[kLongUnroll];
@@ -1057,8 +1116,7 @@ __device__ bool match_block(const DecodeArgs& a, MatchRec* gm, uint32_t b, uint3
             uint8_t* dpj = obase + gD[j];
             const uint32_t hd = (uint32_t)(reinterpret_cast<uintptr_t>(dpj) & 15);
             if (pc >= ((hd + ml + 15) >> 4)) continue;  // the trailing source piece stores nothing
-            const uint8_t* s0 = a.out + gS[j] - hd;
-            const uint4 v = funnel128(A[u], B, (uint32_t)(reinterpret_cast<uintptr_t>(s0) & 15));
+            const uint4 v = funnel128(A[u], B, (uint32_t)(((int64_t)gS[j] - (int64_t)hd) & 15));
             uint8_t* dal = dpj - hd;
             const int first = 16 * (int)pc - (int)hd;  // match byte held by the piece's first byte
             if (first >= 0 && first + 16 <= (int)ml) {
@@ -1666,6 +1724,7 @@ struct BatchArgs {
   uint64_t timeout_ns;
   uint8_t* warp_scratch;
   uint64_t warp_scratch_bytes;
+  uint32_t long_min;
 };
 
 // The work of a batch: (archive, block) items, each archive's blocks in its
@@ -1711,6 +1770,7 @@ __device__ DecodeArgs batch_args(const BatchArgs& ba, const ObjDesc& od) {
   a.level = od.level;
   a.lv_done = od.lv_done;
   a.lv_count = od.lv_count;
+  a.long_min = ba.long_min;
   return a;
 }
 
@@ -2207,6 +2267,7 @@ struct CacheDecodeArgs {
   uint64_t timeout_ns;
   uint8_t* warp_scratch;
   uint64_t warp_scratch_bytes;
+  uint32_t long_min;
 };
 
 // Decodes a batch's work list into cache slots: the same three passes as a
@@ -2247,6 +2308,7 @@ __global__ void __launch_bounds__(256, ACE_PASS_MIN_CTAS(PASS)) cache_decode_ker
     a.n_slots = c.n_slots;
     a.rec_index = arc.wpos;
     a.n_rec_slots = c.front_cap;
+    a.long_min = ca.long_min;
     a.timeout_ns = ca.timeout_ns;
     a.recs = c.recs;
     a.match_ptr = nullptr;
@@ -2374,7 +2436,7 @@ struct ace_index {
 namespace {
 
 struct IndexLayout {
-  uint64_t level, order, lv_count, lv_cursor, match_ptr, total;
+  uint64_t level, order, lv_count, lv_cursor, match_ptr, seen, total;
 };
 
 IndexLayout index_layout(uint64_t nb) {
@@ -2390,6 +2452,8 @@ IndexLayout index_layout(uint64_t nb) {
   o = align256(o + 4 * (nb + 1));
   L.match_ptr = o;
   o = align256(o + 8 * (nb + 1));
+  L.seen = o;  // a stored index's order check marks each block here
+  o = align256(o + 4 * nb);
   L.total = o;
   return L;
 }
@@ -2519,6 +2583,7 @@ struct Launch {
   uint32_t grid[4];
   uint64_t timeout;
   uint32_t schedule;
+  uint32_t long_min;  // the copy-width knob as the long class's shortest match
 };
 
 template <class K>
@@ -2554,6 +2619,8 @@ ace_status plan_launch(const ace_index* idx, const ace_tune* tune, uint32_t log2
   L->timeout = t.wait_timeout_ns ? t.wait_timeout_ns : kDefaultTimeoutNs;
   L->schedule = t.schedule;
   if (L->schedule > ACE_SCHEDULE_FUSED) return ACE_E_INVAL;
+  if (t.copy_width != 0 && t.copy_width != 8 && t.copy_width != 16) return ACE_E_INVAL;
+  L->long_min = t.copy_width == 16 ? kLongMinWide : kLongMinNarrow;
   // automatic: the pass schedule, measured faster on every profile (the
   // fused launch's match jobs of the first levels form a serial chain)
   if (L->schedule == ACE_SCHEDULE_AUTO) L->schedule = ACE_SCHEDULE_PASSES;
@@ -2669,19 +2736,27 @@ ace_status ace_index_size(const void* h_header, uint64_t header_bytes, uint64_t*
   return ACE_OK;
 }
 
-ace_status ace_index_build(const void* d_archive, uint64_t archive_bytes, const void* h_header,
-                           uint64_t header_bytes, void* d_index_mem, uint64_t index_bytes, cudaStream_t s,
-                           ace_index** out) {
-  if (!out || !d_index_mem || (!d_archive && archive_bytes)) return ACE_E_INVAL;
-  if (!aligned(d_archive, 16) || !aligned(d_index_mem, 256)) return ACE_E_INVAL;
+}  // extern "C"
+
+namespace {
+
+// A new host handle over the archive and index memory, and the arguments of
+// the index kernels.  Returns null with *rc set on failure.
+ace_index* index_handle(const void* d_archive, uint64_t archive_bytes, const void* h_header, uint64_t header_bytes,
+                        void* d_index_mem, uint64_t index_bytes, IndexArgs* a, ace_status* rc) {
+  *rc = ACE_E_INVAL;
+  if (!d_index_mem || (!d_archive && archive_bytes)) return nullptr;
+  if (!aligned(d_archive, 16) || !aligned(d_index_mem, 256)) return nullptr;
   ace_file_header h;
-  ace_status rc = parse_header(h_header, header_bytes, &h);
-  if (rc) return rc;
-  if (h.archive_bytes > archive_bytes) return ACE_E_CORRUPT;
+  *rc = parse_header(h_header, header_bytes, &h);
+  if (*rc) return nullptr;
+  *rc = ACE_E_CORRUPT;
+  if (h.archive_bytes > archive_bytes) return nullptr;
   IndexLayout L = index_layout(h.n_blocks);
-  if (index_bytes < L.total) return ACE_E_NOMEM;
+  *rc = ACE_E_NOMEM;
+  if (index_bytes < L.total) return nullptr;
   ace_index* idx = new (std::nothrow) ace_index();
-  if (!idx) return ACE_E_NOMEM;
+  if (!idx) return nullptr;
   idx->d_arc = static_cast<const uint8_t*>(d_archive);
   idx->arc_bytes = archive_bytes;
   idx->h = h;
@@ -2692,37 +2767,95 @@ ace_status ace_index_build(const void* d_archive, uint64_t archive_bytes, const 
   idx->d_order = reinterpret_cast<uint32_t*>(idx->d_mem + L.order);
   idx->d_dep_ptr = reinterpret_cast<const uint32_t*>(idx->d_arc + h.deps_off);
   idx->tune = ace_tune{};
+  *rc = ACE_E_CUDA;
+  if (cudaGetDevice(&idx->device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&idx->num_sms, cudaDevAttrMultiProcessorCount, idx->device) != cudaSuccess) {
+    delete idx;
+    return nullptr;
+  }
+  // the interval table's bounds are checked on the device with the rest
+  idx->d_dep_iv = reinterpret_cast<const uint32_t*>(idx->d_arc + h.deps_off + 4 * (h.n_blocks + 1));
+  a->arc = idx->d_arc;
+  a->dir = reinterpret_cast<const ace_block_dir*>(idx->d_arc + h.dir_off);
+  a->dep_ptr = idx->d_dep_ptr;
+  a->dep_iv = idx->d_dep_iv;
+  a->ih = idx->d_ih;
+  a->level = idx->d_level;
+  a->order = idx->d_order;
+  a->lv_count = reinterpret_cast<uint32_t*>(idx->d_mem + L.lv_count);
+  a->lv_cursor = reinterpret_cast<uint32_t*>(idx->d_mem + L.lv_cursor);
+  a->match_ptr = reinterpret_cast<uint64_t*>(idx->d_mem + L.match_ptr);
+  idx->d_match_ptr = a->match_ptr;
+  idx->d_lv_count = a->lv_count;
+  a->nb = h.n_blocks;
+  a->total = h.total_size;
+  a->payload_off = h.payload_off;
+  a->arc_bytes = h.archive_bytes;
+  a->deps_off = h.deps_off;
+  a->max_iv = (h.payload_off - h.deps_off - 4 * (h.n_blocks + 1)) / 8;
+  a->log2B = h.log2_block;
+  a->w = h.off_width;
+  *rc = ACE_OK;
+  return idx;
+}
+
+// The handle's copies of what the index header holds.
+ace_status index_adopt(ace_index* idx, const IndexHdr& ih) {
+  if (ih.status) return (ace_status)ih.status;
+  idx->n_iv = ih.n_iv;
+  idx->max_ntok = ih.max_ntok;
+  idx->n_levels = ih.n_levels;
+  idx->n_matches = ih.n_matches;
+  idx->by_levels = ih.n_levels <= kMaxLevelLaunches;
+  if (idx->by_levels) {
+    idx->level_start[0] = 0;
+    for (uint32_t l = 0; l < ih.n_levels; l++) idx->level_start[l + 1] = idx->level_start[l] + ih.lvc[l];
+    if (idx->level_start[ih.n_levels] != idx->h.n_blocks) return ACE_E_CORRUPT;
+  }
+  return ACE_OK;
+}
+
+// FNV-1a 64 of host bytes (the stored index's checksum).
+uint64_t host_fnv1a64(const uint8_t* p, uint64_t n) {
+  uint64_t h = 0xcbf29ce484222325ull;
+  for (uint64_t i = 0; i < n; i++) {
+    h ^= p[i];
+    h *= 0x100000001b3ull;
+  }
+  return h;
+}
+
+// Header of a stored index: the archive header it belongs to, the index
+// memory's size and checksum; the index memory follows.
+struct IndexBlobHdr {
+  uint32_t magic;  // "ACEI"
+  uint32_t version;
+  ace_file_header arc;
+  uint64_t index_bytes;
+  uint64_t fnv;
+  uint8_t pad[168];
+};
+static_assert(sizeof(IndexBlobHdr) == 256, "stored index header");
+constexpr uint32_t kIndexMagic = 0x49454341u;  // "ACEI"
+
+}  // namespace
+
+extern "C" {
+
+ace_status ace_index_build(const void* d_archive, uint64_t archive_bytes, const void* h_header,
+                           uint64_t header_bytes, void* d_index_mem, uint64_t index_bytes, cudaStream_t s,
+                           ace_index** out) {
+  if (!out) return ACE_E_INVAL;
+  IndexArgs a;
+  ace_status rc;
+  ace_index* idx = index_handle(d_archive, archive_bytes, h_header, header_bytes, d_index_mem, index_bytes, &a, &rc);
+  if (!idx) return rc;
   auto bail = [&](ace_status r) {
     delete idx;
     return r;
   };
-  if (cudaGetDevice(&idx->device) != cudaSuccess) return bail(ACE_E_CUDA);
-  if (cudaDeviceGetAttribute(&idx->num_sms, cudaDevAttrMultiProcessorCount, idx->device) != cudaSuccess)
-    return bail(ACE_E_CUDA);
-  // the interval table's bounds are checked on the device with the rest
-  idx->d_dep_iv = reinterpret_cast<const uint32_t*>(idx->d_arc + h.deps_off + 4 * (h.n_blocks + 1));
-  if (cudaMemsetAsync(idx->d_mem, 0, L.total, s) != cudaSuccess) return bail(ACE_E_CUDA);
-  IndexArgs a;
-  a.arc = idx->d_arc;
-  a.dir = reinterpret_cast<const ace_block_dir*>(idx->d_arc + h.dir_off);
-  a.dep_ptr = idx->d_dep_ptr;
-  a.dep_iv = idx->d_dep_iv;
-  a.ih = idx->d_ih;
-  a.level = idx->d_level;
-  a.order = idx->d_order;
-  a.lv_count = reinterpret_cast<uint32_t*>(idx->d_mem + L.lv_count);
-  a.lv_cursor = reinterpret_cast<uint32_t*>(idx->d_mem + L.lv_cursor);
-  a.match_ptr = reinterpret_cast<uint64_t*>(idx->d_mem + L.match_ptr);
-  idx->d_match_ptr = a.match_ptr;
-  idx->d_lv_count = a.lv_count;
-  a.nb = h.n_blocks;
-  a.total = h.total_size;
-  a.payload_off = h.payload_off;
-  a.arc_bytes = h.archive_bytes;
-  a.deps_off = h.deps_off;
-  a.max_iv = (h.payload_off - h.deps_off - 4 * (h.n_blocks + 1)) / 8;
-  a.log2B = h.log2_block;
-  a.w = h.off_width;
+  const ace_file_header& h = idx->h;
+  if (cudaMemsetAsync(idx->d_mem, 0, index_layout(h.n_blocks).total, s) != cudaSuccess) return bail(ACE_E_CUDA);
   if (h.n_blocks) {
     // every step on the device, each skipping once the header holds an
     // error; the host reads the header once at the end
@@ -2737,17 +2870,76 @@ ace_status ace_index_build(const void* d_archive, uint64_t archive_bytes, const 
     level_scatter_kernel<<<g, 256, 0, s>>>(a);
     IndexHdr ih;
     if (read_header(idx->d_ih, &ih, sizeof ih, s) != ACE_OK) return bail(ACE_E_CUDA);
-    if (ih.status) return bail((ace_status)ih.status);
-    idx->n_iv = ih.n_iv;
-    idx->max_ntok = ih.max_ntok;
-    idx->n_levels = ih.n_levels;
-    idx->n_matches = ih.n_matches;
-    idx->by_levels = ih.n_levels <= kMaxLevelLaunches;
-    if (idx->by_levels) {
-      idx->level_start[0] = 0;
-      for (uint32_t l = 0; l < ih.n_levels; l++) idx->level_start[l + 1] = idx->level_start[l] + ih.lvc[l];
-      if (idx->level_start[ih.n_levels] != h.n_blocks) return bail(ACE_E_CORRUPT);
-    }
+    rc = index_adopt(idx, ih);
+    if (rc) return bail(rc);
+  }
+  *out = idx;
+  return ACE_OK;
+}
+
+ace_status ace_index_export_size(const ace_index* idx, uint64_t* bytes) {
+  if (!idx || !bytes) return ACE_E_INVAL;
+  *bytes = sizeof(IndexBlobHdr) + index_layout(idx->h.n_blocks).total;
+  return ACE_OK;
+}
+
+ace_status ace_index_export(const ace_index* idx, void* h_blob, uint64_t blob_bytes, cudaStream_t s) {
+  if (!idx || !h_blob) return ACE_E_INVAL;
+  const uint64_t n = index_layout(idx->h.n_blocks).total;
+  if (blob_bytes < sizeof(IndexBlobHdr) + n) return ACE_E_NOMEM;
+  uint8_t* p = static_cast<uint8_t*>(h_blob);
+  CUDA_TRY(cudaMemcpyAsync(p + sizeof(IndexBlobHdr), idx->d_mem, n, cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  IndexBlobHdr bh{};
+  bh.magic = kIndexMagic;
+  bh.version = 1;
+  bh.arc = idx->h;
+  bh.index_bytes = n;
+  bh.fnv = host_fnv1a64(p + sizeof(IndexBlobHdr), n);
+  std::memcpy(p, &bh, sizeof bh);
+  return ACE_OK;
+}
+
+ace_status ace_index_import(const void* d_archive, uint64_t archive_bytes, const void* h_header, uint64_t header_bytes,
+                            const void* h_blob, uint64_t blob_bytes, void* d_index_mem, uint64_t index_bytes,
+                            cudaStream_t s, ace_index** out) {
+  if (!out || !h_blob || blob_bytes < sizeof(IndexBlobHdr)) return ACE_E_INVAL;
+  IndexArgs a;
+  ace_status rc;
+  ace_index* idx = index_handle(d_archive, archive_bytes, h_header, header_bytes, d_index_mem, index_bytes, &a, &rc);
+  if (!idx) return rc;
+  auto bail = [&](ace_status r) {
+    delete idx;
+    return r;
+  };
+  const ace_file_header& h = idx->h;
+  const uint64_t n = index_layout(h.n_blocks).total;
+  IndexBlobHdr bh;
+  std::memcpy(&bh, h_blob, sizeof bh);
+  const uint8_t* body = static_cast<const uint8_t*>(h_blob) + sizeof(IndexBlobHdr);
+  // the stored index must belong to this archive and arrive whole
+  if (bh.magic != kIndexMagic || bh.version != 1 || std::memcmp(&bh.arc, &h, sizeof h) != 0 || bh.index_bytes != n ||
+      blob_bytes < sizeof(IndexBlobHdr) + n || host_fnv1a64(body, n) != bh.fnv)
+    return bail(ACE_E_CORRUPT);
+  if (cudaMemcpyAsync(idx->d_mem, body, n, cudaMemcpyHostToDevice, s) != cudaSuccess) return bail(ACE_E_CUDA);
+  if (h.n_blocks) {
+    // the archive is checked as at a build (directory, dependency table,
+    // match counts, largest token count: recomputed over the stored values),
+    // then the stored levels and order against it
+    IndexLayout L = index_layout(h.n_blocks);
+    if (cudaMemsetAsync(idx->d_mem, 0, 12, s) != cudaSuccess) return bail(ACE_E_CUDA);  // status words
+    uint32_t g = (uint32_t)((h.n_blocks + 255) / 256);
+    validate_kernel<<<g, 256, 0, s>>>(a);
+    match_scan_kernel<<<1, 1024, 0, s>>>(a);
+    const uint32_t gs = (uint32_t)std::min<uint64_t>((h.n_blocks + 7) / 8, (uint64_t)idx->num_sms * 8);
+    level_verify_kernel<<<gs, 256, 0, s>>>(a);
+    uint32_t* seen = reinterpret_cast<uint32_t*>(idx->d_mem + L.seen);
+    if (cudaMemsetAsync(seen, 0, 4 * h.n_blocks, s) != cudaSuccess) return bail(ACE_E_CUDA);
+    order_verify_kernel<<<g, 256, 0, s>>>(a, seen);
+    IndexHdr ih;
+    if (read_header(idx->d_ih, &ih, sizeof ih, s) != ACE_OK) return bail(ACE_E_CUDA);
+    rc = index_adopt(idx, ih);
+    if (rc) return bail(rc);
   }
   *out = idx;
   return ACE_OK;
@@ -2782,7 +2974,9 @@ ace_status ace_index_levels(const ace_index* idx, uint32_t* h_counts, uint32_t n
 
 ace_status ace_index_set_tune(ace_index* idx, const ace_tune* tune) {
   if (!idx) return ACE_E_INVAL;
-  if (tune && (tune->warps_per_cta > kMaxWarpsPerCta || (tune->chunk_tokens & 31) || tune->chunk_tokens > kMaxWindow))
+  if (tune && (tune->warps_per_cta > kMaxWarpsPerCta || (tune->chunk_tokens & 31) || tune->chunk_tokens > kMaxWindow ||
+               tune->schedule > ACE_SCHEDULE_FUSED ||
+               (tune->copy_width != 0 && tune->copy_width != 8 && tune->copy_width != 16)))
     return ACE_E_INVAL;
   idx->tune = tune ? *tune : ace_tune{};
   return ACE_OK;
@@ -2818,7 +3012,7 @@ namespace {
 ace_status decode_all_passes(const ace_index* idx, uint32_t passes, void* d_out, uint64_t out_bytes, void* d_scratch,
                              uint64_t scratch_bytes, const ace_tune* tune, cudaStream_t s) {
   if (!idx || !d_scratch || (!d_out && idx->h.total_size)) return ACE_E_INVAL;
-  if (!aligned(d_scratch, 256)) return ACE_E_INVAL;
+  if (!aligned(d_scratch, 256) || !aligned(d_out, 16)) return ACE_E_INVAL;
   if (out_bytes < idx->h.total_size) return ACE_E_NOMEM;
   ScratchLayout SL = scratch_layout(idx->h.n_blocks, idx->h.log2_block, 0, idx->num_sms, idx->max_ntok, idx->n_matches);
   if (scratch_bytes < SL.total) return ACE_E_NOMEM;
@@ -2850,6 +3044,7 @@ ace_status decode_all_passes(const ace_index* idx, uint32_t passes, void* d_out,
   a.recs = reinterpret_cast<MatchRec*>(static_cast<uint8_t*>(d_scratch) + SL.tail);
   a.match_ptr = idx->d_match_ptr;
   a.level = idx->d_level;
+  a.long_min = L.long_min;
   if (passes == 7 && L.schedule == ACE_SCHEDULE_FUSED) {
     // one launch over the (level, block) order; the level counters start at 0
     a.lv_done = reinterpret_cast<uint32_t*>(static_cast<uint8_t*>(d_scratch) + SL.lv_done);
@@ -2982,6 +3177,7 @@ ace_status ace_seek(const ace_index* idx, uint64_t coord, uint64_t len, void* d_
   a.match_ptr = nullptr;
   a.level = idx->d_level;
   a.closure_flags = true;
+  a.long_min = L.long_min;
   a.lv_done = c.lv_done;
   rc = launch_seek(idx, L, a, s);
   if (rc) return rc;
@@ -2999,6 +3195,28 @@ ace_status ace_sync(const ace_index* idx, void* d_scratch, cudaStream_t s) {
     CUDA_TRY(cudaStreamSynchronize(s));
   }
   return (ace_status)h.status;
+}
+
+ace_status ace_host_register(void* h_p, uint64_t bytes, uint32_t read_only, void** d_p) {
+  if (!h_p || !bytes || !d_p) return ACE_E_INVAL;
+  unsigned flags = cudaHostRegisterMapped | cudaHostRegisterPortable;
+  int dev = 0, ro = 0;
+  CUDA_TRY(cudaGetDevice(&dev));
+  // read-only registration where the platform offers it (a hint only)
+  if (read_only && cudaDeviceGetAttribute(&ro, cudaDevAttrHostRegisterReadOnlySupported, dev) == cudaSuccess && ro)
+    flags |= cudaHostRegisterReadOnly;
+  CUDA_TRY(cudaHostRegister(h_p, bytes, flags));
+  if (cudaHostGetDevicePointer(d_p, h_p, 0) != cudaSuccess) {
+    cudaHostUnregister(h_p);
+    return ACE_E_CUDA;
+  }
+  return ACE_OK;
+}
+
+ace_status ace_host_unregister(void* h_p) {
+  if (!h_p) return ACE_E_INVAL;
+  CUDA_TRY(cudaHostUnregister(h_p));
+  return ACE_OK;
 }
 
 ace_status ace_fnv1a64(const void* d_p, uint64_t n, uint64_t* d_result, cudaStream_t s) {
@@ -3140,6 +3358,7 @@ ace_status ace_batch_create(const ace_index* const* idx, uint32_t n, void* const
   for (uint32_t i = 0; i < n; i++) {
     const ace_index* x = idx[i];
     if (out_bytes[i] < x->h.total_size || (!d_outs[i] && x->h.total_size)) return ACE_E_NOMEM;
+    if (!aligned(d_outs[i], 16)) return ACE_E_INVAL;
     od[i] = ObjDesc{x->d_arc,
                     reinterpret_cast<const ace_block_dir*>(x->d_arc + x->h.dir_off),
                     x->h.payload_off,
@@ -3198,6 +3417,7 @@ ace_status ace_batch_create(const ace_index* const* idx, uint32_t n, void* const
   a.timeout_ns = b->L.timeout;
   a.warp_scratch = base + B.warps;
   a.warp_scratch_bytes = warp_scratch_bytes(B.max_ntok);
+  a.long_min = b->L.long_min;
   *out = b;
   return ACE_OK;
 }
@@ -3433,6 +3653,7 @@ ace_status ace_cache_create(const ace_index* const* idx, uint32_t n, void* const
   d.timeout_ns = c->L.timeout;
   d.warp_scratch = base + C.warps;
   d.warp_scratch_bytes = warp_scratch_bytes(C.max_ntok);
+  d.long_min = c->L.long_min;
   *out = c;
   return ACE_OK;
 }
@@ -3642,6 +3863,7 @@ ace_status ace_seek_noalloc(const ace_index* idx, uint64_t coord, uint64_t len, 
   a.match_ptr = nullptr;
   a.level = idx->d_level;
   a.closure_flags = true;
+  a.long_min = L.long_min;
   a.lv_done = c.lv_done;
   rc = launch_seek(idx, L, a, s);
   if (rc) return rc;

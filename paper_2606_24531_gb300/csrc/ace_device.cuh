@@ -187,6 +187,7 @@ struct Stream {
   uint32_t pos;        // renormalisation bytes consumed
   uint32_t base;       // renormalisation offset held by the ring's oldest segment
   uint32_t x;          // this lane's state
+  uint32_t stored;     // mode 1: the stream holds its symbols verbatim at g (no states, no table)
 };
 
 // Copies renormalisation bytes [off, off + 128) into their segment of a
@@ -205,9 +206,13 @@ __device__ __forceinline__ void ring_issue(const Stream& st, uint8_t* ring, uint
 // point) and locates the renormalisation bytes; issues the first ring fill.
 // The stream bounds were validated when the index was built.  Returns false
 // (all lanes) for a state outside [L, 2^31) or a table overrunning the stream.
+//
+// A stored stream (mode 1; entropy coding chosen per stream at encode time)
+// has no states or table: its bytes are its symbols, read straight from the
+// archive, so it opens with nothing to check but its length.
 template <uint32_t RING = kRing>
 __device__ __forceinline__ bool stream_open(const uint8_t* pay, uint32_t sbytes, uint32_t nsym, uint8_t* ring,
-                                            Stream& st, uint32_t lane) {
+                                            Stream& st, uint32_t lane, uint32_t mode = 0) {
   st.nsym = nsym;
   st.next = st.pos = st.base = 0;
   st.x = ACE_RANS_L;
@@ -215,7 +220,12 @@ __device__ __forceinline__ bool stream_open(const uint8_t* pay, uint32_t sbytes,
   st.head = 0;
   st.k = st.kstep = 0;
   st.nbytes = 0;
+  st.stored = mode == 1;
   if (nsym == 0) return sbytes == 0;
+  if (st.stored) {
+    st.nbytes = sbytes;
+    return sbytes == nsym;
+  }
   uint32_t x = reinterpret_cast<const uint32_t*>(pay)[lane];
   uint32_t present = __popc(pay[128 + lane]);
   present = warp_incl_sum(present, lane);
@@ -249,7 +259,7 @@ constexpr uint32_t kSearchMaxSymbols = 2048;
 // | s, searched per symbol.  Returns false (all lanes) if the frequencies do
 // not sum to 4096.
 __device__ __forceinline__ bool lut_build(Stream& st, Lut& lut, uint32_t lane) {
-  if (st.nsym == 0) return true;
+  if (st.nsym == 0 || st.stored) return true;
   const uint8_t* sp = st.g - st.head;
   uint32_t bm = sp[128 + lane];
   uint32_t cnt = __popc(bm);
@@ -426,6 +436,17 @@ __device__ __forceinline__ uint32_t rans_round_full(Stream& st, uint8_t* ring, c
 template <uint32_t RING = kRing, class Sink>
 __device__ __forceinline__ void rans_run(Stream& st, uint8_t* ring, const Lut& lut, uint32_t end, uint32_t lane,
                                          uint32_t lt, Sink&& sink) {
+  if (st.stored) {  // symbol i is byte i, in rounds of 32 like the coded streams
+    while (st.next < end) {
+      const uint32_t base = st.next & ~31u, i = base + lane;
+      const bool act = i >= st.next && i < end;
+      const uint32_t s = act ? (uint32_t)__ldg(st.g + i) : 0u;
+      sink(act, i, s);
+      st.next = min(base + 32, end);
+    }
+    st.pos = st.next;  // a stored stream's bytes are consumed one per symbol
+    return;
+  }
   if (st.next < end && ((st.next & 31) || end - st.next < 32)) {
     bool act;
     uint32_t i;

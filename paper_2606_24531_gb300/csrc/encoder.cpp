@@ -361,13 +361,14 @@ struct BlockOut {
   std::vector<uint8_t> payload;   // three streams, each padded to 16 bytes
   uint32_t stream_bytes[3] = {0, 0, 0};
   uint32_t nsym[3] = {0, 0, 0};
+  uint8_t mode[3] = {0, 0, 0};    // 0: rANS, 1: stored verbatim
   uint32_t ntok = 0, nesc = 0;
   std::vector<uint32_t> deps;     // (first, last) pairs
   uint64_t n_matches = 0, match_bytes = 0, match_src_bytes = 0;
 };
 
 void code_block(const uint8_t* in, uint64_t b, uint64_t B, uint64_t n, int w, const std::vector<Token>& toks,
-                BlockOut& bo) {
+                bool adaptive, BlockOut& bo) {
   std::vector<uint8_t> lit, esc, codes, off;
   uint64_t bstart = b * B, dst = bstart;
   std::vector<std::pair<uint64_t, uint64_t>> rg;
@@ -413,6 +414,14 @@ void code_block(const uint8_t* in, uint64_t b, uint64_t B, uint64_t n, int w, co
     size_t before = bo.payload.size();
     code_stream(st[k]->data(), (uint32_t)st[k]->size(), bo.payload);
     bo.stream_bytes[k] = (uint32_t)(bo.payload.size() - before);
+    if (adaptive && !st[k]->empty() && bo.stream_bytes[k] >= st[k]->size()) {
+      // rANS did not shrink the stream (its fixed head outweighs the gain on
+      // short or near-uniform streams): store the symbols verbatim
+      bo.payload.resize(before);
+      bo.payload.insert(bo.payload.end(), st[k]->begin(), st[k]->end());
+      bo.stream_bytes[k] = (uint32_t)st[k]->size();
+      bo.mode[k] = 1;
+    }
     bo.payload.resize((bo.payload.size() + 15) & ~(size_t)15, 0);
     bo.nsym[k] = (uint32_t)st[k]->size();
   }
@@ -454,6 +463,7 @@ ace_status ace_encode_run(const void* h_in, uint64_t n, const ace_encode_params*
   uint64_t B = 1ull << prm->log2_block, nb = (n + B - 1) / B;
   if (nb > 0xFFFFFFFFull) return ACE_E_INVAL;
   if (prm->off_width != 0 && prm->off_width != 4 && prm->off_width != 5) return ACE_E_INVAL;
+  if (prm->adaptive > 1) return ACE_E_INVAL;
   if (prm->off_width == 4 && n > (1ull << 32)) return ACE_E_INVAL;
   int w = (n > (1ull << 32) || prm->off_width == 5) ? 5 : 4;
   ace_encoder* e = new (std::nothrow) ace_encoder();
@@ -473,7 +483,7 @@ ace_status ace_encode_run(const void* h_in, uint64_t n, const ace_encode_params*
         std::vector<Token> toks;
         uint64_t bstart = b * B, bend = std::min(n, bstart + B);
         parse_block(in, n, b, bstart, bend, prm->min_match, max_chain, g, al, *parsers[k], toks);
-        code_block(in, b, B, n, w, toks, e->blocks[b]);
+        code_block(in, b, B, n, w, toks, prm->adaptive != 0, e->blocks[b]);
       });
       for (uint64_t b = w0; b < w1; b++) {  // level: 1 + the deepest block read
         const std::vector<uint32_t>& dv = e->blocks[b].deps;
@@ -507,7 +517,7 @@ ace_status ace_encode_run(const void* h_in, uint64_t n, const ace_encode_params*
       d.stream_off[k] = s;
       d.stream_bytes[k] = bo.stream_bytes[k];
       d.nsym[k] = bo.nsym[k];
-      d.mode[k] = 0;
+      d.mode[k] = bo.mode[k];
       s += (bo.stream_bytes[k] + 15) & ~15ull;
     }
     d.ntok = bo.ntok;

@@ -93,3 +93,28 @@ def test_report_counts_the_token_streams():
     assert rep["lengths"]["raw"] == 2 * toks + 2 * nesc
     assert rep["offsets"]["raw"] == w * matches
     assert rep["literals"]["stored_verbatim_blocks"] == 0
+
+
+@pytest.mark.parametrize("profile", ["genome", "fastq", "text", "mixed"])
+def test_library_encoder_adaptive_option(profile):
+    """The library's host encoder with adaptive set: the oracle decodes its
+    archive to the original, and a stream is stored exactly when the
+    library's rANS-only archive of the same input spends at least its symbol
+    count on it, with the same parse (every other directory count equal)."""
+    from paper_2606_24531_gb300 import ace
+
+    data = synth.generate(profile, 1_500_000, 12)
+    mm = {"genome": 20, "fastq": 16, "text": 4, "mixed": 4}[profile]
+    for log2b in (10, 14):
+        a0 = ace.ace_encode(data, log2b, mm)
+        a1 = ace.ace_encode(data, log2b, mm, adaptive=True)
+        assert np.array_equal(oracle.decode(a1), data)
+        d0, d1 = _dir(a0), _dir(a1)
+        for key in ("nsym", "ntok", "nesc"):
+            assert np.array_equal(d0[key], d1[key])
+        stored = (d0["stored"] >= d0["nsym"]) & (d0["nsym"] > 0)
+        assert np.array_equal(d1["mode"] == 1, stored)
+        assert np.array_equal(d1["stored"], np.where(stored, d0["nsym"], d0["stored"]))
+        assert a1.size <= a0.size
+        for coord, n in ((0, 1), (len(data) // 3, 5000), (len(data) - 100, 100)):
+            assert np.array_equal(oracle.seek(a1, coord, n), data[coord:coord + n])
