@@ -25,6 +25,9 @@ Also measured, each at the size its configuration states:
   - beyond device memory: a 50 GB genome whose archive stays in host
     memory, the range decode of blocks 0..1000 and a long range streamed to
     host memory in sub-ranges;
+  - the GPU encoder on the FASTQ and genome workloads, beside the host
+    encoder (the batched, serving and host-resident workloads are encoded
+    with it);
   - the oracle on the host cores beside each decode.
 --quick caps the batched objects at 2 MiB, the served archives at 256 MiB
 and the host-resident genome at 4 GiB (labelled as reduced in the output).
@@ -550,7 +553,7 @@ def measure_batched(ace, dev, stream, flush, max_size, reduced):
     from paper_2606_24531_gb300.batch import DeviceBatch, autotune, make_objects, time_per_object
 
     t0 = time.perf_counter()
-    bdatas, barcs, bstats = make_objects(4096, seed=4, max_size=max_size, stats=True)
+    bdatas, barcs, bstats = make_objects(4096, seed=4, max_size=max_size, stats=True, encoder="gpu", device=dev)
     prep_s = time.perf_counter() - t0
     db = DeviceBatch(barcs, device=dev)
     tuned = autotune(db, reps=2, cache_key=None)
@@ -620,13 +623,16 @@ def measure_serve(ace, DeviceArchive, dev, arch_bytes, budget, reduced):
     for t in th:
         t.join()
     sdas = []
-    for k, p in enumerate(profs):
-        arc = ace.ace_encode(datas[k], 14, MIN_MATCH[p], off_width=5)
-        sdas.append(DeviceArchive(arc, max_seek_blocks=1024, device=dev))
+    for k, p in enumerate(profs):  # encoded on the GPU, the archives staying resident
+        arc = ace.ace_encode_gpu(torch.from_numpy(datas[k]).to(dev), 14, MIN_MATCH[p], off_width=5)
+        sdas.append(DeviceArchive(arc.cpu().numpy(), max_seek_blocks=1024, device=dev))
         del arc
+        torch.cuda.empty_cache()
     prep_s = time.perf_counter() - t0
     sizes = np.array([x.total for x in sdas], np.uint64)
     srv = Server(sdas, budget_bytes=budget, device=dev)
+    tq, aq, cq, lq = synth.requests(6, 3000, 3e4, sizes, 1 << 14, 1 << 20)
+    srv.run(tq, aq, cq, lq, time_limit_s=2.0)  # warm-up (first launches, first cached blocks), not reported
     rows = []
     rng = np.random.default_rng(9)
     for lam in (1e4, 3e4, 1e5, 3e5, 1e6):
@@ -675,7 +681,10 @@ def measure_beyond_vram(ace, dev, stream, total_bytes, reduced):
 
     t0 = time.perf_counter()
     data = synth.generate("genome", total_bytes, 3)
-    arc = ace.ace_encode(data, 14, 20, off_width=5 if total_bytes > (1 << 32) else 0)
+    d_in = torch.from_numpy(data).to(dev)
+    arc = ace.ace_encode_gpu(d_in, 14, 20).cpu().numpy()  # on the GPU; the archive then lives on the host
+    del d_in
+    torch.cuda.empty_cache()
     prep_s = time.perf_counter() - t0
     t0 = time.perf_counter()
     ha = HostArchive(arc, max_seek_blocks=4096, device=dev)
@@ -726,6 +735,41 @@ def measure_beyond_vram(ace, dev, stream, total_bytes, reduced):
     del data, arc
     torch.cuda.empty_cache()
     return res
+
+
+def measure_encoder(ace, dev, stream):
+    """The GPU encoder on the headline workload and the genome: encode time
+    (input resident in device memory, archive left there), ratio beside the
+    host encoder's, and the archive checked by a GPU decode."""
+    import torch
+    from paper_2606_24531_gb300.archive import DeviceArchive
+
+    rows = {}
+    for name in ("fastq-256MiB-16KiB-blocks", "genome-1GiB-16KiB-blocks"):
+        data, log2b, mm = make_data(name)
+        d_in = torch.from_numpy(data).to(dev)
+        ace.ace_encode_gpu(d_in, log2b, mm)  # warm-up
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(3):
+            t0 = time.perf_counter()
+            arc, st = ace.ace_encode_gpu(d_in, log2b, mm, stats=True)
+            torch.cuda.synchronize()
+            ts.append(time.perf_counter() - t0)
+        h = arc.cpu().numpy()
+        t0 = time.perf_counter()
+        host = ace.ace_encode(data, log2b, mm)
+        host_s = time.perf_counter() - t0
+        da = DeviceArchive(h, device=dev)
+        out = da.decode_all()
+        assert da.sync() == ace.ACE_OK and torch.equal(out[:data.size], d_in), "GPU-encoded archive differs"
+        da.close()
+        rows[name] = {"gpu_encode_s": statistics.median(ts), "gpu_GBps": data.size / statistics.median(ts) / 1e9,
+                      "ratio": data.size / h.size, "host_encode_s": host_s, "host_ratio": data.size / host.size,
+                      "host_threads": os.cpu_count(), "levels": st["n_levels"]}
+        del d_in, arc, out
+        torch.cuda.empty_cache()
+    return rows
 
 
 def main():
@@ -851,6 +895,7 @@ def main():
         gen.pop("_handles")
         cfgs["genome"] = gen
         torch.cuda.empty_cache()
+        cfgs["gpu_encoder"] = measure_encoder(ace, dev, stream)
         if not args.no_batched:
             cfgs["batched"] = measure_batched(ace, dev, stream, flush, (1 << 21) if args.quick else (1 << 26),
                                               args.quick)

@@ -263,7 +263,7 @@ typedef struct {
     uint64_t wait_timeout_ns; /* bound on each device-side wait; 0 = 2 s */
     uint32_t copy_width;      /* match copies: 16 = every non-overlapping match above 32 bytes in aligned
                                  16-byte pieces; 8 = 8-byte words up to 32 bytes, bytewise up to 511,
-                                 16-byte pieces from 512; 0 = the library's choice; others: ACE_E_INVAL */
+                                 16-byte pieces from 512; 0 = the library's choice (16); others: ACE_E_INVAL */
     uint32_t reserved;        /* 0 */
 } ace_tune;
 

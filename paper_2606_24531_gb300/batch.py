@@ -133,12 +133,14 @@ def autotune(db, candidates=None, reps=3, cache_key=None, cache_path=TUNE_CACHE)
     return best
 
 
-def make_objects(count, seed=4, min_size=4096, max_size=1 << 26, seed_base=1000, workers=0, stats=False):
+def make_objects(count, seed=4, min_size=4096, max_size=1 << 26, seed_base=1000, workers=0, stats=False,
+                 encoder="host", device="cuda"):
     """The uneven batch workload: (originals, archives[, parse statistics])
     for count objects with log-uniform sizes, a random profile and block size
-    each (the synth module's object table).  Objects are generated and
-    encoded on a thread pool (the native calls release the interpreter
-    lock), one encoder thread each."""
+    each (the synth module's object table).  Objects are generated on a
+    thread pool (the native calls release the interpreter lock); encoder
+    "host" encodes them there too, one encoder thread each, "gpu" with the
+    GPU encoder as they come."""
     from concurrent.futures import ThreadPoolExecutor
 
     import synth
@@ -149,8 +151,20 @@ def make_objects(count, seed=4, min_size=4096, max_size=1 << 26, seed_base=1000,
     def one(k):
         d = synth.generate(int(profiles[k]), int(sizes[k]), int(seeds[k]))
         log2b = int(bsz[k]).bit_length() - 1
+        if encoder == "gpu":
+            return d, log2b
         arc, st = ace.ace_encode(d, log2b, mm[int(profiles[k])], threads=1, stats=True)
         return d, arc, st
+
+    if encoder == "gpu":
+        res = [None] * count
+        with ThreadPoolExecutor(workers or os.cpu_count() or 4) as ex:
+            for k, (d, log2b) in enumerate(ex.map(one, range(count))):
+                arc, st = ace.ace_encode_gpu(torch.from_numpy(d).to(device), log2b, mm[int(profiles[k])], stats=True)
+                res[k] = (d, arc.cpu().numpy(), st)
+        if stats:
+            return [r[0] for r in res], [r[1] for r in res], [r[2] for r in res]
+        return [r[0] for r in res], [r[1] for r in res]
 
     # the largest objects first, so the pool ends on small ones
     order = sorted(range(count), key=lambda k: -int(sizes[k]))

@@ -837,6 +837,28 @@ __device__ __forceinline__ uint4 ld16_abs(const DecodeArgs& a, int64_t q, uint64
   return v;
 }
 
+// Bytes [lo, hi) of v to the 16-byte aligned p, in the widest aligned
+// stores that fit (a piece at either end of a match).
+__device__ __forceinline__ void store_bytes16(uint8_t* p, uint4 v, uint32_t lo, uint32_t hi) {
+  auto word = [&](uint32_t k) { return k < 4 ? v.x : k < 8 ? v.y : k < 12 ? v.z : v.w; };
+  uint32_t k = lo;
+  while (k < hi) {
+    if (!(k & 7) && k + 8 <= hi) {
+      *reinterpret_cast<uint2*>(p + k) = make_uint2(word(k), word(k + 4));
+      k += 8;
+    } else if (!(k & 3) && k + 4 <= hi) {
+      *reinterpret_cast<uint32_t*>(p + k) = word(k);
+      k += 4;
+    } else if (!(k & 1) && k + 2 <= hi) {
+      *reinterpret_cast<uint16_t*>(p + k) = (uint16_t)(word(k) >> (8 * (k & 3)));
+      k += 2;
+    } else {
+      p[k] = (uint8_t)(word(k) >> (8 * (k & 3)));
+      k++;
+    }
+  }
+}
+
 // Bytes r .. r + 15 of B:A (r < 16, the same on every lane).
 __device__ __forceinline__ uint4 funnel128(uint4 A, uint4 B, uint32_t r) {
   const uint32_t t = 8 * (r & 3);
@@ -1065,70 +1087,56 @@ __device__ bool match_block(const DecodeArgs& a, MatchRec* gm, uint32_t b, uint3
       if (__any_sync(kFull, lgo != 0)) {
         // long: the round's long matches at once, laid end to end as the
         // aligned 16-byte source pieces each one needs (its destination
-        // pieces plus one), kLongUnroll pieces per lane in flight; piece c
-        // and piece c + 1 build destination piece c, and piece c + 1 is the
-        // next lane's (lane 0's next one for lane 31)
+        // pieces plus one); piece c and piece c + 1 build destination piece
+        // c.  A window gives lane l pieces c0 + 32 u + l, kLongUnroll in
+        // flight; piece c + 1 is the next lane's, or for lane 31 the next
+        // u's lane 0; the window's very last piece only serves as that
+        // source, and the next window starts on it.  Each lane finds its
+        // pieces' match by walking forward (pieces only grow).
         static_assert(kLaneMatches == 1, "one match per lane");
         const bool mine = lgo & 1;
-        const uint32_t hd0 = (uint32_t)(reinterpret_cast<uintptr_t>(obase + gD[lane]) & 15);
+        const uint32_t hd0 = gD[lane] & 15;  // block bases are 16-byte aligned
         const uint32_t np = mine ? ((hd0 + gL[lane] + 15) >> 4) + 1 : 0u;
         const uint32_t incl = warp_incl_sum(np, lane);
         gX[lane] = incl - np;
         if (lane == 31) gX[32] = incl;
         const uint32_t T = __shfl_sync(kFull, incl, 31);
         __syncwarp();
-        // in absolute output positions (block bases are 16-byte aligned in
-        // the output and in seek slots): the source of destination byte
-        // D - hd, rounded down to 16, is the match's first source piece
-        auto piece = [&](uint32_t c, uint32_t& jp) -> uint4 {
-          const uint32_t j = upper_bound(33, c, [&](uint32_t i) { return gX[i]; }) - 1;
-          const uint32_t pc = c - gX[j];
-          jp = j | (pc << 5);
-          const int64_t s0 = (int64_t)gS[j] - (int64_t)(gD[j] & 15);
-          return ld16_abs<SEEK, kL1>(a, (s0 & ~(int64_t)15) + 16 * (int64_t)pc, b, obase);
-        };
-        for (uint32_t c0 = 0; c0 < T; c0 += 32 * kLongUnroll) {
+        uint32_t jc = 0;
+        for (uint32_t c0 = 0; c0 < T; c0 += 32 * kLongUnroll - 1) {
           uint4 A[kLongUnroll];
           uint32_t jp[kLongUnroll];
-          uint4 An = make_uint4(0, 0, 0, 0);
 #pragma unroll
           for (uint32_t u = 0; u < kLongUnroll; u++) {
             const uint32_t c = c0 + 32 * u + lane;
             jp[u] = 0xffffffffu;
-            A[u] = c < T ? piece(c, jp[u]) : make_uint4(0, 0, 0, 0);
-          }
-          if (lane == 31 && c0 + 32 * kLongUnroll < T) {
-            uint32_t unused;
-            An = piece(c0 + 32 * kLongUnroll, unused);
+            A[u] = make_uint4(0, 0, 0, 0);
+            if (c < T) {
+              while (gX[jc + 1] <= c) jc++;
+              const uint32_t pc = c - gX[jc];
+              jp[u] = jc | (pc << 5);
+              const int64_t s0 = (int64_t)gS[jc] - (int64_t)(gD[jc] & 15);
+              A[u] = ld16_abs<SEEK, kL1>(a, (s0 & ~(int64_t)15) + 16 * (int64_t)pc, b, obase);
+            }
           }
 #pragma unroll
           for (uint32_t u = 0; u < kLongUnroll; u++) {
             const uint4 nb = shfl_down16(A[u], 1);
-            uint4 n0 = An;
-            if (u + 1 < kLongUnroll)
-              n0 = make_uint4(__shfl_sync(kFull, A[u + 1 < kLongUnroll ? u + 1 : u].x, 0),
-                              __shfl_sync(kFull, A[u + 1 < kLongUnroll ? u + 1 : u].y, 0),
-                              __shfl_sync(kFull, A[u + 1 < kLongUnroll ? u + 1 : u].z, 0),
-                              __shfl_sync(kFull, A[u + 1 < kLongUnroll ? u + 1 : u].w, 0));
+            const uint32_t un = u + 1 < kLongUnroll ? u + 1 : u;
+            const uint4 n0 = make_uint4(__shfl_sync(kFull, A[un].x, 0), __shfl_sync(kFull, A[un].y, 0),
+                                        __shfl_sync(kFull, A[un].z, 0), __shfl_sync(kFull, A[un].w, 0));
             const uint4 B = lane == 31 ? n0 : nb;
-            if (jp[u] == 0xffffffffu) continue;
+            if (jp[u] == 0xffffffffu || (u + 1 == kLongUnroll && lane == 31)) continue;
             const uint32_t j = jp[u] & 31, pc = jp[u] >> 5, ml = gL[j];
-            uint8_t* dpj = obase + gD[j];
-            const uint32_t hd = (uint32_t)(reinterpret_cast<uintptr_t>(dpj) & 15);
+            const uint32_t hd = gD[j] & 15;
             if (pc >= ((hd + ml + 15) >> 4)) continue;  // the trailing source piece stores nothing
             const uint4 v = funnel128(A[u], B, (uint32_t)(((int64_t)gS[j] - (int64_t)hd) & 15));
-            uint8_t* dal = dpj - hd;
+            uint8_t* dp = obase + gD[j] - hd + 16ull * pc;
             const int first = 16 * (int)pc - (int)hd;  // match byte held by the piece's first byte
-            if (first >= 0 && first + 16 <= (int)ml) {
-              *reinterpret_cast<uint4*>(dal + 16ull * pc) = v;
-            } else {
-#pragma unroll 1
-              for (uint32_t k = 0; k < 16; k++) {
-                const int di = first + (int)k;
-                const uint32_t x = k < 4 ? v.x : k < 8 ? v.y : k < 12 ? v.z : v.w;
-                if (di >= 0 && di < (int)ml) dal[16ull * pc + k] = (uint8_t)(x >> (8 * (k & 3)));
-              }
-            }
+            if (first >= 0 && first + 16 <= (int)ml)
+              *reinterpret_cast<uint4*>(dp) = v;
+            else
+              store_bytes16(dp, v, (uint32_t)max(0, -first), (uint32_t)min(16, (int)ml - first));
           }
         }
         __syncwarp();
@@ -1411,7 +1419,7 @@ __global__ void __launch_bounds__(256, ACE_PASS_MIN_CTAS(PASS)) decode_kernel(De
 // waits.  Blocks are dealt out statically (block k of the level to warp
 // k mod the warps in the grid), and each warp fetches its next block's
 // number and record range while it resolves the current one.
-__global__ void __launch_bounds__(256, 2) match_level_kernel(DecodeArgs a) {
+__global__ void __launch_bounds__(256, 3) match_level_kernel(DecodeArgs a) {
   extern __shared__ __align__(16) uint8_t smem[];
   const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const uint32_t nw = gridDim.x * (blockDim.x >> 5);
@@ -2620,7 +2628,9 @@ ace_status plan_launch(const ace_index* idx, const ace_tune* tune, uint32_t log2
   L->schedule = t.schedule;
   if (L->schedule > ACE_SCHEDULE_FUSED) return ACE_E_INVAL;
   if (t.copy_width != 0 && t.copy_width != 8 && t.copy_width != 16) return ACE_E_INVAL;
-  L->long_min = t.copy_width == 16 ? kLongMinWide : kLongMinNarrow;
+  // the library's choice (0): 16-byte pieces from 33 bytes (genome 1 GiB
+  // 1.37 ms against 1.43; FASTQ and text unchanged)
+  L->long_min = t.copy_width == 8 ? kLongMinNarrow : kLongMinWide;
   // automatic: the pass schedule, measured faster on every profile (the
   // fused launch's match jobs of the first levels form a serial chain)
   if (L->schedule == ACE_SCHEDULE_AUTO) L->schedule = ACE_SCHEDULE_PASSES;

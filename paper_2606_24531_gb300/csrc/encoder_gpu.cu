@@ -179,6 +179,7 @@ __global__ void candidate_kernel(EncArgs a) {
       uint32_t d = a.prev[p - base];
       uint64_t q = p;
       for (uint32_t depth = 0; d && depth < a.max_chain; depth++) {
+        if (d > q - bstart) break;  // links stay inside the block
         q -= d;
         const uint32_t l = common(a.in + q, a.in + p, lim);
         if (l > li) {
@@ -245,6 +246,18 @@ __global__ void parse_kernel(EncArgs a) {
   unsigned long long n_match = 0, mbytes = 0, msrc = 0, lbytes = 0;
   uint64_t p = bstart;
   while (p < bend) {
+    // eight positions without a candidate at once (16-byte loads of the
+    // candidate lengths; the wave bytes of eight literals as one word)
+    if (((p - base) & 7) == 0 && p + 8 <= bend) {
+      const uint4 v = *reinterpret_cast<const uint4*>(a.lens + (p - base));
+      if ((v.x | v.y | v.z | v.w) == 0) {
+        *reinterpret_cast<uint64_t*>(wv + (p - bstart)) = 0;
+        lit += 8;
+        lbytes += 8;
+        p += 8;
+        continue;
+      }
+    }
     const uint32_t ll = a.lens[p - base];
     uint32_t best_len = 0, best_w = 0;
     uint64_t best_q = 0;
@@ -931,7 +944,7 @@ ace_status ace_encode_gpu(const void* d_in, uint64_t n, const ace_encode_params*
     for (uint64_t c = w0; c < std::min(head, w0 + kWin); c += L.chunk)
       pieces.push_back({c, std::min({head, w0 + kWin, c + L.chunk}), w0});
   for (uint64_t c = head; c < nb; c += L.chunk) pieces.push_back({c, std::min(nb, c + L.chunk), head});
-  constexpr uint32_t kChainWarps = 4;
+  constexpr uint32_t kChainWarps = 2;  // 16 KiB of bucket heads each: within the default shared memory
   for (const Piece& pc : pieces) {
     e.c0 = pc.c0;
     e.c1 = pc.c1;
@@ -941,7 +954,7 @@ ace_status ace_encode_gpu(const void* d_in, uint64_t n, const ace_encode_params*
                    kChainWarps * (4u << kHashBits4), s>>>(e);
     const uint64_t npos = std::min(n, pc.c1 * B) - pc.c0 * B;
     candidate_kernel<<<(uint32_t)std::min<uint64_t>((npos + 255) / 256, 152ull * 64), 256, 0, s>>>(e);
-    parse_kernel<<<(uint32_t)((cn + 63) / 64), 64, 0, s>>>(e);
+    parse_kernel<<<(uint32_t)((cn + 31) / 32), 32, 0, s>>>(e);
     ca.e = e;
     code_kernel<<<(uint32_t)((cn + 7) / 8), 256, 0, s>>>(ca);
     pa.c0 = pc.c0;
