@@ -354,6 +354,12 @@ struct TokRec {
 };
 
 constexpr uint32_t kMatchGroup = 32;  // matches whose records sit in shared memory at a time
+// Groups of match records in flight to shared memory (a ring after the
+// group's arrays of sources, destinations, lengths and copy starts).
+constexpr uint32_t kRecDepth = 4;
+constexpr uint32_t kRecRingOff = 20 * kMatchGroup + 16;
+// The match pass keeps only its match-record area in shared memory.
+constexpr uint32_t kMatchSmem = kRecRingOff + 16 * kMatchGroup * kRecDepth;
 
 __host__ __device__ inline uint32_t tok_smem_bytes(uint32_t escn) {
   return (sizeof(Lut) + 2 * kRing + 2 * escn + 15) & ~15u;
@@ -788,8 +794,27 @@ __device__ __forceinline__ uint64_t funnel64(uint64_t lo, uint64_t hi, uint32_t 
   return sh ? (lo >> (8 * sh)) | (hi << (64 - 8 * sh)) : lo;
 }
 
+// Bytes [lo, hi) of w to the 8-byte aligned p, in the widest aligned stores
+// that fit.  The lanes of a round store to different lines, so every store
+// a lane saves is an L1 and L2 transaction saved.
+__device__ __forceinline__ void store_bytes8(uint8_t* p, uint64_t w, uint32_t lo, uint32_t hi) {
+  uint32_t k = lo;
+  while (k < hi) {
+    if (!(k & 3) && k + 4 <= hi) {
+      *reinterpret_cast<uint32_t*>(p + k) = (uint32_t)(w >> (8 * k));
+      k += 4;
+    } else if (!(k & 1) && k + 2 <= hi) {
+      *reinterpret_cast<uint16_t*>(p + k) = (uint16_t)(w >> (8 * k));
+      k += 2;
+    } else {
+      p[k] = (uint8_t)(w >> (8 * k));
+      k++;
+    }
+  }
+}
+
 // Destination of a short match: aligned 8-byte words where the match covers
-// them, single bytes at its two ends.  Source byte off + i (off = S mod 8,
+// them, the widest aligned stores that fit at its two ends.  Source byte off + i (off = S mod 8,
 // counted from the first source word) lands at dp[i].
 __device__ __forceinline__ void short_store(uint8_t* dp, uint32_t off, uint32_t len, const uint64_t (&w)[5]) {
   const uint32_t hd = (uint32_t)(reinterpret_cast<uintptr_t>(dp) & 7);
@@ -806,11 +831,7 @@ __device__ __forceinline__ void short_store(uint8_t* dp, uint32_t off, uint32_t 
     if (first >= 0 && first + 8 <= (int)len) {
       *reinterpret_cast<uint64_t*>(dal + 8 * i) = word;
     } else {
-#pragma unroll 1
-      for (uint32_t k = 0; k < 8; k++) {
-        const int di = first + (int)k;
-        if (di >= 0 && di < (int)len) dal[8 * i + k] = (uint8_t)(word >> (8 * k));
-      }
+      store_bytes8(dal + 8 * i, word, (uint32_t)max(0, -first), (uint32_t)min(8, (int)len - first));
     }
   }
 }
@@ -941,23 +962,30 @@ __device__ bool match_block(const DecodeArgs& a, MatchRec* gm, uint32_t b, uint3
   uint32_t* gD = reinterpret_cast<uint32_t*>(gS + kMatchGroup);   // [kMatchGroup] destinations in the block
   uint32_t* gL = gD + kMatchGroup;                                // [kMatchGroup] lengths
   uint32_t* gX = gL + kMatchGroup;                                // [kMatchGroup + 1] starts in a round's copy
-  // each group's records are loaded while the group before it resolves
-  uint4 rn[kLaneMatches];
-#pragma unroll
-  for (uint32_t q = 0; q < kLaneMatches; q++) {
-    const uint32_t j = lane + 32 * q;
-    rn[q] = j < min(kMatchGroup, nm) ? __ldcg(rec + j) : make_uint4(0, 0, 0, 0);
-  }
-  for (uint32_t t0 = 0; ok && t0 < nm; t0 += kMatchGroup) {
-    const uint32_t gn = min(kMatchGroup, nm - t0);
-    uint4 r[kLaneMatches];
-#pragma unroll
-    for (uint32_t q = 0; q < kLaneMatches; q++) r[q] = rn[q];
-    const uint32_t t1 = t0 + kMatchGroup;
+  // records reach a ring of kRecDepth groups by cp.async, kRecDepth - 1
+  // groups ahead of the one resolving; lane j copies and later reads record
+  // j of each group, so no lane reads another's copy
+  uint4* const rring = reinterpret_cast<uint4*>(reinterpret_cast<uint8_t*>(gm) + kRecRingOff);
+  auto issue = [&](uint32_t g) {  // one commit group per call, empty past the last record
+    const uint32_t t = g * kMatchGroup;
 #pragma unroll
     for (uint32_t q = 0; q < kLaneMatches; q++) {
       const uint32_t j = lane + 32 * q;
-      rn[q] = t1 < nm && j < min(kMatchGroup, nm - t1) ? __ldcg(rec + t1 + j) : make_uint4(0, 0, 0, 0);
+      if (t < nm && j < min(kMatchGroup, nm - t)) cp_async16(rring + (g % kRecDepth) * kMatchGroup + j, rec + t + j);
+    }
+    cp_async_commit();
+  };
+#pragma unroll
+  for (uint32_t g = 0; g + 1 < kRecDepth; g++) issue(g);
+  for (uint32_t t0 = 0, g = 0; ok && t0 < nm; t0 += kMatchGroup, g++) {
+    const uint32_t gn = min(kMatchGroup, nm - t0);
+    issue(g + kRecDepth - 1);
+    cp_async_wait<kRecDepth - 1>();  // group g has landed
+    uint4 r[kLaneMatches];
+#pragma unroll
+    for (uint32_t q = 0; q < kLaneMatches; q++) {
+      const uint32_t j = lane + 32 * q;
+      r[q] = j < gn ? rring[(g % kRecDepth) * kMatchGroup + j] : make_uint4(0, 0, 0, 0);
     }
     uint32_t pend = 0;
 #pragma unroll
@@ -994,9 +1022,13 @@ __device__ bool match_block(const DecodeArgs& a, MatchRec* gm, uint32_t b, uint3
       if (k0 < b) {  // blocks k0 .. k1 hold the bytes before this block
         const uint64_t k1 = min((rend - 1) >> a.log2B, (uint64_t)b - 1);
         ext |= 1u << q;
-        const uint32_t* flags = WAIT ? a.ready : a.level;
-        f0[q] = ld_relaxed(flags + k0);
-        f1[q] = k1 != k0 ? ld_relaxed(flags + k1) : f0[q];
+        if (WAIT) {  // flags that other warps publish during the launch
+          f0[q] = ld_relaxed(a.ready + k0);
+          f1[q] = k1 != k0 ? ld_relaxed(a.ready + k1) : f0[q];
+        } else {  // levels, fixed for the launch: through the read-only cache
+          f0[q] = __ldg(a.level + k0);
+          f1[q] = k1 != k0 ? __ldg(a.level + k1) : f0[q];
+        }
       }
       if (rend > bstart) {  // bytes of this block: the group's matches writing them
         const uint32_t s_rel = S > bstart ? (uint32_t)(S - bstart) : 0u, e_rel = (uint32_t)(rend - bstart);
@@ -1198,6 +1230,7 @@ __device__ bool match_block(const DecodeArgs& a, MatchRec* gm, uint32_t b, uint3
       __syncwarp();
     }
   }
+  cp_async_wait<0>();  // no record copy may land after the caller reuses the area
   __syncwarp();
   return ok;
 }
@@ -1217,8 +1250,7 @@ enum { PASS_TOKENS = 0, PASS_LITERALS = 1, PASS_MATCH = 2, PASS_FUSED = 3 };
 // Registers per thread allowed by each pass's launch bounds (256 threads).
 #define ACE_PASS_MIN_CTAS(P) ((P) == PASS_TOKENS ? 4 : (P) == PASS_LITERALS ? 4 : (P) == PASS_FUSED ? 4 : 2)
 
-// The match pass keeps only its match-record area in shared memory.
-constexpr uint32_t kMatchSmem = 20 * kMatchGroup + 16;
+
 
 // Publishes block b (its writes visible device-wide before the flag).
 __device__ __forceinline__ void publish(uint32_t* ready, uint32_t b, uint32_t epoch, uint32_t lane) {
