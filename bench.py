@@ -66,7 +66,11 @@ SCHEDULERS_PER_SM = 4  # warp schedulers per SM: one warp instruction each per c
 METRIC = "decompressed GB/s (% HBM roofline); 16KB seek p50/p99 us, batched vs plain"
 KERNEL_SOURCES = ["paper_2606_24531_gb300/csrc/ace.cu", "paper_2606_24531_gb300/csrc/ace_device.cuh"]
 PROFILES_DIR = os.path.join(ROOT, "profiles")
-LITERAL_PROFILE = os.path.join(PROFILES_DIR, "literal_pass_fastq256.txt")
+# committed ncu summaries of the dominant kernel, per (workload, pass: 0 tokens, 1 literals, 2 matches)
+PROFILES = {("fastq-256MiB-16KiB-blocks", 0): "token_pass_fastq256.txt",
+            ("fastq-256MiB-16KiB-blocks", 1): "literal_pass_fastq256.txt",
+            ("fastq-256MiB-16KiB-blocks", 2): "match_pass_fastq256.txt",
+            ("genome-1GiB-16KiB-blocks", 2): "match_pass_genome1g.txt"}
 
 
 def kernel_sha():
@@ -309,7 +313,7 @@ def run_reference(args, rank):
     }), flush=True)
 
 
-def roofline_of(alg, ms_pass, ms_whole, peaks, peak_kind, sm_count, clocks):
+def roofline_of(alg, ms_pass, ms_whole, peaks, peak_kind, sm_count, clocks, workload):
     """The roofline of the dominant kernel (the slowest pass of the pass
     schedule), on the plain definition's bytes, plus the whole decode.  When
     the committed ncu summary of that kernel matches the current sources, its
@@ -321,7 +325,8 @@ def roofline_of(alg, ms_pass, ms_whole, peaks, peak_kind, sm_count, clocks):
     top = max(range(3), key=lambda p: ms_pass[p])
     hbm_peak = peaks["hbm_gbs"]
     achieved = alg["passes"][top] / (ms_pass[top] / 1e3) / 1e9
-    prof = profile_summary(LITERAL_PROFILE) if top == 1 else None
+    pf = PROFILES.get((workload, top))
+    prof = profile_summary(os.path.join(PROFILES_DIR, pf)) if pf else None
     sm_mhz = (clocks or {}).get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
     issue = None
     if prof and "inst_per_launch" in prof:
@@ -335,7 +340,7 @@ def roofline_of(alg, ms_pass, ms_whole, peaks, peak_kind, sm_count, clocks):
            "peak_kind": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else peak_kind}
     bound = (prof or {}).get("limiter", "hbm")
     r = {"bound": "alu" if bound == "issue" and issue else "hbm", "kernel": names[top],
-         "traffic": int(prof["traffic_bytes_per_launch"]) if prof else None,
+         "traffic": int(prof["traffic_bytes_per_launch"]) if prof and "traffic_bytes_per_launch" in prof else None,
          "algorithmic_bytes": alg["passes"][top], "hbm": hbm, "issue": issue,
          "passes": {n: {"ms": ms_pass[p], "algorithmic_bytes": alg["passes"][p],
                         "achieved_gbs": alg["passes"][p] / (ms_pass[p] / 1e3) / 1e9,
@@ -387,9 +392,10 @@ def decode_config(ace, DeviceArchive, name, dev, stream, flush, steps, warmup, d
     assert da.sync() == ace.ACE_OK
     assert torch.equal(out, d_data), "graph-replayed decode differs from the original (%s)" % name
     del graph
-    peaks, _ = measured_peaks()
+    peaks, peak_kind = measured_peaks()
     alg = algorithmic_bytes(arc, stats, total)
     m = statistics.mean(ms)
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
     res = {"workload": name, "bytes": total, "blocks": info["n_blocks"], "block_size": info["block_size"],
            "archive_bytes": int(arc.size), "ratio": total / arc.size, "ms_per_step": m,
            "ms_median": statistics.median(ms), "GBps": total / (m / 1e3) / 1e9,
@@ -397,6 +403,7 @@ def decode_config(ace, DeviceArchive, name, dev, stream, flush, steps, warmup, d
            "graph_replay": {"ms_median": statistics.median(gms), "GBps": total / (statistics.median(gms) / 1e3) / 1e9},
            "roofline_whole": {"algorithmic_bytes": alg["whole"], "achieved_gbs": alg["whole"] / (m / 1e3) / 1e9,
                               "peak": peaks["hbm_gbs"], "frac": alg["whole"] / (m / 1e3) / 1e9 / peaks["hbm_gbs"]},
+           "roofline": roofline_of(alg, ms_pass, m, peaks, peak_kind, sm_count, None, name),
            "levels": {"count": info["n_levels"],
                       "blocks_per_level": [int(x) for x in ace.ace_index_levels(da.idx, min(info["n_levels"], 64),
                                                                                 stream)]},
@@ -860,7 +867,7 @@ def main():
                    "literal_fraction": stats["literal_bytes"] / total, "matches": stats["n_matches"],
                    "schedule": "passes (tokens, literals, matches by level)",
                    "l2": "flushed between timed steps (256 MiB fill)", "parallelism": "replicas"},
-        "roofline": roofline_of(alg, ms_pass, ms, peaks, peak_kind, sm_count, clocks),
+        "roofline": roofline_of(alg, ms_pass, ms, peaks, peak_kind, sm_count, clocks, args.workload),
         "gpu_launches": (3 + info["n_levels"]) * args.steps,  # per step: header reset, tokens, literals, a match launch per level
         "clocks": clocks,
         "index_build_ms": index_ms,
