@@ -55,6 +55,7 @@ WORKLOADS = {
     "fastq-256MiB-16KiB-blocks": ("fastq", 1 << 28, 1, 14, 16),
     "mixed-1MiB-16KiB-blocks": ("mixed", 1 << 20, 0, 14, 4),
     "genome-1GiB-16KiB-blocks": ("genome", 1 << 30, 3, 14, 20),
+    "text-128MiB-16KiB-blocks": ("text", 1 << 27, 5, 14, 4),  # --workload only: the text profile of configs 4-5
 }
 WORKLOAD = "fastq-256MiB-16KiB-blocks"
 MIN_MATCH = {"fastq": 16, "genome": 20, "text": 4, "mixed": 4}

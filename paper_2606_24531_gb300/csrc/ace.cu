@@ -1085,8 +1085,11 @@ __device__ bool match_block(const DecodeArgs& a, MatchRec* gm, uint32_t b, uint3
     uint32_t chk = ext;
 
     while (__any_sync(kFull, pend != 0)) {
-      const uint32_t P0 = __ballot_sync(kFull, pend & 1u), P1 = __ballot_sync(kFull, pend & 2u);
-      const uint32_t P2 = __ballot_sync(kFull, pend & 4u), P3 = __ballot_sync(kFull, pend & 8u);
+      // pending matches of the group, one bit each (words past the group's size are zero)
+      const uint32_t P0 = __ballot_sync(kFull, pend & 1u);
+      const uint32_t P1 = kLaneMatches > 1 ? __ballot_sync(kFull, pend & 2u) : 0u;
+      const uint32_t P2 = kLaneMatches > 2 ? __ballot_sync(kFull, pend & 4u) : 0u;
+      const uint32_t P3 = kLaneMatches > 3 ? __ballot_sync(kFull, pend & 8u) : 0u;
       uint32_t go = 0;
 #pragma unroll
       for (uint32_t q = 0; q < kLaneMatches; q++)
@@ -1176,6 +1179,11 @@ __device__ bool match_block(const DecodeArgs& a, MatchRec* gm, uint32_t b, uint3
       // the rest laid end to end in group order: gX[j] is where match j
       // starts, gX[kMatchGroup] the total
       const uint32_t bgo = go & ~sgo & ~lgo;
+      if (!__any_sync(kFull, bgo != 0)) {  // none this round
+        pend &= ~go;
+        __syncwarp();  // the round's copies are seen by the next round's loads
+        continue;
+      }
       uint32_t carry = 0;
 #pragma unroll
       for (uint32_t q = 0; q < kLaneMatches; q++) {
@@ -2428,14 +2436,42 @@ __global__ void begin_call_kernel(ScratchHdr* sh) {
   sh->ticket3 = 0;
 }
 
-// FNV-1a 64 (Fowler/Noll/Vo): sequential by definition, one thread.
+// FNV-1a 64 (Fowler/Noll/Vo): sequential by definition, one thread.  The
+// bytes arrive in aligned 16-byte vectors, kFnvBatch at a time, the next
+// batch's loads issued before the current batch is hashed, so the hash chain
+// rather than the load latency sets the time.  The state is kept as two
+// 32-bit halves: with the prime P = 2^40 + 0x1b3, h P mod 2^64 has low word
+// (lo 0x1b3) mod 2^32 and high word ((lo 0x1b3) >> 32) + hi 0x1b3 + (lo << 8),
+// so the chain from byte to byte runs through the low word alone.
+constexpr uint32_t kFnvBatch = 8;
 __global__ void fnv_kernel(const uint8_t* p, uint64_t n, uint64_t* out) {
-  uint64_t h = 0xcbf29ce484222325ull;
-  for (uint64_t i = 0; i < n; i++) {
-    h ^= p[i];
-    h *= 0x100000001b3ull;
+  uint32_t lo = 0x84222325u, hi = 0xcbf29ce4u;  // the 64-bit offset basis
+  auto step = [&](uint32_t b) {
+    lo ^= b;
+    hi = hi * 0x1b3u + __umulhi(lo, 0x1b3u) + (lo << 8);  // beside the low word's chain
+    lo *= 0x1b3u;
+  };
+  uint64_t i = 0;
+  for (; i < n && (reinterpret_cast<uintptr_t>(p + i) & 15); i++) step(p[i]);
+  const uint4* v = reinterpret_cast<const uint4*>(p + i);
+  const uint64_t nb = (n - i) / (16 * kFnvBatch);  // whole batches
+  uint4 cur[kFnvBatch], nxt[kFnvBatch];
+#pragma unroll
+  for (uint32_t k = 0; k < kFnvBatch; k++) cur[k] = nb ? v[k] : make_uint4(0, 0, 0, 0);
+  for (uint64_t q = 0; q < nb; q++) {
+#pragma unroll
+    for (uint32_t k = 0; k < kFnvBatch; k++) nxt[k] = q + 1 < nb ? v[(q + 1) * kFnvBatch + k] : cur[k];
+#pragma unroll
+    for (uint32_t k = 0; k < kFnvBatch; k++) {
+      const uint32_t w[4] = {cur[k].x, cur[k].y, cur[k].z, cur[k].w};
+#pragma unroll
+      for (uint32_t j = 0; j < 16; j++) step((w[j >> 2] >> (8 * (j & 3))) & 0xffu);
+    }
+#pragma unroll
+    for (uint32_t k = 0; k < kFnvBatch; k++) cur[k] = nxt[k];
   }
-  *out = h;
+  for (i += nb * 16 * kFnvBatch; i < n; i++) step(p[i]);
+  *out = ((uint64_t)hi << 32) | lo;
 }
 
 }  // namespace

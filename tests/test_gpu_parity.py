@@ -395,12 +395,16 @@ def test_corrupt_directory_rejected_at_index_build():
 
 
 def test_device_fnv_matches_oracle():
+    """Whole buffers and slices at every start alignment, with lengths around
+    the 16-byte vectors and 128-byte batches the kernel reads."""
     data = synth.generate("fastq", 100_000, 15)
     d = torch.from_numpy(data).cuda()
     res = torch.zeros(1, dtype=torch.int64, device="cuda")
-    ace.ace_fnv1a64(d, data.size, res)
-    torch.cuda.synchronize()
-    assert int(res.cpu().numpy().view(np.uint64)[0]) == oracle.fnv1a64(data)
+    cases = [(0, data.size), (0, 0)] + [(o, n) for o in range(0, 18) for n in (1, 15, 16, 127, 128, 129, 300, 4099)]
+    for off, n in cases:
+        ace.ace_fnv1a64(d[off:], n, res)
+        torch.cuda.synchronize()
+        assert int(res.cpu().numpy().view(np.uint64)[0]) == oracle.fnv1a64(data[off:off + n]), (off, n)
 
 
 def test_levels_match_oracle():
