@@ -463,8 +463,8 @@ ace_status ace_fnv1a64(const void *d_p, uint64_t n, uint64_t *d_result, cudaStre
  * so order them (one stream, or events).  The first call on a device looks
  * up the array's device address; make that first call before any stream
  * capture.  The index's device must be current.  Archives whose per-block
- * tables and token records do not fit, or requests covering more blocks
- * than the remaining slots, return ACE_E_NOMEM.  Calls no allocator (the
+ * tables do not fit, or requests covering more blocks than the remaining
+ * slots, return ACE_E_NOMEM.  Calls no allocator (the
  * status buffer above already exists once an index was built).
  * Synchronises s and returns the seek's device-side status (ACE_OK,
  * ACE_E_CORRUPT, ACE_E_TIMEOUT, ACE_E_NOMEM when the closure exceeds the

@@ -308,8 +308,6 @@ struct DecodeArgs {
   uint8_t* slice;          // seek: caller's output
   uint64_t coord, len;     // seek: requested range
   uint64_t timeout_ns;
-  uint8_t* warp_scratch;   // per-warp token records
-  uint64_t warp_scratch_bytes;
   MatchRec* recs;          // match records, from the token pass to the literal and match passes
   const uint64_t* match_ptr;  // whole decode: block -> first record; null: max_ntok records per slot
   const uint32_t* level;   // each block's dependency level
@@ -344,15 +342,6 @@ struct LitMem {
   uint32_t* tlit;  // [window + 1] index of each token's first literal among the block's literals
 };
 
-// Token records of the block a warp is decoding, in global scratch: for
-// every token the start of its literal run, its match length, and its
-// match's offset bytes.
-struct TokRec {
-  uint32_t* tdst;  // [max_ntok + 1]
-  uint32_t* tml;   // [max_ntok]
-  uint8_t* offb;   // [5 max_ntok]
-};
-
 constexpr uint32_t kMatchGroup = 32;  // matches whose records sit in shared memory at a time
 // Groups of match records in flight to shared memory (a ring after the
 // group's arrays of sources, destinations, lengths and copy starts).
@@ -373,10 +362,6 @@ __host__ __device__ inline uint32_t lit_smem_bytes(uint32_t window, uint32_t rin
   return (sizeof(Lut) + ring + 8 * (window + 1) + 15) & ~15u;
 }
 
-__host__ __device__ inline uint64_t warp_scratch_bytes(uint64_t max_ntok) {
-  return (4 * (max_ntok + 1) * 2 + 5 * max_ntok + 255) & ~255ull;
-}
-
 __device__ inline TokMem carve_tok(uint8_t* base) {
   TokMem m;
   m.lut = reinterpret_cast<Lut*>(base);
@@ -392,14 +377,6 @@ __device__ inline LitMem carve_lit(uint8_t* base, uint32_t window, uint32_t ring
   m.tdst = reinterpret_cast<uint32_t*>(m.ring + ring);
   m.tlit = m.tdst + (window + 1);
   return m;
-}
-
-__device__ inline TokRec tok_records(uint8_t* base, uint64_t max_ntok) {
-  TokRec r;
-  r.tdst = reinterpret_cast<uint32_t*>(base);
-  r.tml = r.tdst + (max_ntok + 1);
-  r.offb = reinterpret_cast<uint8_t*>(r.tml + (max_ntok + 1));
-  return r;
 }
 
 // Slot of block k in a seek's scratch.  The entry is read back from scratch
@@ -514,7 +491,7 @@ __device__ __forceinline__ void warp_copy(uint8_t* dst, const uint8_t* src, uint
 // token positions from these records.  Returns false if the block is corrupt
 // (the error is recorded).
 template <bool SEEK>
-__device__ bool token_block(const DecodeArgs& a, const TokMem& m, const TokRec& g, uint32_t b, uint32_t lane) {
+__device__ bool token_block(const DecodeArgs& a, const TokMem& m, uint32_t b, uint32_t lane) {
   bool ok = true;
   const uint32_t* dw = reinterpret_cast<const uint32_t*>(a.dir + b);
   uint32_t dv = lane < 16 ? __ldg(dw + lane) : 0u;
@@ -557,6 +534,10 @@ __device__ bool token_block(const DecodeArgs& a, const TokMem& m, const TokRec& 
   uint32_t out_pos = 0, lit_pos = 0, esc_rank = 0;
   bool bad = false;
   const uint32_t cbase = 2 * nesc, cend = cbase + 2 * ntok;
+  // match t's record is written whole here (destination and length; the
+  // source's bytes follow from the offset stream); a match ends token t
+  // (t < ntok - 1), its destination is the token's start plus its run
+  uint4* const rec4 = reinterpret_cast<uint4*>(recs_of<SEEK>(a, b));
   if (ok) rans_run(sn, rn, *m.lut, cend, lane, lt, [&](bool act, uint32_t i, uint32_t s) {
     bool e = act && s == 255;
     uint32_t eb = __ballot_sync(kFull, e);
@@ -573,48 +554,44 @@ __device__ bool token_block(const DecodeArgs& a, const TokMem& m, const TokRec& 
     uint32_t io = warp_incl_sum(to, lane), il = warp_incl_sum(tl, lane);
     if (own) {
       uint32_t t = (i - cbase) >> 1;
-      g.tdst[t] = out_pos + io - to;
-      g.tml[t] = ml;
-      if (t == ntok - 1 && ml) bad = true;  // the block's last token carries no match
+      if (t + 1 < ntok) rec4[t] = make_uint4(0u, 0u, out_pos + io - to + lr, ml);
+      else if (ml) bad = true;  // the block's last token carries no match
     }
     out_pos += __shfl_sync(kFull, io, 31);
     lit_pos += __shfl_sync(kFull, il, 31);
     if (out_pos > blen) bad = true;
   });
-  if (lane == 0) g.tdst[ntok] = out_pos;
   bad |= out_pos != blen || lit_pos != nlit || esc_rank != nesc;
   if (__any_sync(kFull, bad)) fail(a, ok, ACE_E_CORRUPT, b, 32, lane);
 
   // ---- absolute offsets: off_width bytes for every token but the last
   const uint32_t nm = ntok - 1;
   if (ok && nm) {
+    __syncwarp();  // the records' zero source bytes are written before any lane fills them
     if (!lut_build(so, *m.lut, lane)) fail(a, ok, ACE_E_CORRUPT, b, 33, lane);
     const uint32_t oend = w * nm;
+    // offset byte i is byte i mod w of match i / w's absolute source (little
+    // endian, w = 4 or 5), written straight into its record
+    uint8_t* const rb = reinterpret_cast<uint8_t*>(rec4);
+    auto at = [&](uint32_t i) -> uint8_t* {
+      const uint32_t t = w == 4 ? i >> 2 : __umulhi(i, 0xCCCCCCCDu) >> 2;  // floor(i / 5) for every 32-bit i
+      return rb + 16 * (size_t)t + (i - w * t);
+    };
     auto put = [&](bool act, uint32_t i, uint32_t s) {
-      if (act) g.offb[i] = (uint8_t)s;
+      if (act) *at(i) = (uint8_t)s;
     };
     if (ok && !so.stored && so.k == 0 && oend >= 64) {  // slot-table streams: full rounds in the fast loop
       uint32_t i = lane;
       table_full_rounds(so, ro, *m.lut, oend >> 5, lane, lt, [&](uint32_t s) {
-        g.offb[i] = (uint8_t)s;
+        *at(i) = (uint8_t)s;
         i += 32;
       });
     }
     if (ok) rans_run(so, ro, *m.lut, oend, lane, lt, put);
   }
   __syncwarp();
-  // the match records: absolute source, destination in the block, length
-  if (ok) {
-    MatchRec* rec = recs_of<SEEK>(a, b);
-    for (uint32_t t = lane; t < nm; t += 32) {
-      uint32_t ml = g.tml[t];
-      uint64_t S = read_src(g.offb + w * t, w);
-      uint32_t dl = g.tdst[t + 1] - ml;
-      if (ml && S >= bstart + dl) bad = true;  // a source must precede its destination
-      rec[t] = MatchRec{S, dl, ml};
-    }
-    if (__any_sync(kFull, bad)) fail(a, ok, ACE_E_CORRUPT, b, 37, lane);
-  }
+  // a source at or after its destination is caught where sources are read:
+  // match_block and match_small_kernel check every record
   if (ok) {
     bool fin = stream_finished(sn) && stream_finished(so);
     if (!__all_sync(kFull, fin)) fail(a, ok, ACE_E_CORRUPT, b, 40, lane);
@@ -1306,9 +1283,8 @@ constexpr uint32_t kMaxWarps = 8;
 // the warp holding it.
 template <bool SEEK, class Jobs>
 __device__ void fused_loop(const Jobs& jobs, ScratchHdr* sh, uint32_t n_items, uint64_t timeout_ns, uint8_t* wsm,
-                           uint8_t* wreg, uint32_t lane, uint32_t epoch, uint32_t window, uint32_t max_ntok) {
+                           uint32_t lane, uint32_t epoch, uint32_t window) {
   uint32_t* const ticket = &sh->ticket;
-  const TokRec g = tok_records(wreg, max_ntok);
   constexpr uint32_t ring = SEEK ? kSeekRing : kRing;
   // list positions of the warp's deferred blocks, a ring in shared memory
   // (registers are the scarce resource here): q[(q0 + k) % kDeferred]
@@ -1395,7 +1371,7 @@ __device__ void fused_loop(const Jobs& jobs, ScratchHdr* sh, uint32_t n_items, u
     }
     uint32_t b;
     auto&& a = jobs.job(u, b);
-    bool ok = token_block<SEEK>(a, carve_tok(wsm), g, b, lane);
+    bool ok = token_block<SEEK>(a, carve_tok(wsm), b, lane);
     if (ok) ok = literal_block<SEEK, ring>(a, carve_lit(wsm, window, ring), b, lane);
     if (!ok) break;
     if (lane == 0) q[(q0 + nq) % kDeferred] = u;
@@ -1419,8 +1395,7 @@ __global__ void __launch_bounds__(256, ACE_PASS_MIN_CTAS(PASS)) decode_kernel(De
   if (PASS != PASS_TOKENS && *(volatile uint32_t*)&a.sh->status) return;
   uint8_t* wsm = smem + (size_t)wid * a.warp_smem;
   if (PASS == PASS_FUSED) {
-    uint8_t* wreg = a.warp_scratch + (size_t)(blockIdx.x * (blockDim.x >> 5) + wid) * a.warp_scratch_bytes;
-    fused_loop<SEEK>(ArchiveJobs<SEEK>{a}, a.sh, n_items, a.timeout_ns, wsm, wreg, lane, epoch, a.window, a.max_ntok);
+    fused_loop<SEEK>(ArchiveJobs<SEEK>{a}, a.sh, n_items, a.timeout_ns, wsm, lane, epoch, a.window);
     return;
   }
   uint32_t* ticket = PASS == PASS_TOKENS ? &a.sh->ticket : PASS == PASS_LITERALS ? &a.sh->ticket2 : &a.sh->ticket3;
@@ -1431,9 +1406,7 @@ __global__ void __launch_bounds__(256, ACE_PASS_MIN_CTAS(PASS)) decode_kernel(De
     if (it >= n_items) break;
     uint32_t b = __ldg(a.items + it);
     if (PASS == PASS_TOKENS) {
-      TokRec g = tok_records(a.warp_scratch + (size_t)(blockIdx.x * (blockDim.x >> 5) + wid) * a.warp_scratch_bytes,
-                             a.max_ntok);
-      token_block<SEEK>(a, carve_tok(wsm), g, b, lane);
+      token_block<SEEK>(a, carve_tok(wsm), b, lane);
       continue;
     }
     if (PASS == PASS_LITERALS) {
@@ -1770,8 +1743,6 @@ struct BatchArgs {
   uint32_t window, warp_smem, esc_cap, max_ntok;
   ScratchHdr* sh;
   uint64_t timeout_ns;
-  uint8_t* warp_scratch;
-  uint64_t warp_scratch_bytes;
   uint32_t long_min;
 };
 
@@ -1837,9 +1808,7 @@ __global__ void __launch_bounds__(256, ACE_PASS_MIN_CTAS(PASS)) batch_decode_ker
   uint8_t* wsm = smem + (size_t)wid * ba.warp_smem;
   const uint32_t epoch = *(volatile uint32_t*)&ba.sh->epoch;
   if (PASS == PASS_FUSED) {
-    uint8_t* wreg = ba.warp_scratch + (size_t)(blockIdx.x * (blockDim.x >> 5) + wid) * ba.warp_scratch_bytes;
-    fused_loop<false>(BatchJobs{ba}, ba.sh, ba.n_items, ba.timeout_ns, wsm, wreg, lane, epoch, ba.window,
-                      ba.max_ntok);
+    fused_loop<false>(BatchJobs{ba}, ba.sh, ba.n_items, ba.timeout_ns, wsm, lane, epoch, ba.window);
     return;
   }
   uint32_t* ticket = PASS == PASS_TOKENS ? &ba.sh->ticket : PASS == PASS_LITERALS ? &ba.sh->ticket2 : &ba.sh->ticket3;
@@ -1852,9 +1821,7 @@ __global__ void __launch_bounds__(256, ACE_PASS_MIN_CTAS(PASS)) batch_decode_ker
     uint32_t b;
     const DecodeArgs a = jobs.job(it, b);
     if (PASS == PASS_TOKENS) {
-      TokRec g = tok_records(ba.warp_scratch + (size_t)(blockIdx.x * (blockDim.x >> 5) + wid) * ba.warp_scratch_bytes,
-                             ba.max_ntok);
-      token_block<false>(a, carve_tok(wsm), g, b, lane);
+      token_block<false>(a, carve_tok(wsm), b, lane);
     } else if (PASS == PASS_LITERALS) {
       literal_block<false, kRing>(a, carve_lit(wsm, ba.window, kRing), b, lane);
     } else {
@@ -2313,8 +2280,6 @@ struct CacheDecodeArgs {
   CacheArgs c;
   uint32_t window, warp_smem, esc_cap, max_ntok;
   uint64_t timeout_ns;
-  uint8_t* warp_scratch;
-  uint64_t warp_scratch_bytes;
   uint32_t long_min;
 };
 
@@ -2361,9 +2326,7 @@ __global__ void __launch_bounds__(256, ACE_PASS_MIN_CTAS(PASS)) cache_decode_ker
     a.recs = c.recs;
     a.match_ptr = nullptr;
     if (PASS == PASS_TOKENS) {
-      TokRec g = tok_records(ca.warp_scratch + (size_t)(blockIdx.x * (blockDim.x >> 5) + wid) * ca.warp_scratch_bytes,
-                             ca.max_ntok);
-      token_block<true>(a, carve_tok(wsm), g, b, lane);
+      token_block<true>(a, carve_tok(wsm), b, lane);
     } else if (PASS == PASS_LITERALS) {
       literal_block<true, kSeekRing>(a, carve_lit(wsm, ca.window, kSeekRing), b, lane);
     } else {
@@ -2535,8 +2498,7 @@ IndexLayout index_layout(uint64_t nb) {
 }
 
 struct ScratchLayout {
-  uint64_t ready, slot_of, work, marks, front0, front1, lv_done, warps, tail, total;
-  uint64_t n_warps;  // per-warp token regions available
+  uint64_t ready, slot_of, work, marks, front0, front1, lv_done, tail, total;
 };
 
 // Bytes one seek slot needs: the decoded block and its match records.
@@ -2546,14 +2508,13 @@ inline uint64_t slot_bytes(uint32_t log2B, uint64_t max_ntok) {
 
 constexpr uint32_t kMaxWindow = 256;
 constexpr uint32_t kMaxWarpsPerCta = 8;  // the decode kernel's launch bounds: 256 threads
-constexpr uint32_t kMaxWarpsPerSM = 32;  // per-warp token regions provisioned per SM
 
 // One layout serves every call on a scratch buffer, so whole decodes and
 // seeks may share it: header, ready flags, the seek's slot map, work list,
-// closure marks and frontiers, the per-warp token regions, then a tail that a
-// whole decode uses for the archive's match records and a seek for its block
-// slots followed by their match records.
-ScratchLayout scratch_layout(uint64_t nb, uint32_t log2B, uint64_t max_seek, int num_sms, uint64_t max_ntok,
+// closure marks and frontiers, the fused schedule's level counters, then a
+// tail that a whole decode uses for the archive's match records and a seek
+// for its block slots followed by their match records.
+ScratchLayout scratch_layout(uint64_t nb, uint32_t log2B, uint64_t max_seek, uint64_t max_ntok,
                              uint64_t n_matches) {
   ScratchLayout L;
   uint64_t o = sizeof(ScratchHdr);
@@ -2571,10 +2532,6 @@ ScratchLayout scratch_layout(uint64_t nb, uint32_t log2B, uint64_t max_seek, int
   o = align256(o + 4 * nb);
   L.lv_done = o;
   o = align256(o + 4 * (nb + 1));
-  uint64_t items = std::max<uint64_t>(nb, max_seek);
-  L.n_warps = std::min<uint64_t>((uint64_t)num_sms * kMaxWarpsPerSM, items + 16);
-  L.warps = o;
-  o = align256(o + L.n_warps * warp_scratch_bytes(max_ntok));
   L.tail = o;
   o = align256(o + std::max<uint64_t>(16 * n_matches, max_seek * slot_bytes(log2B, max_ntok)));
   L.total = o;
@@ -2686,7 +2643,7 @@ ace_status occupancy(K kernel, int device, uint32_t warps, size_t smem, int* occ
 // k3 is the fused pass
 template <class K0, class K1, class K2, class K3>
 ace_status plan_launch(const ace_index* idx, const ace_tune* tune, uint32_t log2B, uint64_t max_items,
-                       uint64_t max_warps, K0 k0, K1 k1, K2 k2, K3 k3, int* occ_cache, Launch* L,
+                       K0 k0, K1 k1, K2 k2, K3 k3, int* occ_cache, Launch* L,
                        uint32_t lit_ring = kRing) {
   ace_tune t = tune ? *tune : idx->tune;
   L->warps = t.warps_per_cta ? t.warps_per_cta : 4;
@@ -2722,22 +2679,13 @@ ace_status plan_launch(const ace_index* idx, const ace_tune* tune, uint32_t log2
     if (t.ctas_per_sm && (int)t.ctas_per_sm < per[p]) per[p] = (int)t.ctas_per_sm;
   }
   uint64_t need = std::max<uint64_t>(1, (max_items + L->warps - 1) / L->warps);
-  // the token and fused passes keep per-warp records in scratch: at most
-  // max_warps warps
-  uint64_t g0 = std::min<uint64_t>((uint64_t)idx->num_sms * per[0], max_warps / L->warps);
-  uint64_t g3 = std::min<uint64_t>((uint64_t)idx->num_sms * per[3], max_warps / L->warps);
-  if (g0 < 1 || g3 < 1) return ACE_E_NOMEM;
-  L->grid[PASS_TOKENS] = (uint32_t)std::min(g0, need);
-  L->grid[PASS_LITERALS] = (uint32_t)std::min<uint64_t>((uint64_t)idx->num_sms * per[1], need);
-  L->grid[PASS_MATCH] = (uint32_t)std::min<uint64_t>((uint64_t)idx->num_sms * per[2], need);
-  L->grid[PASS_FUSED] = (uint32_t)std::min(g3, need);
+  for (int p = 0; p < 4; p++) L->grid[p] = (uint32_t)std::min<uint64_t>((uint64_t)idx->num_sms * per[p], need);
   return ACE_OK;
 }
 
 template <bool SEEK>
-ace_status plan_index_launch(const ace_index* idx, const ace_tune* tune, uint64_t max_items, uint64_t max_warps,
-                             Launch* L) {
-  return plan_launch(idx, tune, idx->h.log2_block, max_items, max_warps, decode_kernel<SEEK, PASS_TOKENS>,
+ace_status plan_index_launch(const ace_index* idx, const ace_tune* tune, uint64_t max_items, Launch* L) {
+  return plan_launch(idx, tune, idx->h.log2_block, max_items, decode_kernel<SEEK, PASS_TOKENS>,
                      decode_kernel<SEEK, PASS_LITERALS>, decode_kernel<SEEK, PASS_MATCH>,
                      decode_kernel<SEEK, PASS_FUSED>, &idx->occ_cache[SEEK][0][0][0], L,
                      SEEK ? kSeekRing : kRing);
@@ -3067,16 +3015,16 @@ ace_status ace_index_free(ace_index* idx) {
 
 ace_status ace_scratch_size(const ace_index* idx, uint64_t max_seek_blocks, uint64_t* bytes) {
   if (!idx || !bytes) return ACE_E_INVAL;
-  *bytes = scratch_layout(idx->h.n_blocks, idx->h.log2_block, max_seek_blocks, idx->num_sms, idx->max_ntok, idx->n_matches).total;
+  *bytes = scratch_layout(idx->h.n_blocks, idx->h.log2_block, max_seek_blocks, idx->max_ntok, idx->n_matches).total;
   return ACE_OK;
 }
 
 ace_status ace_scratch_init(const ace_index* idx, void* d_scratch, uint64_t scratch_bytes, cudaStream_t s) {
   if (!idx || !d_scratch || !aligned(d_scratch, 256)) return ACE_E_INVAL;
-  ScratchLayout L0 = scratch_layout(idx->h.n_blocks, idx->h.log2_block, 0, idx->num_sms, idx->max_ntok, idx->n_matches);
+  ScratchLayout L0 = scratch_layout(idx->h.n_blocks, idx->h.log2_block, 0, idx->max_ntok, idx->n_matches);
   if (scratch_bytes < L0.total) return ACE_E_NOMEM;
   // header, ready flags, and (when present) slot map, work list and marks
-  uint64_t clear = L0.warps;
+  uint64_t clear = L0.tail;
   CUDA_TRY(cudaMemsetAsync(d_scratch, 0, clear, s));
   return ACE_OK;
 }
@@ -3092,11 +3040,11 @@ ace_status decode_all_passes(const ace_index* idx, uint32_t passes, void* d_out,
   if (!idx || !d_scratch || (!d_out && idx->h.total_size)) return ACE_E_INVAL;
   if (!aligned(d_scratch, 256) || !aligned(d_out, 16)) return ACE_E_INVAL;
   if (out_bytes < idx->h.total_size) return ACE_E_NOMEM;
-  ScratchLayout SL = scratch_layout(idx->h.n_blocks, idx->h.log2_block, 0, idx->num_sms, idx->max_ntok, idx->n_matches);
+  ScratchLayout SL = scratch_layout(idx->h.n_blocks, idx->h.log2_block, 0, idx->max_ntok, idx->n_matches);
   if (scratch_bytes < SL.total) return ACE_E_NOMEM;
   if (!idx->h.n_blocks) return ACE_OK;
   Launch L;
-  ace_status rc = plan_index_launch<false>(idx, tune, idx->h.n_blocks, SL.n_warps, &L);
+  ace_status rc = plan_index_launch<false>(idx, tune, idx->h.n_blocks, &L);
   if (rc) return rc;
   ScratchHdr* sh = static_cast<ScratchHdr*>(d_scratch);
   DecodeArgs a{};
@@ -3117,8 +3065,6 @@ ace_status decode_all_passes(const ace_index* idx, uint32_t passes, void* d_out,
   a.sh = sh;
   a.ready = reinterpret_cast<uint32_t*>(static_cast<uint8_t*>(d_scratch) + SL.ready);
   a.timeout_ns = L.timeout;
-  a.warp_scratch = static_cast<uint8_t*>(d_scratch) + SL.warps;
-  a.warp_scratch_bytes = warp_scratch_bytes(idx->max_ntok);
   a.recs = reinterpret_cast<MatchRec*>(static_cast<uint8_t*>(d_scratch) + SL.tail);
   a.match_ptr = idx->d_match_ptr;
   a.level = idx->d_level;
@@ -3195,7 +3141,7 @@ ace_status ace_seek(const ace_index* idx, uint64_t coord, uint64_t len, void* d_
   if (out_bytes < len) return ACE_E_NOMEM;
   uint64_t nb = idx->h.n_blocks;
   uint32_t log2B = idx->h.log2_block;
-  ScratchLayout S1 = scratch_layout(nb, log2B, 1, idx->num_sms, idx->max_ntok, 0);
+  ScratchLayout S1 = scratch_layout(nb, log2B, 1, idx->max_ntok, 0);
   if (scratch_bytes < S1.total) return ACE_E_NOMEM;
   // the layout before the slots does not depend on the slot count (a seek
   // never decodes more than n_blocks blocks)
@@ -3221,7 +3167,7 @@ ace_status ace_seek(const ace_index* idx, uint64_t coord, uint64_t len, void* d_
   c.n_levels = idx->n_levels;
   c.ready = reinterpret_cast<uint32_t*>(base + S1.ready);
   Launch L;
-  ace_status rc = plan_index_launch<true>(idx, nullptr, cap, S1.n_warps, &L);
+  ace_status rc = plan_index_launch<true>(idx, nullptr, cap, &L);
   if (rc) return rc;
   // the fused schedule needs the closure's work list in level order
   if (!idx->by_levels) L.schedule = ACE_SCHEDULE_PASSES;
@@ -3249,8 +3195,6 @@ ace_status ace_seek(const ace_index* idx, uint64_t coord, uint64_t len, void* d_
   a.coord = coord;
   a.len = len;
   a.timeout_ns = L.timeout;
-  a.warp_scratch = base + S1.warps;
-  a.warp_scratch_bytes = warp_scratch_bytes(idx->max_ntok);
   a.recs = reinterpret_cast<MatchRec*>(base + S1.tail + (cap << log2B));
   a.match_ptr = nullptr;
   a.level = idx->d_level;
@@ -3368,7 +3312,7 @@ struct ace_batch {
 namespace {
 
 struct BatchLayout {
-  uint64_t objs, item_start, ready, lv_done, lv_done_bytes, warps, recs, total, n_warps, max_ntok, items, n_matches;
+  uint64_t objs, item_start, ready, lv_done, lv_done_bytes, recs, total, max_ntok, items, n_matches;
   uint32_t max_log2B;
 };
 
@@ -3376,7 +3320,7 @@ ace_status batch_layout(const ace_index* const* idx, uint32_t n, BatchLayout* B)
   if (!idx || n == 0) return ACE_E_INVAL;
   uint64_t ready = 0, items = 0, max_ntok = 0, matches = 0, levels = 0;
   uint32_t max_log2B = 0;
-  int dev = idx[0] ? idx[0]->device : -1, sms = idx[0] ? idx[0]->num_sms : 0;
+  int dev = idx[0] ? idx[0]->device : -1;
   for (uint32_t i = 0; i < n; i++) {
     if (!idx[i] || idx[i]->device != dev) return ACE_E_INVAL;
     items += idx[i]->h.n_blocks;
@@ -3397,9 +3341,6 @@ ace_status batch_layout(const ace_index* const* idx, uint32_t n, BatchLayout* B)
   B->lv_done = o;
   B->lv_done_bytes = 4 * levels;
   o = align256(o + 4 * levels);
-  B->n_warps = std::min<uint64_t>((uint64_t)sms * kMaxWarpsPerSM, items + 16);
-  B->warps = o;
-  o = align256(o + B->n_warps * warp_scratch_bytes(max_ntok));
   B->recs = o;
   o = align256(o + 16 * matches);
   B->total = o;
@@ -3469,11 +3410,11 @@ ace_status ace_batch_create(const ace_index* const* idx, uint32_t n, void* const
   b->lv_done_off = B.lv_done;
   b->lv_done_bytes = B.lv_done_bytes;
   // the launch shape uses the largest block size's escape table
-  rc = plan_launch(idx[0], tune, B.max_log2B, B.items, B.n_warps, batch_decode_kernel<PASS_TOKENS>,
+  rc = plan_launch(idx[0], tune, B.max_log2B, B.items, batch_decode_kernel<PASS_TOKENS>,
                    batch_decode_kernel<PASS_LITERALS>, batch_decode_kernel<PASS_MATCH>,
                    batch_decode_kernel<PASS_FUSED>, &b->occ[0][0][0], &b->L);
   if (rc == ACE_OK &&
-      (cudaMemsetAsync(base, 0, B.warps, s) != cudaSuccess ||
+      (cudaMemsetAsync(base, 0, B.recs, s) != cudaSuccess ||
        cudaMemcpyAsync(base + B.objs, od.data(), n * sizeof(ObjDesc), cudaMemcpyHostToDevice, s) != cudaSuccess ||
        cudaMemcpyAsync(base + B.item_start, start.data(), 4ull * (n + 1), cudaMemcpyHostToDevice, s) != cudaSuccess ||
        cudaStreamSynchronize(s) != cudaSuccess))
@@ -3493,8 +3434,6 @@ ace_status ace_batch_create(const ace_index* const* idx, uint32_t n, void* const
   a.max_ntok = (uint32_t)B.max_ntok;
   a.sh = reinterpret_cast<ScratchHdr*>(base);
   a.timeout_ns = b->L.timeout;
-  a.warp_scratch = base + B.warps;
-  a.warp_scratch_bytes = warp_scratch_bytes(B.max_ntok);
   a.long_min = b->L.long_min;
   *out = b;
   return ACE_OK;
@@ -3559,8 +3498,8 @@ struct ace_cache {
 namespace {
 
 struct CacheLayout {
-  uint64_t arcs, minmax, front0, front1, work, taken, owner_arc, owner_blk, ref, use, reqs, warps, slots, recs, total,
-      n_warps, max_ntok, max_work;
+  uint64_t arcs, minmax, front0, front1, work, taken, owner_arc, owner_blk, ref, use, reqs, slots, recs, total, max_ntok,
+      max_work;
 };
 
 // Blocks one seek batch may decode at most (work items): 32 per request the
@@ -3600,9 +3539,6 @@ CacheLayout cache_layout(const ace_index* const* idx, uint32_t n, uint64_t n_slo
   o = align256(o + 4 * n_slots);
   C.reqs = o;
   o = align256(o + sizeof(ace_seek_req) * (uint64_t)max_reqs);
-  C.n_warps = std::min<uint64_t>((uint64_t)idx[0]->num_sms * kMaxWarpsPerSM, mw + 16);
-  C.warps = o;
-  o = align256(o + C.n_warps * warp_scratch_bytes(max_ntok));
   C.slots = o;
   o = align256(o + (n_slots << log2B));
   C.recs = o;
@@ -3685,7 +3621,7 @@ ace_status ace_cache_create(const ace_index* const* idx, uint32_t n, void* const
   c->owner_off = C.owner_arc;
   // seek batches run the three passes (their work list is in block order,
   // not level order); the fused entry only sizes like the match pass
-  rc = plan_launch(idx[0], tune, log2B, C.max_work, C.n_warps, cache_decode_kernel<PASS_TOKENS>,
+  rc = plan_launch(idx[0], tune, log2B, C.max_work, cache_decode_kernel<PASS_TOKENS>,
                    cache_decode_kernel<PASS_LITERALS>, cache_decode_kernel<PASS_MATCH>,
                    cache_decode_kernel<PASS_MATCH>, &c->occ[0][0][0], &c->L, kSeekRing);
   // header (epoch 1: no block is cached, since every ready flag starts at 0)
@@ -3729,8 +3665,6 @@ ace_status ace_cache_create(const ace_index* const* idx, uint32_t n, void* const
   d.esc_cap = esc_cap(log2B);
   d.max_ntok = (uint32_t)C.max_ntok;
   d.timeout_ns = c->L.timeout;
-  d.warp_scratch = base + C.warps;
-  d.warp_scratch_bytes = warp_scratch_bytes(C.max_ntok);
   d.long_min = c->L.long_min;
   *out = c;
   return ACE_OK;
@@ -3841,7 +3775,6 @@ ace_status ace_cache_free(ace_cache* c) {
 namespace {
 
 constexpr uint64_t kStaticScratchBytes = 32ull << 20;
-constexpr int kStaticWarpSMs = 2;  // per-warp token regions for 2 SMs' worth (64 warps)
 constexpr int kMaxDevices = 64;
 
 __device__ __align__(256) uint8_t g_static_scratch[kStaticScratchBytes];
@@ -3878,7 +3811,7 @@ ace_status ace_seek_noalloc(const ace_index* idx, uint64_t coord, uint64_t len, 
   if (rc) return rc;
   const uint64_t nb = idx->h.n_blocks;
   const uint32_t log2B = idx->h.log2_block;
-  ScratchLayout S = scratch_layout(nb, log2B, 1, kStaticWarpSMs, idx->max_ntok, 0);
+  ScratchLayout S = scratch_layout(nb, log2B, 1, idx->max_ntok, 0);
   if (S.tail > kStaticScratchBytes) return ACE_E_NOMEM;  // archive too large for the fixed scratch
   uint64_t cap = std::min<uint64_t>(nb, (kStaticScratchBytes - S.tail) / slot_bytes(log2B, idx->max_ntok));
   uint64_t first = coord >> log2B, last = (coord + len - 1) >> log2B;
@@ -3908,7 +3841,7 @@ ace_status ace_seek_noalloc(const ace_index* idx, uint64_t coord, uint64_t len, 
   c.n_levels = idx->n_levels;
   c.ready = reinterpret_cast<uint32_t*>(base + S.ready);
   Launch L;
-  rc = plan_index_launch<true>(idx, nullptr, cap, S.n_warps, &L);
+  rc = plan_index_launch<true>(idx, nullptr, cap, &L);
   if (rc) return rc;
   if (!idx->by_levels) L.schedule = ACE_SCHEDULE_PASSES;
   c.lv_done = L.schedule == ACE_SCHEDULE_FUSED ? reinterpret_cast<uint32_t*>(base + S.lv_done) : nullptr;
@@ -3935,8 +3868,6 @@ ace_status ace_seek_noalloc(const ace_index* idx, uint64_t coord, uint64_t len, 
   a.coord = coord;
   a.len = len;
   a.timeout_ns = L.timeout;
-  a.warp_scratch = base + S.warps;
-  a.warp_scratch_bytes = warp_scratch_bytes(idx->max_ntok);
   a.recs = reinterpret_cast<MatchRec*>(base + S.tail + (cap << log2B));
   a.match_ptr = nullptr;
   a.level = idx->d_level;

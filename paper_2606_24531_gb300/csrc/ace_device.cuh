@@ -36,7 +36,7 @@ struct IndexHdr {
   uint32_t err_block;
   uint32_t err_where;
   uint32_t n_levels;
-  uint32_t max_ntok;   // most tokens in any block: sizes the per-warp token records
+  uint32_t max_ntok;   // most tokens in any block: sizes a seek slot's match records
   uint32_t pad0;
   uint64_t n_matches;  // matches in the archive: sizes a whole decode's match records
   uint32_t relax[8];   // level sweep k changed a level
