@@ -247,10 +247,20 @@ __device__ __forceinline__ bool stream_open(const uint8_t* pay, uint32_t sbytes,
   return true;
 }
 
-// Streams this short are decoded by searching the present symbols' ranges
-// instead of building the 4096-entry slot table: fewer rounds than the table
-// costs to build.
+// Short streams are decoded by searching the present symbols' ranges
+// instead of building the 4096-entry slot table when that costs less: a
+// search step per level of the k present symbols per round, against the
+// table's build (kSearchStep and kTableBuild, in warp instructions, set by
+// measurement: offset streams of 12 rounds over ~200 symbols decode faster
+// by search, length streams of ~30 rounds over ~100 symbols by the table).
 constexpr uint32_t kSearchMaxSymbols = 2048;
+constexpr uint32_t kSearchStep = 6;
+constexpr uint32_t kTableBuild = 1200;
+__device__ __forceinline__ bool use_search(uint32_t nsym, uint32_t k) {
+  if (nsym > kSearchMaxSymbols) return false;
+  const uint32_t depth = k > 1 ? 32 - __clz(k - 1) : 0;  // ceil(log2 k)
+  return ((nsym + 31) / 32) * kSearchStep * depth <= kTableBuild;
+}
 
 // Builds the stream's decode tables.  Slot table mode: fc[s] = f_s << 16 |
 // c_s, and the slot -> symbol table by marking each symbol's first slot and
@@ -281,7 +291,8 @@ __device__ __forceinline__ bool lut_build(Stream& st, Lut& lut, uint32_t lane) {
   uint32_t cincl = warp_incl_sum(fsum, lane);
   bad |= __shfl_sync(kFull, cincl, 31) != ACE_SCALE;
   if (__any_sync(kFull, bad)) return false;
-  if (st.nsym <= kSearchMaxSymbols) {
+  const uint32_t present = __shfl_sync(kFull, first + cnt, 31);  // present symbols
+  if (use_search(st.nsym, present)) {
     uint32_t* pk = reinterpret_cast<uint32_t*>(lut.sym);
     uint32_t c = cincl - fsum, j = first;
 #pragma unroll
@@ -290,9 +301,8 @@ __device__ __forceinline__ bool lut_build(Stream& st, Lut& lut, uint32_t lane) {
         pk[j++] = (c << 20) | ((f[q] - 1) << 8) | (lane * 8 + q);
         c += f[q];
       }
-    uint32_t k = __shfl_sync(kFull, warp_incl_sum(cnt, lane), 31);
-    st.k = k;
-    st.kstep = k > 1 ? 1u << (31 - __clz(k - 1)) : 0u;
+    st.k = present;
+    st.kstep = present > 1 ? 1u << (31 - __clz(present - 1)) : 0u;
     __syncwarp();
     return true;
   }
