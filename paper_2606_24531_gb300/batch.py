@@ -183,8 +183,7 @@ def time_per_object(items, out_views, reps=1):
     whole sequence).  One scratch buffer, sized for the largest object,
     serves every call: calls on one stream run in order, and a whole decode
     of these archives (at most 32 dependency levels) uses only the scratch
-    header, its per-warp records and its match records, each rewritten by
-    the call."""
+    header and its match records, both rewritten by the call."""
     st = torch.cuda.current_stream()
     nbytes = max(ace.ace_scratch_size(x.idx, 0) for x in items)
     scratch = torch.empty(nbytes, dtype=torch.uint8, device=items[0].device)
