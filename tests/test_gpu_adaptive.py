@@ -140,3 +140,34 @@ def test_adaptive_genome_is_smaller_and_decodes():
     assert a1.size < a0.size
     st, out = _decode(a1, ace.ACE_SCHEDULE_PASSES)
     assert st == ace.ACE_OK and np.array_equal(out, data)
+
+
+def test_source_not_before_its_destination_is_reported():
+    """A match whose absolute source lies at or after its own destination
+    breaks the rule of the sequential copy (Section 2).  Patched into a
+    stored offset stream, where no rANS end-of-stream check can catch it,
+    it must come back as ACE_E_CORRUPT from whole decodes under both
+    schedules and from a seek of its block, as the oracle rejects it too."""
+    data = synth.generate("genome", 2_000_000, 9)
+    arc = ace.ace_encode(data, 14, 20, adaptive=True)
+    hdr = arc[:64].view(np.uint64)
+    total, nb, dir_off, payload_off = (int(hdr[i]) for i in (2, 3, 4, 6))
+    w = int(arc[9])  # off_width
+    d = arc[dir_off:dir_off + 64 * nb].reshape(nb, 64)
+    stored_off = [b for b in range(1, nb - 1)
+                  if d[b, 58] == 1 and int(d[b, 44:48].copy().view(np.uint32)[0]) >= w]
+    assert stored_off, "no block with a stored offset stream"
+    b = stored_off[len(stored_off) // 2]
+    off = payload_off + int(d[b, 16:24].copy().view(np.uint64)[0])  # the block's first match source
+    bad = arc.copy()
+    bad[off:off + w] = np.frombuffer(np.uint64(total - 1).tobytes()[:w], np.uint8)  # the data's last byte
+    with pytest.raises(oracle.OracleError):
+        oracle.decode(bad)
+    for schedule in SCHEDULES:
+        st, _ = _decode(bad, schedule)
+        assert st == ace.ACE_E_CORRUPT, ace.ace_status_str(st)
+    da = DeviceArchive(bad, max_seek_blocks=1024)
+    B = 1 << 14
+    da.seek(b * B, B)
+    assert da.sync() == ace.ACE_E_CORRUPT
+    da.close()
