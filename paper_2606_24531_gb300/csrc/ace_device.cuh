@@ -180,7 +180,6 @@ struct Stream {
   const uint8_t* g;    // renormalisation bytes (16-byte aligned); the payload starts head bytes before
   uint32_t head;       // bytes of states, present bitmap and frequencies
   uint32_t k;          // search mode: present symbols (0: slot table mode)
-  uint32_t kstep;      // search mode: largest power of two below k
   uint32_t nsym;       // symbols in the stream
   uint32_t nbytes;     // renormalisation bytes
   uint32_t next;       // next symbol index to decode
@@ -218,7 +217,7 @@ __device__ __forceinline__ bool stream_open(const uint8_t* pay, uint32_t sbytes,
   st.x = ACE_RANS_L;
   st.g = pay;
   st.head = 0;
-  st.k = st.kstep = 0;
+  st.k = 0;
   st.nbytes = 0;
   st.stored = mode == 1;
   if (nsym == 0) return sbytes == 0;
@@ -254,6 +253,7 @@ __device__ __forceinline__ bool stream_open(const uint8_t* pay, uint32_t sbytes,
 // measurement: offset streams of 12 rounds over ~200 symbols decode faster
 // by search, length streams of ~30 rounds over ~100 symbols by the table).
 constexpr uint32_t kSearchMaxSymbols = 2048;
+constexpr uint32_t kCoarseOff = 1024;  // search mode: the coarse table after the (at most 256) packed words
 constexpr uint32_t kSearchStep = 6;
 constexpr uint32_t kTableBuild = 1200;
 __device__ __forceinline__ bool use_search(uint32_t nsym, uint32_t k) {
@@ -293,16 +293,35 @@ __device__ __forceinline__ bool lut_build(Stream& st, Lut& lut, uint32_t lane) {
   if (__any_sync(kFull, bad)) return false;
   const uint32_t present = __shfl_sync(kFull, first + cnt, 31);  // present symbols
   if (use_search(st.nsym, present)) {
+    // the packed words, and beside them the coarse table: entry b is the
+    // index of the symbol owning slot 16 b.  Each symbol marks the first
+    // bucket start in its range; a prefix maximum carries the mark over the
+    // rest of the range (indices grow with slots, and slot 0 is marked).
     uint32_t* pk = reinterpret_cast<uint32_t*>(lut.sym);
+    uint8_t* cz = lut.sym + kCoarseOff;
+    reinterpret_cast<uint2*>(cz)[lane] = make_uint2(0u, 0u);
+    __syncwarp();
     uint32_t c = cincl - fsum, j = first;
 #pragma unroll
     for (int q = 0; q < 8; q++)
       if (f[q]) {
-        pk[j++] = (c << 20) | ((f[q] - 1) << 8) | (lane * 8 + q);
+        pk[j] = (c << 20) | ((f[q] - 1) << 8) | (lane * 8 + q);
+        const uint32_t bb = (c + 15) >> 4;  // the first bucket starting in [c, c + f)
+        if (16 * bb < c + f[q]) cz[bb] = (uint8_t)j;
+        j++;
         c += f[q];
       }
+    __syncwarp();
+    uint2 w = reinterpret_cast<uint2*>(cz)[lane];  // entries 8 lane .. 8 lane + 7
+    w.x = __vmaxu4(w.x, w.x << 8);
+    w.x = __vmaxu4(w.x, w.x << 16);
+    w.y = __vmaxu4(w.y, w.y << 8);
+    w.y = __vmaxu4(__vmaxu4(w.y, w.y << 16), (w.x >> 24) * 0x01010101u);
+    const uint32_t carry = warp_excl_max(w.y >> 24, lane);
+    w.x = __vmaxu4(w.x, carry * 0x01010101u);
+    w.y = __vmaxu4(w.y, carry * 0x01010101u);
+    reinterpret_cast<uint2*>(cz)[lane] = w;
     st.k = present;
-    st.kstep = present > 1 ? 1u << (31 - __clz(present - 1)) : 0u;
     __syncwarp();
     return true;
   }
@@ -351,11 +370,8 @@ __device__ __forceinline__ void lookup(const Stream& st, const Lut& lut, uint32_
                                        uint32_t& c) {
   if (st.k) {
     const uint32_t* pk = reinterpret_cast<const uint32_t*>(lut.sym);
-    uint32_t lo = 0;
-    for (uint32_t step = st.kstep; step; step >>= 1) {
-      uint32_t j = lo + step;
-      if (j < st.k && (pk[j] >> 20) <= slot) lo = j;
-    }
+    uint32_t lo = lut.sym[kCoarseOff + (slot >> 4)];  // owner of the bucket's first slot
+    while (lo + 1 < st.k && (pk[lo + 1] >> 20) <= slot) lo++;  // at most 15 starts inside a bucket
     uint32_t e = pk[lo];
     s = e & 0xffu;
     f = ((e >> 8) & 0xfffu) + 1;
