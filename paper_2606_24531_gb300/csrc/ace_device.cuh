@@ -246,21 +246,13 @@ __device__ __forceinline__ bool stream_open(const uint8_t* pay, uint32_t sbytes,
   return true;
 }
 
-// Short streams are decoded by searching the present symbols' ranges
-// instead of building the 4096-entry slot table when that costs less: a
-// search step per level of the k present symbols per round, against the
-// table's build (kSearchStep and kTableBuild, in warp instructions, set by
-// measurement: offset streams of 12 rounds over ~200 symbols decode faster
-// by search, length streams of ~30 rounds over ~100 symbols by the table).
+// Streams of at most kSearchMaxSymbols symbols are decoded by looking their
+// symbols up among the present ones (a coarse table of bucket owners, then a
+// short forward step) instead of building the 4096-entry slot table, whose
+// build costs more than such a stream's rounds save (measured on the FASTQ,
+// genome and text token streams and on batches of 4-64 KiB blocks).
 constexpr uint32_t kSearchMaxSymbols = 2048;
 constexpr uint32_t kCoarseOff = 1024;  // search mode: the coarse table after the (at most 256) packed words
-constexpr uint32_t kSearchStep = 6;
-constexpr uint32_t kTableBuild = 1200;
-__device__ __forceinline__ bool use_search(uint32_t nsym, uint32_t k) {
-  if (nsym > kSearchMaxSymbols) return false;
-  const uint32_t depth = k > 1 ? 32 - __clz(k - 1) : 0;  // ceil(log2 k)
-  return ((nsym + 31) / 32) * kSearchStep * depth <= kTableBuild;
-}
 
 // Builds the stream's decode tables.  Slot table mode: fc[s] = f_s << 16 |
 // c_s, and the slot -> symbol table by marking each symbol's first slot and
@@ -292,7 +284,7 @@ __device__ __forceinline__ bool lut_build(Stream& st, Lut& lut, uint32_t lane) {
   bad |= __shfl_sync(kFull, cincl, 31) != ACE_SCALE;
   if (__any_sync(kFull, bad)) return false;
   const uint32_t present = __shfl_sync(kFull, first + cnt, 31);  // present symbols
-  if (use_search(st.nsym, present)) {
+  if (st.nsym <= kSearchMaxSymbols) {
     // the packed words, and beside them the coarse table: entry b is the
     // index of the symbol owning slot 16 b.  Each symbol marks the first
     // bucket start in its range; a prefix maximum carries the mark over the
